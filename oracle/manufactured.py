@@ -1,0 +1,66 @@
+"""Manufactured solutions u and sources f = -Laplace(u) (oracle, Section 3.1).
+
+TEST INFRASTRUCTURE ONLY.
+
+For the annulus maps (geometry.Annulus) the solution is written in the
+coordinates with the twist and swell undone, (x', y', zeta):
+
+    u = (rho^2 - r_in^2)(r_out^2 - rho^2) x' y' zeta (1 - zeta)
+        * (1 + sum_k a_k sin(b_k . x + c_k)),          rho^2 = x'^2 + y'^2,
+
+which vanishes on all six faces of the patch (homogeneous Dirichlet data).
+With r_in = 1, r_out = 2, H = 1, no twist and no modes it is
+(r^2 - 1)(4 - r^2) x y z (1 - z).  For geometry.Box the bubble is
+sin(pi x/Lx) sin(pi y/Ly) sin(pi z/Lz) times the same modulation.
+f = -Laplace(u) in physical coordinates, by hyper-dual differentiation.
+"""
+import numpy as np
+
+from . import hyperdual as hd
+from .geometry import Annulus, Box
+
+
+class Manufactured:
+    def __init__(self, geom, modes=()):
+        """modes: iterable of (a, (b1, b2, b3), c) for the factor 1 + sum a sin(b.x + c)."""
+        self.geom = geom
+        self.modes = [(float(a), tuple(float(v) for v in b), float(c)) for a, b, c in modes]
+
+    def _u(self, x, y, z):
+        g = self.geom
+        if isinstance(g, Annulus):
+            zeta = z * (1.0 / g.height)
+            phi = zeta * g.twist
+            s = 1.0 + g.swell * hd.sin(zeta * np.pi)
+            cp, sp = hd.cos(phi), hd.sin(phi)
+            xp = (cp * x + sp * y) / s
+            yp = (cp * y - sp * x) / s
+            rho2 = xp * xp + yp * yp
+            bubble = (rho2 - g.r_in ** 2) * (g.r_out ** 2 - rho2) * xp * yp * zeta * (1.0 - zeta)
+        elif isinstance(g, Box):
+            bubble = (hd.sin(x * (np.pi / g.L[0])) * hd.sin(y * (np.pi / g.L[1]))
+                      * hd.sin(z * (np.pi / g.L[2])))
+        else:
+            raise TypeError("unknown geometry")
+        mod = 1.0
+        for a, (b1, b2, b3), c in self.modes:
+            mod = mod + a * hd.sin(x * b1 + y * b2 + z * b3 + c)
+        return bubble * mod
+
+    def u(self, X):
+        """Exact solution at physical points X[..., 3]."""
+        return np.asarray(self._u(X[..., 0], X[..., 1], X[..., 2]), dtype=np.float64) * np.ones(X.shape[:-1])
+
+    def f(self, X):
+        """Source term f = -Laplace(u) at physical points X[..., 3]."""
+        return -hd.laplacian(self._u, X)
+
+
+class ConstantSource:
+    """f = value everywhere and no exact solution (volume / load-vector pins)."""
+
+    def __init__(self, value=1.0):
+        self.value = float(value)
+
+    def f(self, X):
+        return np.full(X.shape[:-1], self.value)

@@ -1,0 +1,78 @@
+"""Seeded synthetic inputs shared by the oracle tests, the CUDA-path tests and bench.py.
+
+This module holds problem descriptors and random draws only: no step of the
+TT-IGA method is computed here.  Every draw is a numpy PCG64 stream keyed by
+an explicit seed.
+
+Geometry descriptor (dict): kind ('annulus' or 'box'), r_in, r_out, height,
+twist, swell (annulus), lx, ly, lz (box).
+Right-hand-side descriptor: list of modes (a, (b1, b2, b3), c) modulating the
+manufactured bubble by 1 + sum a sin(b . x + c).
+"""
+import math
+
+import numpy as np
+
+QUARTER_CYLINDER = {"kind": "annulus", "r_in": 1.0, "r_out": 2.0, "height": 1.0, "twist": 0.0, "swell": 0.0}
+TWISTED_ANNULUS = {"kind": "annulus", "r_in": 1.0, "r_out": 2.0, "height": 1.0, "twist": 0.8, "swell": 0.2}
+UNIT_BOX = {"kind": "box", "lx": 1.0, "ly": 1.0, "lz": 1.0}
+
+# Named workloads.  Sizes are basis functions per direction (n) and degree (p).
+WORKLOADS = {
+    "quarter_cylinder_p2_n16": {"geometry": QUARTER_CYLINDER, "p": 2, "n": 16, "cross_tol": 1e-12,
+                                "round_tol": 1e-12, "modes": []},
+    "quarter_cylinder_p3_n128": {"geometry": QUARTER_CYLINDER, "p": 3, "n": 128, "cross_tol": 1e-12,
+                                 "round_tol": 1e-12, "modes": [], "sweep": [16, 32, 64, 128]},
+    "twisted_annulus_p3_n512": {"geometry": TWISTED_ANNULUS, "p": 3, "n": 512, "cross_tol": 1e-10,
+                                "round_tol": 1e-10, "modes": []},
+}
+
+
+def rng(seed):
+    return np.random.Generator(np.random.PCG64(int(seed)))
+
+
+def random_tt_cores(dims, ranks, seed, scale=1.0):
+    """Gaussian TT cores G_k[r_{k-1}, n_k, r_k] with r_0 = r_d = 1."""
+    g = rng(seed)
+    r = [1] + list(ranks) + [1]
+    return [scale * g.standard_normal((r[k], dims[k], r[k + 1])) for k in range(len(dims))]
+
+
+def random_modes(seed, count=None):
+    """Random smooth modulation modes: |a| <= 0.3, |b| <= 3, c in [0, 2 pi)."""
+    g = rng(seed)
+    k = int(g.integers(1, 4)) if count is None else int(count)
+    modes = []
+    for _ in range(k):
+        a = float(g.uniform(-0.3, 0.3))
+        v = g.standard_normal(3)
+        v = v / np.linalg.norm(v) * g.uniform(0.0, 3.0)
+        c = float(g.uniform(0.0, 2.0 * math.pi))
+        modes.append((a, tuple(float(t) for t in v), c))
+    return modes
+
+
+def random_instance(seed, n_lo=32, n_hi=256):
+    """One instance of the batched workload (geometry, degree, size, right-hand sides)."""
+    g = rng(1_000_003 * int(seed) + 17)
+    r_in = float(g.uniform(0.5, 1.5))
+    thick = float(g.uniform(0.5, 1.5))
+    twist = float(g.uniform(0.0, 1.2))
+    p = int(g.choice([2, 3]))
+    n = int(round(math.exp(g.uniform(math.log(n_lo), math.log(n_hi)))))
+    n_rhs = int(g.integers(1, 9))
+    geom = {"kind": "annulus", "r_in": r_in, "r_out": r_in + thick, "height": 1.0, "twist": twist, "swell": 0.0}
+    rhs = [random_modes(10_000 * int(seed) + k) for k in range(n_rhs)]
+    return {"seed": int(seed), "geometry": geom, "p": p, "n": n, "rhs": rhs}
+
+
+def poisson_arrivals(rate_hz, count, seed):
+    """Arrival times (s) of an open-loop Poisson request stream."""
+    g = rng(seed)
+    return np.cumsum(g.exponential(1.0 / rate_hz, size=count))
+
+
+def random_points(m, seed):
+    """m parametric points in [0, 1]^3."""
+    return rng(seed).uniform(0.0, 1.0, size=(m, 3))
