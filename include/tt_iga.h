@@ -1,0 +1,305 @@
+/*
+ * tt_iga.h -- C ABI of the TT-IGA library: a tensor-train isogeometric solver
+ * for the 3D Poisson problem -Laplace(u) = f with homogeneous Dirichlet data
+ * on a single-patch spline geometry, running on one NVIDIA GB300 (sm_103a).
+ *
+ * Method (arXiv 2509.13224):
+ *   geometry coefficients R = det J J^{-1} J^{-T} (Eq. Rxi) and the source
+ *   f det J sampled at tensor Gauss points are compressed into TT cores by
+ *   TT-cross (Section 4.1.2, 4.2.1, 4.2.2); each core is contracted per
+ *   direction with the univariate basis factors a_ij^(d) into the cores of a
+ *   TT-matrix stiffness K and a TT load vector F (Section 4.2.1-4.2.2); the
+ *   sum over (i, j) is recompressed by TT rounding (Section 4.2.1, global
+ *   assembly); the Dirichlet rows/columns are removed (Section 4.3); and the
+ *   system K u = F is solved by an AMEn TT solver (Section 4.1.2).
+ *
+ * Conventions shared by every call:
+ *   - Return value: 0 (TT_IGA_OK) on success, a negative tt_iga_status on
+ *     failure; tt_iga_last_error(ctx) then holds a one-line message.
+ *   - Every call runs on the context's CUDA stream.  Device inputs must be
+ *     ready when the call is made.  Calls that return host values (ranks,
+ *     statistics, norms, host buffers) and the kernel-level entry points
+ *     synchronise that stream before returning.
+ *   - Opaque handles (tt_iga_geom, tt_iga_system, tt_iga_solution) are owned by
+ *     the library and released with the matching *_destroy call; they must not
+ *     outlive their context.
+ *   - Pointers documented as "device" must be device (or managed) memory of the
+ *     context's device; "host" pointers are ordinary host memory.  Arrays are
+ *     dense, row-major (last index fastest) unless stated.
+ *   - Direction d = 1, 2, 3 is parametric coordinate xi_d.  The flattened
+ *     global index of a multi-index (i1, i2, i3) is g = i1 + n1 (i2 + n2 i3)
+ *     (i1 fastest).  For the annulus geometry xi_1 is radial, xi_2 angular and
+ *     xi_3 axial.
+ *   - TT cores of a tensor with mode sizes n_k are stored as
+ *     G_k[r_{k-1}][n_k][r_k] with r_0 = r_3 = 1 (Section 4.1.1).  TT-matrix
+ *     cores are band-stored as M_k[r_{k-1}][n_k][2p+1][r_k]: entry (i, j) of
+ *     mode k is at band slot o = j - i + p; slots with j outside [0, n_k) hold 0.
+ *   - All arithmetic is FP64 unless a call says otherwise.
+ */
+#ifndef TT_IGA_H
+#define TT_IGA_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  TT_IGA_OK = 0,
+  TT_IGA_ERR_ARG = -1,           /* invalid argument (null pointer, size, enum) */
+  TT_IGA_ERR_OOM = -2,           /* device allocation failed */
+  TT_IGA_ERR_CUDA = -3,          /* a CUDA runtime call or kernel launch failed */
+  TT_IGA_ERR_NOT_CONVERGED = -4, /* iteration cap reached; a partial result is still returned */
+  TT_IGA_ERR_TIMEOUT = -5,       /* a bounded device-side wait ran out */
+  TT_IGA_ERR_TOO_LARGE = -6,     /* a size exceeds a documented limit */
+  TT_IGA_ERR_BAD_GEOMETRY = -7,  /* det J <= 0 somewhere on the quadrature grid */
+  TT_IGA_ERR_STATE = -8          /* handle used with the wrong context or in the wrong state */
+} tt_iga_status;
+
+typedef struct tt_iga_ctx tt_iga_ctx;
+typedef struct tt_iga_geom tt_iga_geom;
+typedef struct tt_iga_system tt_iga_system;
+typedef struct tt_iga_solution tt_iga_solution;
+
+/* ---------------------------------------------------------------- context */
+
+typedef struct {
+  void *stream;  /* cudaStream_t to run on (cudaStreamLegacy = (void*)1 is accepted); NULL: the
+                  * library creates its own non-blocking stream */
+  int device;    /* CUDA device ordinal */
+  /* Optional device allocator (both or neither).  NULL: stream-ordered
+   * cudaMallocAsync / cudaFreeAsync on the context stream. */
+  void *(*alloc_fn)(size_t bytes, void *stream, void *user);
+  void (*free_fn)(void *ptr, void *stream, void *user);
+  void *alloc_user;
+} tt_iga_ctx_opts;
+
+/* Create a context.  o may be NULL (device 0, own stream, default allocator). */
+int tt_iga_ctx_create(tt_iga_ctx **ctx, const tt_iga_ctx_opts *o);
+/* Synchronise and destroy; releases everything the context still owns. */
+void tt_iga_ctx_destroy(tt_iga_ctx *ctx);
+/* Message of the last failing call on ctx ("" if none).  Valid until the next call. */
+const char *tt_iga_last_error(const tt_iga_ctx *ctx);
+/* Bytes currently held by the context's device allocations. */
+int tt_iga_ctx_memory(const tt_iga_ctx *ctx, size_t *bytes_in_use, size_t *bytes_peak);
+/* Number of CUDA kernels the library has launched in this process (all contexts). */
+unsigned long long tt_iga_launch_count(void);
+
+/* Live timing of one kernel family on the context stream, for roofline
+ * reporting: every launch of the family is bracketed by a CUDA event pair.
+ * family: 0 off, 1 band stage of the AMEn local matvec, 2 FP64 GEMM,
+ * 3 Householder QR panel.  Enabling resets the record. */
+int tt_iga_profile_enable(tt_iga_ctx *ctx, int family);
+/* Synchronise and return the summed event time (ms), the number of timed
+ * launches and their summed algorithmic FLOPs. */
+int tt_iga_profile_read(tt_iga_ctx *ctx, double *ms_total, long long *launches, double *flops_total);
+
+/* --------------------------------------------------------------- geometry */
+
+enum { TT_IGA_GEOM_BOX = 0, TT_IGA_GEOM_ANNULUS = 1 };
+
+/* Geometry and discretisation (Section 3.3, Section 2).
+ *  ANNULUS: quarter annulus of radii r_in < r_out and height `height`: radial
+ *    degree-1 B-spline, angular quadratic NURBS quarter arc (weights 1,
+ *    sqrt(2)/2, 1), axial degree-1 B-spline, composed with a twist about z by
+ *    angle twist*zeta and a radial swell 1 + swell*sin(pi zeta), zeta = z/height.
+ *  BOX: [0,lx] x [0,ly] x [0,lz].
+ * Discretisation: open uniform knots with n[d] B-splines of degree p per
+ * direction (n[d] >= p+2 so that interior unknowns exist), nq Gauss points
+ * per element (0: p+1).  The coefficient fields R_ij are compressed by TT-cross
+ * to relative accuracy cross_tol with TT ranks capped at max_rank (0: 64);
+ * seed drives the random fibre and validation samples. */
+typedef struct {
+  int kind;
+  double r_in, r_out, height, twist, swell;
+  double lx, ly, lz;
+  int p;
+  int n[3];
+  int nq;
+  double cross_tol;
+  int max_rank;
+  uint64_t seed;
+} tt_iga_geom_desc;
+
+/* Build the 1D tables of every direction and the TT cores of the six unique
+ * entries of R (Section 4.2.1, R_ij^TT) on the device.  ERR_BAD_GEOMETRY if a
+ * sampled det J <= 0; ERR_NOT_CONVERGED if the cross did not validate within
+ * max_rank (the handle is still returned). */
+int tt_iga_geometry(tt_iga_ctx *ctx, const tt_iga_geom_desc *g, tt_iga_geom **out);
+void tt_iga_geom_destroy(tt_iga_geom *g);
+/* TT ranks (r1, r2) of field f = 0..5 in the order R11, R12, R13, R22, R23, R33
+ * (rank 0 marks a field that is zero to the cross tolerance), plus the
+ * validated maximum relative sample error of each field. */
+int tt_iga_geom_ranks(const tt_iga_geom *g, int ranks[6][2], double max_rel_err[6]);
+
+/* ------------------------------------------------------------ right-hand side */
+
+enum { TT_IGA_RHS_MANUFACTURED = 0, TT_IGA_RHS_CONSTANT = 1 };
+#define TT_IGA_MAX_MODES 8
+
+/* Source term.  MANUFACTURED: f = -Laplace(u) of the bubble solution of the
+ * geometry (annulus: (rho^2 - r_in^2)(r_out^2 - rho^2) x' y' zeta (1 - zeta) in
+ * the coordinates with twist and swell undone; box: sin(pi x/lx) sin(pi y/ly)
+ * sin(pi z/lz)) times 1 + sum_k a[k] sin(b[k] . x + c[k]); the Laplacian is
+ * taken exactly on the device by hyper-dual arithmetic.  CONSTANT: f = value. */
+typedef struct {
+  int kind;
+  int n_modes; /* 0 .. TT_IGA_MAX_MODES */
+  double a[TT_IGA_MAX_MODES];
+  double b[TT_IGA_MAX_MODES][3];
+  double c[TT_IGA_MAX_MODES];
+  double value;
+} tt_iga_rhs_desc;
+
+/* --------------------------------------------------------------- assembly */
+
+/* Assemble the restricted TT system (Sections 4.2-4.3): K^TT = sum_ij K_ij^TT
+ * from the R_ij cores by per-direction quadrature contraction, rounded to
+ * relative accuracy round_tol (Oseledets QR + SVD rounding, FP64), and one TT
+ * load vector per right-hand side (f det J by TT-cross to cross_tol, then the
+ * per-direction contraction with N_d).  Boundary functions 0 and n_d - 1 of
+ * every direction are dropped (homogeneous Dirichlet data), so the unknowns
+ * per direction are n_d - 2.  rhs points to n_rhs descriptors (n_rhs >= 1). */
+int tt_iga_assemble(tt_iga_ctx *ctx, const tt_iga_geom *g, const tt_iga_rhs_desc *rhs, int n_rhs,
+                    double round_tol, tt_iga_system **out);
+void tt_iga_system_destroy(tt_iga_system *s);
+/* Operator TT ranks (R1, R2), load ranks of right-hand side k, and mode sizes. */
+int tt_iga_system_info(const tt_iga_system *s, int op_ranks[2], int n_rhs_max, int (*rhs_ranks)[2],
+                       int modes[3]);
+
+/* ------------------------------------------------------------------ solve */
+
+enum { TT_IGA_FP64 = 0, TT_IGA_MIXED_FP32 = 1, TT_IGA_MIXED_TF32 = 2 };
+
+/* AMEn options (Section 4.1.2).  tol: target relative residual
+ * ||F - K u||_2 / ||F||_2.  precision FP64: every contraction in FP64;
+ * MIXED_*: local linear solves run in FP32 (SIMT) or TF32 (tensor cores, FP32
+ * accumulation) inside FP64 iterative refinement of each local system, while
+ * interfaces, residuals, QR/SVD truncation stay FP64.  Zero fields take the
+ * defaults in brackets. */
+typedef struct {
+  double tol;       /* [1e-8] */
+  int precision;    /* [TT_IGA_FP64] */
+  int max_sweeps;   /* [30] */
+  int kickrank;     /* [4] residual enrichment columns per step; negative disables */
+  int max_rank;     /* [256] */
+  int local_maxit;  /* [500] local PCG iteration cap */
+  int rhs_index;    /* which right-hand side of the system to solve [0] */
+  int verbose;      /* print one line per sweep to stderr */
+} tt_iga_solve_opts;
+
+typedef struct {
+  int sweeps;
+  int ranks[2];
+  double rel_residual;      /* exact ||F - K u|| / ||F|| from TT arithmetic, or -1 if skipped */
+  double local_residual;    /* largest relative local residual of the last sweep */
+  long long local_matvecs;  /* local operator applications (all precisions) */
+  long long local_matvecs_fp64;
+  double ms_total;          /* device time of the solve (CUDA events) */
+  int converged;
+} tt_iga_stats;
+
+/* Solve K u = F for right-hand side opts->rhs_index.  On ERR_NOT_CONVERGED the
+ * last iterate is returned in *out.  st may be NULL. */
+int tt_iga_solve(tt_iga_ctx *ctx, const tt_iga_system *s, const tt_iga_solve_opts *opts,
+                 tt_iga_solution **out, tt_iga_stats *st);
+void tt_iga_solution_destroy(tt_iga_solution *u);
+/* TT ranks of the solution. */
+int tt_iga_solution_ranks(const tt_iga_solution *u, int ranks[2]);
+/* Exact relative residual ||F - K u||_2 / ||F||_2 of u against right-hand side k,
+ * computed in TT arithmetic with orthogonal projections (FP64). */
+int tt_iga_residual(tt_iga_ctx *ctx, const tt_iga_system *s, const tt_iga_solution *u, int k,
+                    double *rel_residual);
+
+/* Copy the solution's TT cores to host memory: out receives core 1
+ * [1][m1][r1], core 2 [r1][m2][r2] and core 3 [r2][m3][1] back to back (FP64);
+ * modes[3] (m_d = n_d - 2) and ranks[4] are filled.  ERR_TOO_LARGE if cap (in
+ * doubles) is too small; pass out = NULL to query the sizes only. */
+int tt_iga_solution_cores(tt_iga_ctx *ctx, const tt_iga_solution *u, double *out, size_t cap, int modes[3],
+                          int ranks[4]);
+
+/* ------------------------------------------------------------ evaluation */
+
+/* u_h(xi) = sum_a u_a N_a(xi) at m parametric points xi[m][3] in [0,1]^3.
+ * xi and u_out are device pointers (FP64). */
+int tt_iga_eval(tt_iga_ctx *ctx, const tt_iga_solution *u, int m, const double *xi, double *u_out);
+/* Relative L2 error sqrt(int (u_h - u)^2) / sqrt(int u^2) over the mapped
+ * domain (Eq. L2norm, with p+3 Gauss points per element) against the
+ * manufactured solution of rhs (kind MANUFACTURED). */
+int tt_iga_l2_error(tt_iga_ctx *ctx, const tt_iga_geom *g, const tt_iga_solution *u,
+                    const tt_iga_rhs_desc *rhs, double *rel_l2);
+
+/* ----------------------------------------------------- dense test hooks */
+
+/* Dense restricted operator (N x N, N = prod(n_d - 2), host, row g = i1 + ...).
+ * ERR_TOO_LARGE if N > 4096 or cap < N*N. */
+int tt_iga_densify_operator(tt_iga_ctx *ctx, const tt_iga_system *s, double *out, size_t cap);
+/* Dense restricted load vector k / solution (N entries, host). ERR_TOO_LARGE if N > 2^22. */
+int tt_iga_densify_rhs(tt_iga_ctx *ctx, const tt_iga_system *s, int k, double *out, size_t cap);
+int tt_iga_densify_solution(tt_iga_ctx *ctx, const tt_iga_solution *u, double *out, size_t cap);
+/* Entries of the restricted operator / load / solution at m multi-indices
+ * (host int arrays rows[m][3], cols[m][3], 0-based restricted indices) into host out[m]. */
+int tt_iga_operator_entries(tt_iga_ctx *ctx, const tt_iga_system *s, int m, const int *rows,
+                            const int *cols, double *out);
+int tt_iga_vector_entries(tt_iga_ctx *ctx, const tt_iga_system *s, const tt_iga_solution *u, int k,
+                          int m, const int *idx, double *out);
+
+/* ------------------------------------------------- kernel-level entry points */
+
+/* 1D tables (Section 2.1): Q = (n - p) * nq Gauss points of the open uniform
+ * knot vector, ordered element by element.  Device outputs: pts[Q], wts[Q],
+ * N[Q][p+1], dN[Q][p+1] (value / derivative of basis e + k at point q of
+ * element e).  p <= 7, nq <= 8. */
+int tt_iga_basis_tables(tt_iga_ctx *ctx, int n, int p, int nq, double *pts, double *wts, double *N,
+                        double *dN);
+
+/* Point evaluator (Section 3.3, Eq. Rxi): for m grid points given by device
+ * int32 idx[m][3] into the Gauss grids of g, writes device out[m][8] =
+ * (R11, R12, R13, R22, R23, R33, det J, f det J) with f from rhs (may be NULL:
+ * f = 0).  *bad_geometry (host) is set to the number of points with det J <= 0. */
+int tt_iga_geom_points(tt_iga_ctx *ctx, const tt_iga_geom *g, const tt_iga_rhs_desc *rhs, int m,
+                       const int *idx, double *out, long long *bad_geometry);
+
+/* Per-direction quadrature contraction (Section 4.2.1):
+ *   M[a][o][b] with b index = beta: M[alpha][i][o][beta] = sum_q w_q G[alpha][q][beta] A[i][q] B[i+o-p][q]
+ * for a coefficient core G[r0][Q][r1] (device), with A, B chosen by
+ * test_deriv / trial_deriv (0: N, 1: N') from the tables of tt_iga_basis_tables
+ * for (n, p, nq).  Output M[r0][n][2p+1][r1] (device, fully overwritten). */
+int tt_iga_stiffness_core(tt_iga_ctx *ctx, int n, int p, int nq, const double *wts, const double *N,
+                          const double *dN, const double *G, int r0, int r1, int test_deriv,
+                          int trial_deriv, double *M);
+/* Load contraction (Section 4.2.2): F[alpha][i][beta] = sum_q w_q G[alpha][q][beta] N_i(q). */
+int tt_iga_load_core(tt_iga_ctx *ctx, int n, int p, int nq, const double *wts, const double *N,
+                     const double *G, int r0, int r1, double *F);
+
+/* TT rounding (Oseledets 2011, the recompression used after each summation in
+ * Section 4.2.1): right-to-left QR orthogonalisation then left-to-right
+ * truncated SVD with threshold eps ||X||_F / sqrt(d - 1), FP64.
+ * Input: d = 3 cores (device) of mode sizes nm[3] (n_k, or n_k (2p+1) for
+ * band-stored TT-matrices) and ranks r[4] (r[0] = r[3] = 1, r1, r2 <= 256).
+ * Output: the rounded cores are written to out_cores[k] (device, caller-owned,
+ * each with room for at least r[k] nm[k] r[k+1] doubles -- rounding never
+ * raises a rank) and their ranks to out_r[4] (host).  out_cores may alias
+ * cores.  max_rank caps the result (0: none). */
+int tt_iga_round(tt_iga_ctx *ctx, const int nm[3], const int r[4], const double *const cores[3],
+                 double eps, int max_rank, double *const out_cores[3], int out_r[4]);
+
+/* Tall-skinny Householder QR, FP64: A (device, m x k row-major, lda >= k)
+ * = Q R with Q (device, m x k, ld k) orthonormal columns and R (device, k x k
+ * upper triangular).  k <= 256.  Q may alias A only if lda == k. */
+int tt_iga_qr(tt_iga_ctx *ctx, int m, int k, const double *A, int lda, double *Q, double *R);
+/* SVD of a small square matrix A (device, k x k): A = U diag(s) V^T by
+ * one-sided Jacobi, FP64, singular values descending.  k <= 256. */
+int tt_iga_svd_small(tt_iga_ctx *ctx, int k, const double *A, double *U, double *s, double *V);
+/* Maximum-volume row selection (Goreinov et al. 2010) of a tall matrix U
+ * (device, m x r): device outputs rows[r] (int32) and B = U U[rows,:]^{-1}
+ * (device, m x r).  Stops when max |B| <= 1 + delta or after maxit swaps. */
+int tt_iga_maxvol(tt_iga_ctx *ctx, int m, int r, const double *U, double delta, int maxit, int *rows,
+                  double *B);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TT_IGA_H */

@@ -1,0 +1,446 @@
+"""Python binding of the TT-IGA C library (include/tt_iga.h).
+
+Argument marshalling only: every step of geometry, assembly, solve and
+evaluation runs in the CUDA kernels of libtt_iga.so.  PyTorch supplies device
+memory (for the kernel-level calls and evaluation points) and the CUDA stream.
+The functions keep the C names; failures raise TTIgaError carrying the status
+code and the library's last error message.  There is no fallback: if the
+shared library is missing, importing this package raises ImportError.
+"""
+import ctypes
+import os
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libtt_iga.so")
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError("libtt_iga.so is not built; run `python -c 'import __graft_entry__ as g; g.build()'`")
+_lib = ctypes.CDLL(LIB_PATH)
+
+OK, ERR_ARG, ERR_OOM, ERR_CUDA, ERR_NOT_CONVERGED, ERR_TIMEOUT, ERR_TOO_LARGE, ERR_BAD_GEOMETRY, ERR_STATE = (
+    0, -1, -2, -3, -4, -5, -6, -7, -8)
+GEOM_BOX, GEOM_ANNULUS = 0, 1
+RHS_MANUFACTURED, RHS_CONSTANT = 0, 1
+FP64, MIXED_FP32, MIXED_TF32 = 0, 1, 2
+MAX_MODES = 8
+
+_c_double_p = ctypes.POINTER(ctypes.c_double)
+_c_int_p = ctypes.POINTER(ctypes.c_int)
+
+
+class TTIgaError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"tt_iga error {code}: {msg}")
+        self.code = code
+
+
+class CtxOpts(ctypes.Structure):
+    _fields_ = [("stream", ctypes.c_void_p), ("device", ctypes.c_int),
+                ("alloc_fn", ctypes.c_void_p), ("free_fn", ctypes.c_void_p), ("alloc_user", ctypes.c_void_p)]
+
+
+class GeomDesc(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int), ("r_in", ctypes.c_double), ("r_out", ctypes.c_double),
+                ("height", ctypes.c_double), ("twist", ctypes.c_double), ("swell", ctypes.c_double),
+                ("lx", ctypes.c_double), ("ly", ctypes.c_double), ("lz", ctypes.c_double),
+                ("p", ctypes.c_int), ("n", ctypes.c_int * 3), ("nq", ctypes.c_int),
+                ("cross_tol", ctypes.c_double), ("max_rank", ctypes.c_int), ("seed", ctypes.c_uint64)]
+
+
+class RhsDesc(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int), ("n_modes", ctypes.c_int), ("a", ctypes.c_double * MAX_MODES),
+                ("b", (ctypes.c_double * 3) * MAX_MODES), ("c", ctypes.c_double * MAX_MODES),
+                ("value", ctypes.c_double)]
+
+
+class SolveOpts(ctypes.Structure):
+    _fields_ = [("tol", ctypes.c_double), ("precision", ctypes.c_int), ("max_sweeps", ctypes.c_int),
+                ("kickrank", ctypes.c_int), ("max_rank", ctypes.c_int), ("local_maxit", ctypes.c_int),
+                ("rhs_index", ctypes.c_int), ("verbose", ctypes.c_int)]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("sweeps", ctypes.c_int), ("ranks", ctypes.c_int * 2), ("rel_residual", ctypes.c_double),
+                ("local_residual", ctypes.c_double), ("local_matvecs", ctypes.c_longlong),
+                ("local_matvecs_fp64", ctypes.c_longlong), ("ms_total", ctypes.c_double),
+                ("converged", ctypes.c_int)]
+
+    def as_dict(self):
+        return {"sweeps": self.sweeps, "ranks": [self.ranks[0], self.ranks[1]],
+                "rel_residual": self.rel_residual, "local_residual": self.local_residual,
+                "local_matvecs": self.local_matvecs, "local_matvecs_fp64": self.local_matvecs_fp64,
+                "ms_total": self.ms_total, "converged": bool(self.converged)}
+
+
+_vp = ctypes.c_void_p
+_SIGS = {
+    "tt_iga_ctx_create": (ctypes.c_int, [ctypes.POINTER(_vp), ctypes.POINTER(CtxOpts)]),
+    "tt_iga_ctx_destroy": (None, [_vp]),
+    "tt_iga_last_error": (ctypes.c_char_p, [_vp]),
+    "tt_iga_ctx_memory": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_size_t), ctypes.POINTER(ctypes.c_size_t)]),
+    "tt_iga_launch_count": (ctypes.c_ulonglong, []),
+    "tt_iga_profile_enable": (ctypes.c_int, [_vp, ctypes.c_int]),
+    "tt_iga_profile_read": (ctypes.c_int, [_vp, _c_double_p, ctypes.POINTER(ctypes.c_longlong), _c_double_p]),
+    "tt_iga_solution_cores": (ctypes.c_int, [_vp, _vp, _c_double_p, ctypes.c_size_t, ctypes.POINTER(ctypes.c_int * 3),
+                                             ctypes.POINTER(ctypes.c_int * 4)]),
+    "tt_iga_geometry": (ctypes.c_int, [_vp, ctypes.POINTER(GeomDesc), ctypes.POINTER(_vp)]),
+    "tt_iga_geom_destroy": (None, [_vp]),
+    "tt_iga_geom_ranks": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_int * 2 * 6), ctypes.POINTER(ctypes.c_double * 6)]),
+    "tt_iga_assemble": (ctypes.c_int, [_vp, _vp, ctypes.POINTER(RhsDesc), ctypes.c_int, ctypes.c_double,
+                                       ctypes.POINTER(_vp)]),
+    "tt_iga_system_destroy": (None, [_vp]),
+    "tt_iga_system_info": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_int * 2), ctypes.c_int, _vp,
+                                          ctypes.POINTER(ctypes.c_int * 3)]),
+    "tt_iga_solve": (ctypes.c_int, [_vp, _vp, ctypes.POINTER(SolveOpts), ctypes.POINTER(_vp), ctypes.POINTER(Stats)]),
+    "tt_iga_solution_destroy": (None, [_vp]),
+    "tt_iga_solution_ranks": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_int * 2)]),
+    "tt_iga_residual": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int, _c_double_p]),
+    "tt_iga_eval": (ctypes.c_int, [_vp, _vp, ctypes.c_int, _vp, _vp]),
+    "tt_iga_l2_error": (ctypes.c_int, [_vp, _vp, _vp, ctypes.POINTER(RhsDesc), _c_double_p]),
+    "tt_iga_densify_operator": (ctypes.c_int, [_vp, _vp, _c_double_p, ctypes.c_size_t]),
+    "tt_iga_densify_rhs": (ctypes.c_int, [_vp, _vp, ctypes.c_int, _c_double_p, ctypes.c_size_t]),
+    "tt_iga_densify_solution": (ctypes.c_int, [_vp, _vp, _c_double_p, ctypes.c_size_t]),
+    "tt_iga_operator_entries": (ctypes.c_int, [_vp, _vp, ctypes.c_int, _c_int_p, _c_int_p, _c_double_p]),
+    "tt_iga_vector_entries": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int, ctypes.c_int, _c_int_p, _c_double_p]),
+    "tt_iga_basis_tables": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, _vp, _vp, _vp, _vp]),
+    "tt_iga_geom_points": (ctypes.c_int, [_vp, _vp, ctypes.POINTER(RhsDesc), ctypes.c_int, _vp, _vp,
+                                          ctypes.POINTER(ctypes.c_longlong)]),
+    "tt_iga_stiffness_core": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, _vp, _vp, _vp, _vp,
+                                             ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, _vp]),
+    "tt_iga_load_core": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, _vp, _vp, _vp, ctypes.c_int,
+                                        ctypes.c_int, _vp]),
+    "tt_iga_round": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_int * 3), ctypes.POINTER(ctypes.c_int * 4),
+                                    ctypes.POINTER(_vp * 3), ctypes.c_double, ctypes.c_int, ctypes.POINTER(_vp * 3),
+                                    ctypes.POINTER(ctypes.c_int * 4)]),
+    "tt_iga_qr": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, _vp, ctypes.c_int, _vp, _vp]),
+    "tt_iga_svd_small": (ctypes.c_int, [_vp, ctypes.c_int, _vp, _vp, _vp, _vp]),
+    "tt_iga_maxvol": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, _vp, ctypes.c_double, ctypes.c_int, _vp, _vp]),
+}
+for _name, (_res, _args) in _SIGS.items():
+    _fn = getattr(_lib, _name)
+    _fn.restype = _res
+    _fn.argtypes = _args
+
+
+def exported_symbols():
+    """Names of the C entry points this binding wraps."""
+    return sorted(_SIGS)
+
+
+def _check(ctx, code, allow=()):
+    if code != OK and code not in allow:
+        msg = _lib.tt_iga_last_error(ctx).decode() if ctx else ""
+        raise TTIgaError(code, msg)
+    return code
+
+
+def _ptr(t):
+    """Raw device pointer of a torch tensor (None -> NULL)."""
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+# ------------------------------------------------------------------ descriptors
+
+def geom_desc(geometry, p, n, cross_tol=1e-10, max_rank=0, seed=0, nq=0):
+    """GeomDesc from a geometry dict (see synthetic.py) and discretisation sizes."""
+    d = GeomDesc()
+    if geometry["kind"] == "annulus":
+        d.kind = GEOM_ANNULUS
+        d.r_in, d.r_out, d.height = geometry["r_in"], geometry["r_out"], geometry["height"]
+        d.twist, d.swell = geometry.get("twist", 0.0), geometry.get("swell", 0.0)
+    elif geometry["kind"] == "box":
+        d.kind = GEOM_BOX
+        d.lx, d.ly, d.lz = geometry["lx"], geometry["ly"], geometry["lz"]
+    else:
+        raise ValueError("unknown geometry kind")
+    d.p = int(p)
+    nn = [int(n)] * 3 if isinstance(n, int) else [int(v) for v in n]
+    for k in range(3):
+        d.n[k] = nn[k]
+    d.nq = int(nq)
+    d.cross_tol = float(cross_tol)
+    d.max_rank = int(max_rank)
+    d.seed = int(seed)
+    return d
+
+
+def rhs_desc(modes=(), constant=None):
+    """RhsDesc: manufactured source with modulation modes [(a, (b1,b2,b3), c)], or a constant f."""
+    r = RhsDesc()
+    if constant is not None:
+        r.kind = RHS_CONSTANT
+        r.value = float(constant)
+        return r
+    modes = list(modes)
+    if len(modes) > MAX_MODES:
+        raise ValueError("too many modes")
+    r.kind = RHS_MANUFACTURED
+    r.n_modes = len(modes)
+    for k, (a, b, c) in enumerate(modes):
+        r.a[k] = a
+        for j in range(3):
+            r.b[k][j] = b[j]
+        r.c[k] = c
+    return r
+
+
+def solve_opts(tol=1e-8, precision=FP64, max_sweeps=0, kickrank=0, max_rank=0, local_maxit=0, rhs_index=0,
+               verbose=False):
+    o = SolveOpts()
+    o.tol, o.precision, o.max_sweeps, o.kickrank = tol, precision, max_sweeps, kickrank
+    o.max_rank, o.local_maxit, o.rhs_index, o.verbose = max_rank, local_maxit, rhs_index, int(bool(verbose))
+    return o
+
+
+# --------------------------------------------------------------------- calls
+
+def tt_iga_ctx_create(stream=None, device=0):
+    """Context on `device`, running on `stream` (a torch.cuda.Stream, a raw handle, or None)."""
+    o = CtxOpts()
+    if stream is not None:
+        h = stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+        # handle 0 is the legacy default stream; pass it as cudaStreamLegacy so the
+        # library orders its work with the caller's instead of creating its own stream
+        o.stream = h if h != 0 else 1
+    o.device = device
+    h = ctypes.c_void_p()
+    _check(None, _lib.tt_iga_ctx_create(ctypes.byref(h), ctypes.byref(o)))
+    return h
+
+
+def tt_iga_ctx_destroy(ctx):
+    _lib.tt_iga_ctx_destroy(ctx)
+
+
+def tt_iga_last_error(ctx):
+    return _lib.tt_iga_last_error(ctx).decode()
+
+
+def tt_iga_ctx_memory(ctx):
+    a, b = ctypes.c_size_t(), ctypes.c_size_t()
+    _check(ctx, _lib.tt_iga_ctx_memory(ctx, ctypes.byref(a), ctypes.byref(b)))
+    return a.value, b.value
+
+
+def tt_iga_launch_count():
+    return int(_lib.tt_iga_launch_count())
+
+
+PROF_OFF, PROF_LOCAL_BAND, PROF_GEMM64, PROF_QR = 0, 1, 2, 3
+
+
+def tt_iga_profile_enable(ctx, family):
+    _check(ctx, _lib.tt_iga_profile_enable(ctx, int(family)))
+
+
+def tt_iga_profile_read(ctx):
+    ms, n, w = ctypes.c_double(), ctypes.c_longlong(), ctypes.c_double()
+    _check(ctx, _lib.tt_iga_profile_read(ctx, ctypes.byref(ms), ctypes.byref(n), ctypes.byref(w)))
+    return ms.value, n.value, w.value
+
+
+def tt_iga_solution_cores(ctx, u, out=None):
+    """Solution TT cores copied to host. With out (a float64 numpy buffer, ideally pinned) fills it in place."""
+    import numpy as np
+    modes, ranks = (ctypes.c_int * 3)(), (ctypes.c_int * 4)()
+    _check(ctx, _lib.tt_iga_solution_cores(ctx, u, None, 0, ctypes.byref(modes), ctypes.byref(ranks)))
+    m, r = list(modes), list(ranks)
+    sizes = [r[k] * m[k] * r[k + 1] for k in range(3)]
+    tot = sum(sizes)
+    if out is None:
+        out = np.zeros(tot)
+    _check(ctx, _lib.tt_iga_solution_cores(ctx, u, out.ctypes.data_as(_c_double_p), out.size, ctypes.byref(modes),
+                                           ctypes.byref(ranks)))
+    cores, off = [], 0
+    for k in range(3):
+        cores.append(out[off:off + sizes[k]].reshape(r[k], m[k], r[k + 1]))
+        off += sizes[k]
+    return cores
+
+
+def tt_iga_geometry(ctx, desc, allow_not_converged=False):
+    h = ctypes.c_void_p()
+    allow = (ERR_NOT_CONVERGED,) if allow_not_converged else ()
+    code = _lib.tt_iga_geometry(ctx, ctypes.byref(desc), ctypes.byref(h))
+    if code != OK and h.value:
+        if code not in allow:
+            msg = tt_iga_last_error(ctx)
+            _lib.tt_iga_geom_destroy(h)
+            raise TTIgaError(code, msg)
+    else:
+        _check(ctx, code, allow)
+    return h
+
+
+def tt_iga_geom_destroy(g):
+    _lib.tt_iga_geom_destroy(g)
+
+
+def tt_iga_geom_ranks(g):
+    ranks = (ctypes.c_int * 2 * 6)()
+    err = (ctypes.c_double * 6)()
+    _check(None, _lib.tt_iga_geom_ranks(g, ctypes.byref(ranks), ctypes.byref(err)))
+    return [(ranks[f][0], ranks[f][1]) for f in range(6)], list(err)
+
+
+def tt_iga_assemble(ctx, g, rhs_list, round_tol=1e-12):
+    arr = (RhsDesc * len(rhs_list))(*rhs_list)
+    h = ctypes.c_void_p()
+    _check(ctx, _lib.tt_iga_assemble(ctx, g, arr, len(rhs_list), round_tol, ctypes.byref(h)))
+    return h
+
+
+def tt_iga_system_destroy(s):
+    _lib.tt_iga_system_destroy(s)
+
+
+def tt_iga_system_info(s, n_rhs_max=8):
+    op = (ctypes.c_int * 2)()
+    rr = (ctypes.c_int * 2 * n_rhs_max)()
+    modes = (ctypes.c_int * 3)()
+    cnt = _lib.tt_iga_system_info(s, ctypes.byref(op), n_rhs_max, ctypes.cast(rr, ctypes.c_void_p), ctypes.byref(modes))
+    if cnt < 0:
+        raise TTIgaError(cnt, "system_info")
+    return {"op_ranks": (op[0], op[1]), "rhs_ranks": [(rr[k][0], rr[k][1]) for k in range(min(cnt, n_rhs_max))],
+            "modes": (modes[0], modes[1], modes[2]), "n_rhs": cnt}
+
+
+def tt_iga_solve(ctx, s, opts, allow_not_converged=False):
+    h = ctypes.c_void_p()
+    st = Stats()
+    allow = (ERR_NOT_CONVERGED,) if allow_not_converged else ()
+    code = _lib.tt_iga_solve(ctx, s, ctypes.byref(opts), ctypes.byref(h), ctypes.byref(st))
+    if code != OK and code not in allow:
+        msg = tt_iga_last_error(ctx)
+        if h.value:
+            _lib.tt_iga_solution_destroy(h)
+        raise TTIgaError(code, msg)
+    return h, st.as_dict()
+
+
+def tt_iga_solution_destroy(u):
+    _lib.tt_iga_solution_destroy(u)
+
+
+def tt_iga_solution_ranks(u):
+    r = (ctypes.c_int * 2)()
+    _check(None, _lib.tt_iga_solution_ranks(u, ctypes.byref(r)))
+    return r[0], r[1]
+
+
+def tt_iga_residual(ctx, s, u, k=0):
+    v = ctypes.c_double()
+    _check(ctx, _lib.tt_iga_residual(ctx, s, u, k, ctypes.byref(v)))
+    return v.value
+
+
+def tt_iga_eval(ctx, u, xi, out):
+    """u_h at parametric points xi (torch float64 CUDA tensor [m, 3]) into out (float64 CUDA [m])."""
+    _check(ctx, _lib.tt_iga_eval(ctx, u, int(xi.shape[0]), _ptr(xi), _ptr(out)))
+    return out
+
+
+def tt_iga_l2_error(ctx, g, u, rhs):
+    v = ctypes.c_double()
+    _check(ctx, _lib.tt_iga_l2_error(ctx, g, u, ctypes.byref(rhs), ctypes.byref(v)))
+    return v.value
+
+
+def _host_buffer(n):
+    import numpy as np
+    a = np.zeros(n, dtype=np.float64)
+    return a, a.ctypes.data_as(_c_double_p)
+
+
+def tt_iga_densify_operator(ctx, s):
+    import numpy as np
+    m = tt_iga_system_info(s)["modes"]
+    N = m[0] * m[1] * m[2]
+    a, p = _host_buffer(N * N)
+    _check(ctx, _lib.tt_iga_densify_operator(ctx, s, p, N * N))
+    return a.reshape(N, N)
+
+
+def tt_iga_densify_rhs(ctx, s, k=0):
+    m = tt_iga_system_info(s)["modes"]
+    N = m[0] * m[1] * m[2]
+    a, p = _host_buffer(N)
+    _check(ctx, _lib.tt_iga_densify_rhs(ctx, s, k, p, N))
+    return a
+
+
+def tt_iga_densify_solution(ctx, u, modes):
+    N = modes[0] * modes[1] * modes[2]
+    a, p = _host_buffer(N)
+    _check(ctx, _lib.tt_iga_densify_solution(ctx, u, p, N))
+    return a
+
+
+def tt_iga_operator_entries(ctx, s, rows, cols):
+    import numpy as np
+    rows = np.ascontiguousarray(rows, dtype=np.int32)
+    cols = np.ascontiguousarray(cols, dtype=np.int32)
+    out = np.zeros(len(rows))
+    _check(ctx, _lib.tt_iga_operator_entries(ctx, s, len(rows), rows.ctypes.data_as(_c_int_p),
+                                             cols.ctypes.data_as(_c_int_p), out.ctypes.data_as(_c_double_p)))
+    return out
+
+
+def tt_iga_vector_entries(ctx, s, u, k, idx):
+    import numpy as np
+    idx = np.ascontiguousarray(idx, dtype=np.int32)
+    out = np.zeros(len(idx))
+    _check(ctx, _lib.tt_iga_vector_entries(ctx, s, u, k, len(idx), idx.ctypes.data_as(_c_int_p),
+                                           out.ctypes.data_as(_c_double_p)))
+    return out
+
+
+def tt_iga_basis_tables(ctx, n, p, nq, pts, wts, N, dN):
+    _check(ctx, _lib.tt_iga_basis_tables(ctx, n, p, nq, _ptr(pts), _ptr(wts), _ptr(N), _ptr(dN)))
+
+
+def tt_iga_geom_points(ctx, g, rhs, idx, out):
+    bad = ctypes.c_longlong()
+    _check(ctx, _lib.tt_iga_geom_points(ctx, g, ctypes.byref(rhs) if rhs is not None else None, int(idx.shape[0]),
+                                        _ptr(idx), _ptr(out), ctypes.byref(bad)))
+    return bad.value
+
+
+def tt_iga_stiffness_core(ctx, n, p, nq, wts, N, dN, G, r0, r1, test_deriv, trial_deriv, M):
+    _check(ctx, _lib.tt_iga_stiffness_core(ctx, n, p, nq, _ptr(wts), _ptr(N), _ptr(dN), _ptr(G), r0, r1,
+                                           int(test_deriv), int(trial_deriv), _ptr(M)))
+
+
+def tt_iga_load_core(ctx, n, p, nq, wts, N, G, r0, r1, F):
+    _check(ctx, _lib.tt_iga_load_core(ctx, n, p, nq, _ptr(wts), _ptr(N), _ptr(G), r0, r1, _ptr(F)))
+
+
+def tt_iga_round(ctx, cores, eps, max_rank=0):
+    """Round a TT given as three float64 CUDA tensors [r0, m, r1]; returns (cores, ranks)."""
+    import torch
+    nm = (ctypes.c_int * 3)(*[int(G.shape[1]) for G in cores])
+    r = (ctypes.c_int * 4)(1, int(cores[0].shape[2]), int(cores[1].shape[2]), 1)
+    cin = (ctypes.c_void_p * 3)(*[G.data_ptr() for G in cores])
+    outs = [torch.empty_like(G) for G in cores]
+    cout = (ctypes.c_void_p * 3)(*[t.data_ptr() for t in outs])
+    rout = (ctypes.c_int * 4)()
+    _check(ctx, _lib.tt_iga_round(ctx, ctypes.byref(nm), ctypes.byref(r), ctypes.byref(cin), eps, max_rank,
+                                  ctypes.byref(cout), ctypes.byref(rout)))
+    res = []
+    for k in range(3):
+        cnt = rout[k] * nm[k] * rout[k + 1]
+        res.append(outs[k].reshape(-1)[:cnt].reshape(rout[k], nm[k], rout[k + 1]))
+    return res, [rout[k] for k in range(4)]
+
+
+def tt_iga_qr(ctx, A, Q, R):
+    m, k = int(A.shape[0]), int(A.shape[1])
+    _check(ctx, _lib.tt_iga_qr(ctx, m, k, _ptr(A), int(A.stride(0)), _ptr(Q), _ptr(R)))
+
+
+def tt_iga_svd_small(ctx, A, U, s, V):
+    _check(ctx, _lib.tt_iga_svd_small(ctx, int(A.shape[0]), _ptr(A), _ptr(U), _ptr(s), _ptr(V)))
+
+
+def tt_iga_maxvol(ctx, U, rows, B, delta=1e-2, maxit=100):
+    _check(ctx, _lib.tt_iga_maxvol(ctx, int(U.shape[0]), int(U.shape[1]), _ptr(U), delta, maxit, _ptr(rows), _ptr(B)))

@@ -1,0 +1,511 @@
+// AMEn TT linear solver for the SPD system K u = F (Section 4.1.2).
+//
+// The paper solves with TT-Toolbox's amen_solve: one TT core of u is updated
+// at a time by minimising the residual over it, and an enrichment step with a
+// low-rank approximation of the residual controls rank growth.  This is a GPU
+// implementation of that scheme (Dolgov and Savostyanov 2014) for d = 3:
+//
+//   forward sweep k = 1, 2, 3:
+//     local system  B_k = PhiL_k (x) A_k (x) PhiR_k, rhs_k = PsiL_k F_k PsiR_k
+//     local solve   PCG with a band block-Jacobi preconditioner (FP64), or
+//                   FP32 PCG inside FP64 iterative refinement (mixed)
+//     truncation    QR + SVD of the (r_{k-1} n_k) x r_k solution, smallest rank
+//                   whose local residual stays below the truncation tolerance
+//     enrichment    append the residual projected onto the right interface of
+//                   a rank-rho residual approximation z, re-orthogonalise (QR)
+//     z update      core k of z = residual projected on z's own interfaces
+//     interfaces    left interfaces of u and z for core k + 1
+//   backward pass: right-orthogonalise cores 3, 2 of u and z, refresh the
+//   right interfaces.
+//   stop:  exact ||F - K u|| / ||F|| <= tol (TT arithmetic with QR
+//   orthogonalisation) when the residual's rank allows it, otherwise the
+//   largest relative local residual of the sweep.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+
+#include "amen.cuh"
+#include "amen_ops.cuh"
+#include "linalg.cuh"
+#include "tt.cuh"
+
+namespace ttiga {
+
+namespace {
+
+struct SplitMix64 {
+  uint64_t s;
+  uint64_t next() {
+    uint64_t z = (s += 0x9E3779B97F4A7C15ULL);
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+    return z ^ (z >> 31);
+  }
+  double uniform() { return (next() >> 11) * (1.0 / 9007199254740992.0) * 2.0 - 1.0; }
+};
+
+void random_tt(Ctx *c, TT3 &x, const int m[3], int r1, int r2, uint64_t seed) {
+  SplitMix64 rng{seed};
+  for (int k = 0; k < 3; ++k) x.m[k] = m[k];
+  x.r[0] = 1; x.r[1] = r1; x.r[2] = r2; x.r[3] = 1;
+  x.alloc(c);
+  for (int k = 0; k < 3; ++k) {
+    std::vector<double> h(x.core_elems(k));
+    for (auto &v : h) v = rng.uniform();
+    c->h2d(x.core[k].get(), h.data(), h.size() * sizeof(double));
+  }
+}
+
+DBuf ones(Ctx *c) {
+  DBuf d(c, sizeof(double));
+  const double one = 1.0;
+  c->h2d(d.get(), &one, sizeof one);
+  return d;
+}
+
+__global__ void k_sub(const double *a, double *b, long long n) {  // b = a - b
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    b[i] = a[i] - b[i];
+}
+
+template <typename T>
+__global__ void k_pcg_xr(T *x, T *r, const T *p, const T *q, const double *rz, const double *pq, long long n) {
+  const double alpha = (*pq != 0.0) ? *rz / *pq : 0.0;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    x[i] += (T)alpha * p[i];
+    r[i] -= (T)alpha * q[i];
+  }
+}
+
+template <typename T>
+__global__ void k_pcg_p(T *p, const T *z, const double *rz_new, const double *rz_old, long long n) {
+  const double beta = (*rz_old != 0.0) ? *rz_new / *rz_old : 0.0;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    p[i] = z[i] + (T)beta * p[i];
+}
+
+// Deterministic dot product of FP32 or FP64 vectors accumulated in FP64.
+template <typename T>
+__global__ void k_dot_part(const T *x, const T *y, long long n, double *part) {
+  __shared__ double red[32];
+  double s = 0.0;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    s += (double)x[i] * (double)y[i];
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+    part[blockIdx.x] = t;
+  }
+}
+__global__ void k_dot_final(const double *part, int np, double *out) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    double t = 0.0;
+    for (int i = 0; i < np; ++i) t += part[i];
+    *out = t;
+  }
+}
+
+template <typename T> void dot_dev(Ctx *c, const T *x, const T *y, long long n, double *out, double *part) {
+  const int nb = (int)std::min<long long>(128, std::max<long long>(1, (n + 255) / 256));
+  k_dot_part<T><<<nb, 256, 0, c->stream>>>(x, y, n, part);
+  TTI_LAUNCH();
+  k_dot_final<<<1, 32, 0, c->stream>>>(part, nb, out);
+  TTI_LAUNCH();
+}
+
+}  // namespace
+
+struct Amen {
+  Ctx *c;
+  const tt_iga_system *S;
+  const TT3 &F;
+  double Fnorm;
+  tt_iga_solve_opts o;
+  TT3 u, z;
+  BandCore A[3];
+  DBuf A32[3];
+  int R[4], f[4];
+  DBuf PhiL[3], PhiR[3], PsiL[3], PsiR[3], PhiLz[3], PhiRz[3], PsiLz[3], PsiRz[3];
+  Work<double> w64;
+  Work<float> w32;
+  tt_iga_stats st{};
+  double last_local = 0.0;
+  // scratch scalars on the device: [0] rz, [1] pq, [2] rz_new, [8..] partials
+  DBuf scal;
+
+  Amen(Ctx *c_, const tt_iga_system *s, const tt_iga_solve_opts &opts)
+      : c(c_), S(s), F(s->F[opts.rhs_index]), Fnorm(s->F_norm[opts.rhs_index]), o(opts), w64{c_}, w32{c_} {
+    for (int k = 0; k < 4; ++k) { R[k] = S->K.r[k]; f[k] = F.r[k]; }
+    for (int k = 0; k < 3; ++k) {
+      A[k].A = S->K.core[k].d();
+      A[k].A32 = nullptr;
+      A[k].Rl = R[k]; A[k].Rr = R[k + 1];
+      A[k].n = S->n[k]; A[k].b = S->b; A[k].p = S->p;
+    }
+    scal = DBuf(c, 256 * sizeof(double));
+    if (o.precision != TT_IGA_FP64) {
+      for (int k = 0; k < 3; ++k) {
+        const long long ne = (long long)S->K.core_elems(k);
+        A32[k] = DBuf(c, ne * sizeof(float));
+        convert_f64_to_f32(c, A[k].A, A32[k].as<float>(), ne);
+        A[k].A32 = A32[k].as<float>();
+      }
+    }
+  }
+
+  int rl(int k) const { return u.r[k]; }
+  int rr(int k) const { return u.r[k + 1]; }
+  int n(int k) const { return S->n[k]; }
+
+  void right_interfaces(int k) {  // from core k (1 or 2) into index k-1
+    PhiR[k - 1] = DBuf(c, (size_t)u.r[k] * R[k] * u.r[k] * sizeof(double));
+    right_update(c, w64, u.core[k].d(), u.r[k], u.r[k + 1], A[k], PhiR[k].d(), u.core[k].d(), u.r[k], u.r[k + 1],
+                 PhiR[k - 1].d());
+    PsiR[k - 1] = DBuf(c, (size_t)u.r[k] * f[k] * sizeof(double));
+    rhs_right_update(c, w64, u.core[k].d(), u.r[k], u.r[k + 1], F.core[k].d(), f[k], n(k), f[k + 1], PsiR[k].d(),
+                     PsiR[k - 1].d());
+    PhiRz[k - 1] = DBuf(c, (size_t)z.r[k] * R[k] * u.r[k] * sizeof(double));
+    right_update(c, w64, z.core[k].d(), z.r[k], z.r[k + 1], A[k], PhiRz[k].d(), u.core[k].d(), u.r[k], u.r[k + 1],
+                 PhiRz[k - 1].d());
+    PsiRz[k - 1] = DBuf(c, (size_t)z.r[k] * f[k] * sizeof(double));
+    rhs_right_update(c, w64, z.core[k].d(), z.r[k], z.r[k + 1], F.core[k].d(), f[k], n(k), f[k + 1], PsiRz[k].d(),
+                     PsiRz[k - 1].d());
+  }
+
+  void left_interfaces(int k) {  // from core k (0 or 1) into index k+1
+    PhiL[k + 1] = DBuf(c, (size_t)u.r[k + 1] * R[k + 1] * u.r[k + 1] * sizeof(double));
+    left_update(c, w64, u.core[k].d(), u.r[k], u.r[k + 1], PhiL[k].d(), A[k], u.core[k].d(), u.r[k], u.r[k + 1],
+                PhiL[k + 1].d());
+    PsiL[k + 1] = DBuf(c, (size_t)u.r[k + 1] * f[k + 1] * sizeof(double));
+    rhs_left_update(c, w64, u.core[k].d(), u.r[k], u.r[k + 1], PsiL[k].d(), F.core[k].d(), f[k], n(k), f[k + 1],
+                    PsiL[k + 1].d());
+    PhiLz[k + 1] = DBuf(c, (size_t)z.r[k + 1] * R[k + 1] * u.r[k + 1] * sizeof(double));
+    left_update(c, w64, z.core[k].d(), z.r[k], z.r[k + 1], PhiLz[k].d(), A[k], u.core[k].d(), u.r[k], u.r[k + 1],
+                PhiLz[k + 1].d());
+    PsiLz[k + 1] = DBuf(c, (size_t)z.r[k + 1] * f[k + 1] * sizeof(double));
+    rhs_left_update(c, w64, z.core[k].d(), z.r[k], z.r[k + 1], PsiLz[k].d(), F.core[k].d(), f[k], n(k), f[k + 1],
+                    PsiLz[k + 1].d());
+  }
+
+  void init() {
+    const int m[3] = {n(0), n(1), n(2)};
+    const int r0 = std::max(1, std::min(2, std::min(m[0], m[2])));
+    random_tt(c, u, m, r0, r0, 0x5EED5EEDULL + 31 * o.rhs_index);
+    tt_orth_rl(c, u);
+    const int rho = std::max(0, o.kickrank);
+    if (rho > 0) {
+      const int zr = std::min(rho, std::min(m[0], m[2]));
+      random_tt(c, z, m, zr, zr, 0xC0FFEEULL + 17 * o.rhs_index);
+      tt_orth_rl(c, z);
+    } else {
+      random_tt(c, z, m, 1, 1, 0xC0FFEEULL);
+    }
+    PhiL[0] = ones(c); PsiL[0] = ones(c); PhiLz[0] = ones(c); PsiLz[0] = ones(c);
+    PhiR[2] = ones(c); PsiR[2] = ones(c); PhiRz[2] = ones(c); PsiRz[2] = ones(c);
+    right_interfaces(2);
+    right_interfaces(1);
+  }
+
+  // B x for core k in FP64
+  void matvec64(int k, const double *x, double *y) {
+    apply_local<double>(c, w64, PhiL[k].d(), rl(k), rl(k), A[k], A[k].A, PhiR[k].d(), rr(k), rr(k), x, y);
+    st.local_matvecs++;
+    st.local_matvecs_fp64++;
+  }
+
+  // Local residual r = rhs - B x, returns ||r||.
+  double residual64(int k, const double *rhs, const double *x, double *r) {
+    const long long N = (long long)rl(k) * n(k) * rr(k);
+    matvec64(k, x, r);
+    k_sub<<<grid1d(N, 256), 256, 0, c->stream>>>(rhs, r, N);
+    TTI_LAUNCH();
+    return host_nrm2(c, r, N);
+  }
+
+  // PCG on B d = r (type T), d starts at zero.  Absolute tolerance tol on ||r - B d||.
+  template <typename T>
+  int pcg(int k, const T *PhiLk, const T *PhiRk, const T *Ak, const T *L, const T *b, T *x, double tol, int maxit) {
+    const long long N = (long long)rl(k) * n(k) * rr(k);
+    Work<T> &w = work((T *)nullptr);
+    DBuf rb(c, N * sizeof(T)), zb(c, N * sizeof(T)), pb(c, N * sizeof(T)), qb(c, N * sizeof(T));
+    T *r = rb.as<T>(), *zz = zb.as<T>(), *p = pb.as<T>(), *q = qb.as<T>();
+    double *sc = scal.d();
+    double *part = sc + 16;
+    TTI_CUDA(cudaMemcpyAsync(r, b, N * sizeof(T), cudaMemcpyDeviceToDevice, c->stream));
+    c->zero(x, N * sizeof(T));
+    precond_apply<T>(c, L, rl(k), n(k), S->p, rr(k), r, zz);
+    TTI_CUDA(cudaMemcpyAsync(p, zz, N * sizeof(T), cudaMemcpyDeviceToDevice, c->stream));
+    dot_dev<T>(c, r, zz, N, sc + 0, part);
+    int it = 0;
+    for (; it < maxit; ++it) {
+      apply_local<T>(c, w, PhiLk, rl(k), rl(k), A[k], Ak, PhiRk, rr(k), rr(k), p, q);
+      st.local_matvecs++;
+      if (sizeof(T) == 8) st.local_matvecs_fp64++;
+      dot_dev<T>(c, p, q, N, sc + 1, part);
+      k_pcg_xr<T><<<grid1d(N, 256), 256, 0, c->stream>>>(x, r, p, q, sc + 0, sc + 1, N);
+      TTI_LAUNCH();
+      if ((it % 4) == 3 || it == maxit - 1) {
+        dot_dev<T>(c, r, r, N, sc + 3, part);
+        double rr2;
+        c->d2h(&rr2, sc + 3, sizeof rr2);
+        if (sqrt(std::max(rr2, 0.0)) <= tol) { ++it; break; }
+      }
+      precond_apply<T>(c, L, rl(k), n(k), S->p, rr(k), r, zz);
+      dot_dev<T>(c, r, zz, N, sc + 2, part);
+      k_pcg_p<T><<<grid1d(N, 256), 256, 0, c->stream>>>(p, zz, sc + 2, sc + 0, N);
+      TTI_LAUNCH();
+      TTI_CUDA(cudaMemcpyAsync(sc + 0, sc + 2, sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
+    }
+    return it;
+  }
+
+  Work<double> &work(double *) { return w64; }
+  Work<float> &work(float *) { return w32; }
+
+  // Solve the local system of core k for x (in/out).  Returns the residual before the solve.
+  double local_solve(int k, const double *rhs, double *x, double tol_abs) {
+    const long long N = (long long)rl(k) * n(k) * rr(k);
+    DBuf rbuf(c, N * sizeof(double));
+    const double res0 = residual64(k, rhs, x, rbuf.d());
+    if (res0 <= tol_abs) return res0;
+    const int maxit = o.local_maxit;
+    const size_t Lsz = (size_t)n(k) * (S->p + 1) * rl(k) * rr(k);
+    if (o.precision == TT_IGA_FP64) {
+      DBuf L(c, Lsz * sizeof(double)), d(c, N * sizeof(double));
+      precond_build<double>(c, PhiL[k].d(), rl(k), A[k], PhiR[k].d(), rr(k), L.d());
+      // correction form: B d = r, x += d, checked in FP64
+      for (int rep = 0; rep < 3; ++rep) {
+        pcg<double>(k, PhiL[k].d(), PhiR[k].d(), A[k].A, L.d(), rbuf.d(), d.d(), 0.5 * tol_abs, maxit);
+        axpy<double>(c, N, 1.0, d.d(), x);
+        if (residual64(k, rhs, x, rbuf.d()) <= tol_abs) break;
+      }
+    } else {
+      // FP32 PCG on the correction inside FP64 iterative refinement.
+      DBuf L(c, Lsz * sizeof(float)), d32(c, N * sizeof(float)), r32(c, N * sizeof(float)), d64(c, N * sizeof(double));
+      precond_build<float>(c, PhiL[k].d(), rl(k), A[k], PhiR[k].d(), rr(k), L.as<float>());
+      const long long nl = (long long)rl(k) * R[k] * rl(k), nr = (long long)rr(k) * R[k + 1] * rr(k);
+      DBuf pl(c, nl * sizeof(float)), pr(c, nr * sizeof(float));
+      convert_f64_to_f32(c, PhiL[k].d(), pl.as<float>(), nl);
+      convert_f64_to_f32(c, PhiR[k].d(), pr.as<float>(), nr);
+      double res = res0;
+      for (int rep = 0; rep < 12 && res > tol_abs; ++rep) {
+        // scale the residual to unit norm so FP32 keeps its relative precision
+        convert_f64_to_f32(c, rbuf.d(), r32.as<float>(), N);
+        scale<float>(c, r32.as<float>(), N, (float)(1.0 / res));
+        pcg<float>(k, pl.as<float>(), pr.as<float>(), A[k].A32, L.as<float>(), r32.as<float>(), d32.as<float>(),
+                   std::max(1e-5, 0.5 * tol_abs / res), maxit);
+        convert_f32_to_f64(c, d32.as<float>(), d64.d(), N);
+        axpy<double>(c, N, res, d64.d(), x);
+        res = residual64(k, rhs, x, rbuf.d());
+      }
+    }
+    return res0;
+  }
+
+  // Truncate the solution x of core k (k < 2) and enrich; updates u cores k, k+1.
+  void truncate_enrich(int k, const double *rhs, const double *x, double tol_trunc) {
+    const int a = rl(k), nk = n(k), b = rr(k);
+    const int rows = a * nk;
+    DBuf Q(c, (size_t)rows * b * sizeof(double)), Rm(c, (size_t)b * b * sizeof(double));
+    qr(c, rows, b, x, b, Q.d(), Rm.d());
+    DBuf Ur(c, (size_t)b * b * sizeof(double)), Sv(c, (size_t)b * sizeof(double)), V(c, (size_t)b * b * sizeof(double));
+    svd_small(c, b, Rm.d(), Ur.d(), Sv.d(), V.d());
+    std::vector<double> s(b);
+    c->d2h(s.data(), Sv.d(), b * sizeof(double));
+    // SVt[j][l] = s_j V[l][j]
+    DBuf SVt(c, (size_t)b * b * sizeof(double));
+    {
+      std::vector<double> hv(b * b), h(b * b);
+      c->d2h(hv.data(), V.d(), hv.size() * sizeof(double));
+      for (int j = 0; j < b; ++j)
+        for (int l = 0; l < b; ++l) h[j * b + l] = s[j] * hv[l * b + j];
+      c->h2d(SVt.d(), h.data(), h.size() * sizeof(double));
+    }
+    DBuf QU(c, (size_t)rows * b * sizeof(double));
+    gemm<double>(c, false, false, rows, b, b, 1.0, Q.d(), b, 0, Ur.d(), b, 0, 0.0, QU.d(), b, 0, 1);
+    // numerical rank
+    int rmax = b;
+    while (rmax > 1 && s[rmax - 1] <= 1e-15 * s[0]) --rmax;
+    const long long N = (long long)rows * b;
+    DBuf xt(c, N * sizeof(double)), rt(c, N * sizeof(double));
+    auto res_at = [&](int r) {
+      gemm<double>(c, false, false, rows, b, r, 1.0, QU.d(), b, 0, SVt.d(), b, 0, 0.0, xt.d(), b, 0, 1);
+      return residual64(k, rhs, xt.d(), rt.d());
+    };
+    int lo = 1, hi = rmax;
+    if (res_at(hi) > tol_trunc) {
+      lo = hi;  // cannot meet the tolerance: keep everything
+    } else {
+      while (lo < hi) {
+        const int mid = (lo + hi) / 2;
+        if (res_at(mid) <= tol_trunc) hi = mid; else lo = mid + 1;
+      }
+    }
+    int r = lo;
+    if (o.max_rank > 0) r = std::min(r, o.max_rank);
+    // a rank above the product of the remaining mode sizes only adds null directions
+    const long long right_cap = (k == 0) ? (long long)n(1) * n(2) : (long long)n(2);
+    r = (int)std::min<long long>(r, right_cap);
+    // truncated solution xt = QU[:, :r] SVt[:r]
+    gemm<double>(c, false, false, rows, b, r, 1.0, QU.d(), b, 0, SVt.d(), b, 0, 0.0, xt.d(), b, 0, 1);
+    // enrichment from the residual projected on z's right interface
+    int rho = (o.kickrank > 0) ? z.r[k + 1] : 0;
+    rho = std::min(rho, std::max(0, rows - r));
+    rho = (int)std::min<long long>(rho, std::max<long long>(0, right_cap - r));
+    if (o.max_rank > 0) rho = std::min(rho, std::max(0, o.max_rank - r));
+    const int rn = r + rho;
+    DBuf Ue(c, (size_t)rows * rn * sizeof(double));
+    copy2d(c, Ue.d(), rn, QU.d(), b, rows, r);
+    if (rho > 0) {
+      const int zr = z.r[k + 1];
+      DBuf ez(c, (size_t)rows * zr * sizeof(double)), bz(c, (size_t)rows * zr * sizeof(double));
+      rhs_local(c, w64, PsiL[k].d(), a, F.core[k].d(), f[k], nk, f[k + 1], PsiRz[k].d(), zr, ez.d());
+      apply_local<double>(c, w64, PhiL[k].d(), a, a, A[k], A[k].A, PhiRz[k].d(), zr, b, xt.d(), bz.d());
+      k_sub<<<grid1d((long long)rows * zr, 256), 256, 0, c->stream>>>(ez.d(), bz.d(), (long long)rows * zr);
+      TTI_LAUNCH();
+      copy2d(c, Ue.d() + r, rn, bz.d(), zr, rows, rho);
+    }
+    DBuf Qe(c, (size_t)rows * rn * sizeof(double)), Re(c, (size_t)rn * rn * sizeof(double));
+    qr(c, rows, rn, Ue.d(), rn, Qe.d(), Re.d());
+    // C = Re[:, :r] SVt[:r]  -> rn x b ; next core <- C * core_{k+1}
+    DBuf C(c, (size_t)rn * b * sizeof(double));
+    gemm<double>(c, false, false, rn, b, r, 1.0, Re.d(), rn, 0, SVt.d(), b, 0, 0.0, C.d(), b, 0, 1);
+    const long long cols = (long long)n(k + 1) * u.r[k + 2];
+    DBuf next(c, (size_t)rn * cols * sizeof(double));
+    gemm<double>(c, false, false, rn, (int)cols, b, 1.0, C.d(), b, 0, u.core[k + 1].d(), cols, 0, 0.0, next.d(), cols,
+                 0, 1);
+    // z core k: residual of xt projected on z's interfaces
+    if (o.kickrank > 0) {
+      const int zl = z.r[k], zr = z.r[k + 1];
+      DBuf zk(c, (size_t)zl * nk * zr * sizeof(double)), bz(c, (size_t)zl * nk * zr * sizeof(double));
+      rhs_local(c, w64, PsiLz[k].d(), zl, F.core[k].d(), f[k], nk, f[k + 1], PsiRz[k].d(), zr, zk.d());
+      apply_local<double>(c, w64, PhiLz[k].d(), zl, a, A[k], A[k].A, PhiRz[k].d(), zr, b, xt.d(), bz.d());
+      k_sub<<<grid1d((long long)zl * nk * zr, 256), 256, 0, c->stream>>>(zk.d(), bz.d(), (long long)zl * nk * zr);
+      TTI_LAUNCH();
+      DBuf Zq(c, (size_t)zl * nk * zr * sizeof(double)), Zr(c, (size_t)zr * zr * sizeof(double));
+      qr(c, zl * nk, zr, bz.d(), zr, Zq.d(), Zr.d());
+      z.core[k] = std::move(Zq);
+    }
+    u.core[k] = std::move(Qe);
+    u.core[k + 1] = std::move(next);
+    u.r[k + 1] = rn;
+  }
+
+  void last_core_z(const double *x) {
+    if (o.kickrank <= 0) return;
+    const int k = 2, zl = z.r[2], nk = n(2);
+    DBuf zk(c, (size_t)zl * nk * sizeof(double)), bz(c, (size_t)zl * nk * sizeof(double));
+    rhs_local(c, w64, PsiLz[k].d(), zl, F.core[k].d(), f[k], nk, 1, PsiRz[k].d(), 1, zk.d());
+    apply_local<double>(c, w64, PhiLz[k].d(), zl, rl(k), A[k], A[k].A, PhiRz[k].d(), 1, 1, x, bz.d());
+    k_sub<<<grid1d((long long)zl * nk, 256), 256, 0, c->stream>>>(zk.d(), bz.d(), (long long)zl * nk);
+    TTI_LAUNCH();
+    z.core[2] = std::move(bz);
+  }
+
+  double exact_residual() {
+    // W = F - K u with cores [F_k | (K u)_k] in block form; ||W|| by orthogonalisation.
+    TT3 Ku;
+    for (int k = 0; k < 3; ++k) Ku.m[k] = n(k);
+    for (int k = 0; k < 4; ++k) Ku.r[k] = R[k] * u.r[k];
+    if (Ku.r[1] + f[1] > 256 || Ku.r[2] + f[2] > 256) return -1.0;
+    Ku.alloc(c);
+    for (int k = 0; k < 3; ++k) tt_matvec_core(c, A[k], u.core[k].d(), u.r[k], u.r[k + 1], Ku.core[k].d());
+    TT3 W;
+    tt_sum(c, F, 1.0, Ku, -1.0, W);
+    return tt_norm(c, W) / Fnorm;
+  }
+
+  int run(tt_iga_solution *out) {
+    init();
+    const double tol_abs = o.tol * Fnorm;
+    const double tol_solve = 0.1 * tol_abs / sqrt(3.0);
+    const double tol_trunc = 0.3 * tol_abs / sqrt(3.0);
+    int status = TT_IGA_ERR_NOT_CONVERGED;
+    for (int sweep = 0; sweep < o.max_sweeps; ++sweep) {
+      double maxloc = 0.0;
+      for (int k = 0; k < 3; ++k) {
+        const long long N = (long long)rl(k) * n(k) * rr(k);
+        DBuf rhs(c, N * sizeof(double)), x(c, N * sizeof(double));
+        rhs_local(c, w64, PsiL[k].d(), rl(k), F.core[k].d(), f[k], n(k), f[k + 1], PsiR[k].d(), rr(k), rhs.d());
+        TTI_CUDA(cudaMemcpyAsync(x.d(), u.core[k].d(), N * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
+        const double r0 = local_solve(k, rhs.d(), x.d(), tol_solve);
+        maxloc = std::max(maxloc, r0 / Fnorm);
+        if (k < 2) {
+          truncate_enrich(k, rhs.d(), x.d(), tol_trunc);
+          left_interfaces(k);
+        } else {
+          u.core[2] = std::move(x);
+          last_core_z(u.core[2].d());
+        }
+      }
+      // backward orthogonalisation of u and z, refresh right interfaces
+      for (int k = 2; k >= 1; --k) {
+        orth_right_step(c, u, k);
+        if (o.kickrank > 0) orth_right_step(c, z, k);
+        right_interfaces(k);
+      }
+      st.sweeps = sweep + 1;
+      last_local = maxloc;
+      const double res = exact_residual();
+      st.rel_residual = res;
+      st.local_residual = maxloc;
+      if (o.verbose)
+        fprintf(stderr, "[tt_iga amen] sweep %d ranks %d %d local %.3e residual %.3e matvecs %lld\n", sweep + 1,
+                u.r[1], u.r[2], maxloc, res, st.local_matvecs);
+      if ((res >= 0.0 && res <= o.tol) || (res < 0.0 && maxloc <= o.tol)) {
+        status = TT_IGA_OK;
+        break;
+      }
+    }
+    st.ranks[0] = u.r[1];
+    st.ranks[1] = u.r[2];
+    st.converged = status == TT_IGA_OK;
+    out->ctx = c;
+    for (int k = 0; k < 3; ++k) out->n[k] = n(k);
+    out->p = S->p;
+    out->u = std::move(u);
+    return status;
+  }
+};
+
+
+int amen_solve(Ctx *c, const tt_iga_system *s, const tt_iga_solve_opts &o, tt_iga_solution *out, tt_iga_stats *st) {
+  cudaEvent_t e0, e1;
+  TTI_CUDA(cudaEventCreate(&e0));
+  TTI_CUDA(cudaEventCreate(&e1));
+  TTI_CUDA(cudaEventRecord(e0, c->stream));
+  Amen a(c, s, o);
+  int status = a.run(out);
+  TTI_CUDA(cudaEventRecord(e1, c->stream));
+  TTI_CUDA(cudaEventSynchronize(e1));
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  a.st.ms_total = ms;
+  if (st) *st = a.st;
+  return status;
+}
+
+double exact_residual(Ctx *c, const tt_iga_system *s, const tt_iga_solution *sol, int k) {
+  // Same construction as Amen::exact_residual, without the rank cap.
+  const TT3 &F = s->F[k];
+  TT3 Ku;
+  for (int d = 0; d < 3; ++d) Ku.m[d] = s->n[d];
+  for (int d = 0; d < 4; ++d) Ku.r[d] = s->K.r[d] * sol->u.r[d];
+  TTI_CHECK_ARG(Ku.r[1] + F.r[1] <= 256 && Ku.r[2] + F.r[2] <= 256, "residual: TT rank %d/%d above 256",
+                Ku.r[1] + F.r[1], Ku.r[2] + F.r[2]);
+  Ku.alloc(c);
+  for (int d = 0; d < 3; ++d) {
+    BandCore A{s->K.core[d].d(), nullptr, s->K.r[d], s->n[d], s->b, s->p, s->K.r[d + 1]};
+    tt_matvec_core(c, A, sol->u.core[d].d(), sol->u.r[d], sol->u.r[d + 1], Ku.core[d].d());
+  }
+  TT3 W;
+  tt_sum(c, F, 1.0, Ku, -1.0, W);
+  return tt_norm(c, W) / s->F_norm[k];
+}
+
+}  // namespace ttiga

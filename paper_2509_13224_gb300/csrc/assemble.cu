@@ -1,0 +1,226 @@
+// TT-IGA assembly on the device (Sections 4.2.1, 4.2.2, 4.3).
+//
+// Per-direction quadrature contraction: for a coefficient core G[r0][Q][r1]
+//   M[alpha][i][o][beta] = sum_q w_q G[alpha][q][beta] A_i(q) B_{i+o-p}(q)
+// where (A, B) are (N', N'), (N, N), (N', N) or (N, N') by the a_ij^(d)
+// selector.  Basis functions i and j = i+o-p overlap only on the elements
+// max(i, j) - p .. min(i, j), so each band output sums at most (p+1) nq terms.
+// One thread per band output, consecutive threads on consecutive beta so
+// reads of G and writes of M are coalesced along the rank.
+#include <algorithm>
+#include <cmath>
+
+#include "handles.cuh"
+#include "linalg.cuh"
+#include "tt.cuh"
+
+namespace ttiga {
+
+__global__ void k_stiffness_core(int n, int p, int nq, const double *__restrict__ wts, const double *__restrict__ TA,
+                                 const double *__restrict__ TB, const double *__restrict__ G, int r0, int r1,
+                                 double *__restrict__ M) {
+  const int b = 2 * p + 1, ne = n - p, Q = ne * nq, P = p + 1;
+  const long long tot = (long long)r0 * n * b * r1;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < tot; e += (long long)gridDim.x * blockDim.x) {
+    const int beta = (int)(e % r1);
+    long long t = e / r1;
+    const int o = (int)(t % b);
+    t /= b;
+    const int i = (int)(t % n);
+    const int alpha = (int)(t / n);
+    const int j = i + o - p;
+    double acc = 0.0;
+    if (j >= 0 && j < n) {
+      const int elo = max(max(i, j) - p, 0), ehi = min(min(i, j), ne - 1);
+      for (int el = elo; el <= ehi; ++el) {
+        for (int l = 0; l < nq; ++l) {
+          const int q = el * nq + l;
+          acc += wts[q] * G[((long long)alpha * Q + q) * r1 + beta] * TA[(long long)q * P + (i - el)] *
+                 TB[(long long)q * P + (j - el)];
+        }
+      }
+    }
+    M[e] = acc;
+  }
+}
+
+__global__ void k_load_core(int n, int p, int nq, const double *__restrict__ wts, const double *__restrict__ TN,
+                            const double *__restrict__ G, int r0, int r1, double *__restrict__ F) {
+  const int ne = n - p, Q = ne * nq, P = p + 1;
+  const long long tot = (long long)r0 * n * r1;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < tot; e += (long long)gridDim.x * blockDim.x) {
+    const int beta = (int)(e % r1);
+    const long long t = e / r1;
+    const int i = (int)(t % n);
+    const int alpha = (int)(t / n);
+    const int elo = max(i - p, 0), ehi = min(i, ne - 1);
+    double acc = 0.0;
+    for (int el = elo; el <= ehi; ++el)
+      for (int l = 0; l < nq; ++l) {
+        const int q = el * nq + l;
+        acc += wts[q] * G[((long long)alpha * Q + q) * r1 + beta] * TN[(long long)q * P + (i - el)];
+      }
+    F[e] = acc;
+  }
+}
+
+void stiffness_core(Ctx *c, int n, int p, int nq, const double *wts, const double *N, const double *dN, const double *G,
+                    int r0, int r1, int test_deriv, int trial_deriv, double *M) {
+  TTI_CHECK_ARG(n > p && p >= 1 && nq >= 1 && r0 >= 1 && r1 >= 1, "stiffness_core: bad sizes");
+  const long long tot = (long long)r0 * n * (2 * p + 1) * r1;
+  k_stiffness_core<<<grid1d(tot, 256, 152 * 32), 256, 0, c->stream>>>(n, p, nq, wts, test_deriv ? dN : N,
+                                                                     trial_deriv ? dN : N, G, r0, r1, M);
+  TTI_LAUNCH();
+}
+
+void load_core(Ctx *c, int n, int p, int nq, const double *wts, const double *N, const double *G, int r0, int r1,
+               double *F) {
+  TTI_CHECK_ARG(n > p && p >= 1 && nq >= 1 && r0 >= 1 && r1 >= 1, "load_core: bad sizes");
+  const long long tot = (long long)r0 * n * r1;
+  k_load_core<<<grid1d(tot, 256, 152 * 32), 256, 0, c->stream>>>(n, p, nq, wts, N, G, r0, r1, F);
+  TTI_LAUNCH();
+}
+
+// Drop basis functions 0 and n-1 (homogeneous Dirichlet, Section 4.3):
+// band core [r0][n][b][r1] -> [r0][n-2][b][r1], zeroing couplings to the dropped functions.
+__global__ void k_restrict_band(const double *src, double *dst, int r0, int n, int p, int r1) {
+  const int b = 2 * p + 1, nr = n - 2;
+  const long long tot = (long long)r0 * nr * b * r1;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < tot; e += (long long)gridDim.x * blockDim.x) {
+    const int beta = (int)(e % r1);
+    long long t = e / r1;
+    const int o = (int)(t % b);
+    t /= b;
+    const int ir = (int)(t % nr);
+    const int alpha = (int)(t / nr);
+    const int jr = ir + o - p;
+    dst[e] = (jr >= 0 && jr < nr) ? src[(((long long)alpha * n + ir + 1) * b + o) * r1 + beta] : 0.0;
+  }
+}
+
+__global__ void k_restrict_vec(const double *src, double *dst, int r0, int n, int r1) {
+  const int nr = n - 2;
+  const long long tot = (long long)r0 * nr * r1;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < tot; e += (long long)gridDim.x * blockDim.x) {
+    const int beta = (int)(e % r1);
+    const long long t = e / r1;
+    const int ir = (int)(t % nr), alpha = (int)(t / nr);
+    dst[e] = src[((long long)alpha * n + ir + 1) * r1 + beta];
+  }
+}
+
+static void restrict_tt(Ctx *c, TT3 &x, const int n[3], int p, bool band) {
+  for (int k = 0; k < 3; ++k) {
+    const int r0 = x.r[k], r1 = x.r[k + 1];
+    const int nr = n[k] - 2;
+    const int bw = band ? 2 * p + 1 : 1;
+    DBuf out(c, (size_t)r0 * nr * bw * r1 * sizeof(double));
+    const long long tot = (long long)r0 * nr * bw * r1;
+    if (band)
+      k_restrict_band<<<grid1d(tot, 256), 256, 0, c->stream>>>(x.core[k].d(), out.d(), r0, n[k], p, r1);
+    else
+      k_restrict_vec<<<grid1d(tot, 256), 256, 0, c->stream>>>(x.core[k].d(), out.d(), r0, n[k], r1);
+    TTI_LAUNCH();
+    x.core[k] = std::move(out);
+    x.m[k] = nr * bw;
+  }
+}
+
+void assemble_system(Ctx *c, const tt_iga_geom *g, const tt_iga_rhs_desc *rhs, int n_rhs, double round_tol,
+                     tt_iga_system *out) {
+  const int p = g->desc.p;
+  const int b = 2 * p + 1;
+  int n[3];
+  for (int d = 0; d < 3; ++d) n[d] = g->s[d].n;
+  TT3 K;
+  bool have = false;
+  static const int pairs[6][2] = {{0, 0}, {1, 1}, {2, 2}, {0, 1}, {0, 2}, {1, 2}};
+  for (auto &pr : pairs) {
+    const int i = pr[0], j = pr[1];
+    const CrossResult &R = g->R[field_of(i, j)];
+    if (R.zero) continue;
+    const int nterms = (i == j) ? 1 : 2;
+    for (int t = 0; t < nterms; ++t) {
+      const int a = t == 0 ? i : j, bb = t == 0 ? j : i;  // K_ab: derivative on test index in direction a
+      TT3 T;
+      for (int d = 0; d < 3; ++d) T.m[d] = n[d] * b;
+      for (int k = 0; k < 4; ++k) T.r[k] = R.tt.r[k];
+      T.alloc(c);
+      for (int d = 0; d < 3; ++d)
+        stiffness_core(c, n[d], p, g->s[d].nq, g->s[d].wts.d(), g->s[d].N.d(), g->s[d].dN.d(), R.tt.core[d].d(),
+                       R.tt.r[d], R.tt.r[d + 1], d == a, d == bb, T.core[d].d());
+      if (!have) {
+        K = std::move(T);
+        have = true;
+      } else {
+        TT3 S;
+        tt_sum(c, K, 1.0, T, 1.0, S);
+        tt_round(c, S, round_tol, 0);
+        K = std::move(S);
+      }
+    }
+  }
+  TTI_CHECK_ARG(have, "assemble: every coefficient field vanished");
+  restrict_tt(c, K, n, p, true);
+  tt_round(c, K, round_tol, 0);
+  out->ctx = c;
+  out->p = p;
+  out->b = b;
+  for (int d = 0; d < 3; ++d) out->n[d] = n[d] - 2;
+  out->K = std::move(K);
+  out->F.clear();
+  out->F_norm.clear();
+  for (int k = 0; k < n_rhs; ++k) {
+    RhsParams rp = rhs_params(&rhs[k]);
+    CrossResult fj;
+    cross3(c, g->s, g->gp, rp, 7, g->desc.cross_tol, g->desc.max_rank, g->desc.seed + 7919ULL * (k + 1), 0.0, fj);
+    TT3 F;
+    for (int d = 0; d < 3; ++d) F.m[d] = n[d];
+    if (fj.zero) {
+      F.r[1] = F.r[2] = 1;
+      F.alloc(c);
+      for (int d = 0; d < 3; ++d) c->zero(F.core[d].get(), F.core_elems(d) * sizeof(double));
+    } else {
+      for (int q = 0; q < 4; ++q) F.r[q] = fj.tt.r[q];
+      F.alloc(c);
+      for (int d = 0; d < 3; ++d)
+        load_core(c, n[d], p, g->s[d].nq, g->s[d].wts.d(), g->s[d].N.d(), fj.tt.core[d].d(), fj.tt.r[d],
+                  fj.tt.r[d + 1], F.core[d].d());
+    }
+    restrict_tt(c, F, n, p, false);
+    double nrm = tt_round(c, F, round_tol, 0);
+    out->F.push_back(std::move(F));
+    out->F_norm.push_back(nrm);
+  }
+}
+
+// K(row, col) of the restricted band TT operator at index pairs.
+__global__ void k_op_entries(const double *M1, const double *M2, const double *M3, int n1, int n2, int n3, int p,
+                             int r1, int r2, int m, const int *rows, const int *cols, double *out) {
+  const int b = 2 * p + 1;
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < m; t += gridDim.x * blockDim.x) {
+    const int i1 = rows[3 * t], i2 = rows[3 * t + 1], i3 = rows[3 * t + 2];
+    const int o1 = cols[3 * t] - i1 + p, o2 = cols[3 * t + 1] - i2 + p, o3 = cols[3 * t + 2] - i3 + p;
+    double v = 0.0;
+    if (o1 >= 0 && o1 < b && o2 >= 0 && o2 < b && o3 >= 0 && o3 < b) {
+      for (int a = 0; a < r1; ++a) {
+        const double x = M1[((long long)i1 * b + o1) * r1 + a];
+        if (x == 0.0) continue;
+        double s = 0.0;
+        for (int c2 = 0; c2 < r2; ++c2)
+          s += M2[(((long long)a * n2 + i2) * b + o2) * r2 + c2] * M3[((long long)c2 * n3 + i3) * b + o3];
+        v += x * s;
+      }
+    }
+    out[t] = v;
+  }
+}
+
+void operator_entries(Ctx *c, const tt_iga_system *s, int m, const int *rows, const int *cols, double *out) {
+  if (m <= 0) return;
+  k_op_entries<<<grid1d(m, 128), 128, 0, c->stream>>>(s->K.core[0].d(), s->K.core[1].d(), s->K.core[2].d(), s->n[0],
+                                                       s->n[1], s->n[2], s->p, s->K.r[1], s->K.r[2], m, rows, cols, out);
+  TTI_LAUNCH();
+}
+
+}  // namespace ttiga

@@ -1,0 +1,254 @@
+// Device functions of the geometry evaluator shared by the table, cross,
+// evaluation and error kernels (Sections 2.1 and 3.3, Eq. Rxi).
+#pragma once
+#include "geom.cuh"
+
+namespace ttiga {
+
+// ------------------------------------------------------------------ tables
+
+__device__ inline double knot_at(int i, int n, int p) {
+  const int ne = n - p;
+  if (i <= p) return 0.0;
+  if (i >= n) return 1.0;
+  return (double)(i - p) / (double)ne;
+}
+
+// Gauss-Legendre nodes/weights on [-1, 1] by Golub-Welsch (single thread, m <= 8).
+__device__ inline void golub_welsch(int m, double *x, double *w) {
+  double A[8][8], V[8][8];
+  for (int i = 0; i < m; ++i)
+    for (int j = 0; j < m; ++j) {
+      A[i][j] = 0.0;
+      V[i][j] = (i == j) ? 1.0 : 0.0;
+    }
+  for (int k = 1; k < m; ++k) {
+    const double b = k / sqrt(4.0 * k * k - 1.0);
+    A[k - 1][k] = A[k][k - 1] = b;
+  }
+  for (int sweep = 0; sweep < 100; ++sweep) {
+    double off = 0.0;
+    for (int i = 0; i < m; ++i)
+      for (int j = i + 1; j < m; ++j) off += A[i][j] * A[i][j];
+    if (off < 1e-34) break;
+    for (int pp = 0; pp < m; ++pp)
+      for (int q = pp + 1; q < m; ++q) {
+        if (A[pp][q] == 0.0) continue;
+        const double theta = (A[q][q] - A[pp][pp]) / (2.0 * A[pp][q]);
+        const double t = copysign(1.0, theta) / (fabs(theta) + sqrt(theta * theta + 1.0));
+        const double c = 1.0 / sqrt(t * t + 1.0), s = t * c;
+        for (int k = 0; k < m; ++k) {  // A <- A G
+          const double akp = A[k][pp], akq = A[k][q];
+          A[k][pp] = c * akp - s * akq;
+          A[k][q] = s * akp + c * akq;
+        }
+        for (int k = 0; k < m; ++k) {  // A <- G^T A
+          const double apk = A[pp][k], aqk = A[q][k];
+          A[pp][k] = c * apk - s * aqk;
+          A[q][k] = s * apk + c * aqk;
+        }
+        for (int k = 0; k < m; ++k) {
+          const double vkp = V[k][pp], vkq = V[k][q];
+          V[k][pp] = c * vkp - s * vkq;
+          V[k][q] = s * vkp + c * vkq;
+        }
+      }
+  }
+  // sort ascending
+  int idx[8];
+  for (int i = 0; i < m; ++i) idx[i] = i;
+  for (int i = 1; i < m; ++i) {
+    int v = idx[i], j = i - 1;
+    while (j >= 0 && A[idx[j]][idx[j]] > A[v][v]) { idx[j + 1] = idx[j]; --j; }
+    idx[j + 1] = v;
+  }
+  for (int i = 0; i < m; ++i) {
+    x[i] = A[idx[i]][idx[i]];
+    const double v0 = V[0][idx[i]];
+    w[i] = 2.0 * v0 * v0;
+  }
+}
+
+// Nonzero basis values N[0..p] (functions s-p..s) and derivatives at x in knot span s.
+__device__ inline void local_basis(double x, int s, int n, int p, double *N, double *D) {
+  double left[9], right[9], Np[9];
+  N[0] = 1.0;
+  for (int j = 1; j <= p; ++j) {
+    left[j] = x - knot_at(s + 1 - j, n, p);
+    right[j] = knot_at(s + j, n, p) - x;
+    if (j == p)
+      for (int r = 0; r < p; ++r) Np[r] = N[r];  // degree p-1 values
+    double saved = 0.0;
+    for (int r = 0; r < j; ++r) {
+      const double tmp = N[r] / (right[r + 1] + left[j - r]);
+      N[r] = saved + right[r + 1] * tmp;
+      saved = left[j - r] * tmp;
+    }
+    N[j] = saved;
+  }
+  if (p == 0) {
+    D[0] = 0.0;
+    return;
+  }
+  // dN_i = p N_i^{p-1}/(xi_{i+p} - xi_i) - p N_{i+1}^{p-1}/(xi_{i+p+1} - xi_{i+1}), i = s-p+j;
+  // the degree p-1 functions nonzero in span s are s-p+1..s, held in Np[0..p-1].
+  for (int j = 0; j <= p; ++j) {
+    const int i = s - p + j;
+    double v = 0.0;
+    if (j >= 1) {
+      const double den = knot_at(i + p, n, p) - knot_at(i, n, p);
+      if (den > 0.0) v += p * Np[j - 1] / den;
+    }
+    if (j <= p - 1) {
+      const double den = knot_at(i + p + 1, n, p) - knot_at(i + 1, n, p);
+      if (den > 0.0) v -= p * Np[j] / den;
+    }
+    D[j] = v;
+  }
+}
+
+// ----------------------------------------------------------- hyper-duals
+
+struct HDual {
+  double a, b, c, d;  // value, e1, e2, e1e2
+};
+__device__ __forceinline__ HDual hd(double a) { return {a, 0.0, 0.0, 0.0}; }
+__device__ __forceinline__ HDual operator+(HDual x, HDual y) { return {x.a + y.a, x.b + y.b, x.c + y.c, x.d + y.d}; }
+__device__ __forceinline__ HDual operator-(HDual x, HDual y) { return {x.a - y.a, x.b - y.b, x.c - y.c, x.d - y.d}; }
+__device__ __forceinline__ HDual operator*(HDual x, HDual y) {
+  return {x.a * y.a, x.a * y.b + x.b * y.a, x.a * y.c + x.c * y.a, x.a * y.d + x.b * y.c + x.c * y.b + x.d * y.a};
+}
+__device__ __forceinline__ HDual operator*(double s, HDual x) { return {s * x.a, s * x.b, s * x.c, s * x.d}; }
+__device__ __forceinline__ HDual operator+(double s, HDual x) { return {s + x.a, x.b, x.c, x.d}; }
+__device__ __forceinline__ HDual chain(HDual x, double f0, double f1, double f2) {
+  return {f0, f1 * x.b, f1 * x.c, f1 * x.d + f2 * x.b * x.c};
+}
+__device__ __forceinline__ HDual hsin(HDual x) {
+  double s, c;
+  sincos(x.a, &s, &c);
+  return chain(x, s, c, -s);
+}
+__device__ __forceinline__ HDual hcos(HDual x) {
+  double s, c;
+  sincos(x.a, &s, &c);
+  return chain(x, c, -s, -c);
+}
+__device__ __forceinline__ HDual hrecip(HDual x) {
+  const double r = 1.0 / x.a;
+  return chain(x, r, -r * r, 2.0 * r * r * r);
+}
+
+// Manufactured solution at physical point (x, y, z) (hyper-dual arguments).
+__device__ inline HDual manufactured_u(const GeomParams &g, const RhsParams &f, HDual x, HDual y, HDual z) {
+  const double PI = 3.141592653589793238462643383279502884;
+  HDual bubble;
+  if (g.kind == TT_IGA_GEOM_ANNULUS) {
+    const HDual zeta = (1.0 / g.height) * z;
+    const HDual phi = g.twist * zeta;
+    const HDual inv_s = hrecip(1.0 + g.swell * hsin(PI * zeta));
+    const HDual cp = hcos(phi), sp = hsin(phi);
+    const HDual xp = (cp * x + sp * y) * inv_s;
+    const HDual yp = (cp * y - sp * x) * inv_s;
+    const HDual rho2 = xp * xp + yp * yp;
+    bubble = (rho2 - hd(g.r_in * g.r_in)) * (hd(g.r_out * g.r_out) - rho2) * xp * yp * zeta * (hd(1.0) - zeta);
+  } else {
+    bubble = hsin((PI / g.lx) * x) * hsin((PI / g.ly) * y) * hsin((PI / g.lz) * z);
+  }
+  HDual mod = hd(1.0);
+  for (int k = 0; k < f.n_modes; ++k)
+    mod = mod + f.a[k] * hsin(f.b[k][0] * x + f.b[k][1] * y + f.b[k][2] * z + hd(f.c[k]));
+  return bubble * mod;
+}
+
+__device__ inline double manufactured_value(const GeomParams &g, const RhsParams &f, double x, double y, double z) {
+  return manufactured_u(g, f, hd(x), hd(y), hd(z)).a;
+}
+
+__device__ inline double source_term(const GeomParams &g, const RhsParams &f, double x, double y, double z) {
+  if (!f.has) return 0.0;
+  if (f.kind == TT_IGA_RHS_CONSTANT) return f.value;
+  double lap = 0.0;
+  const double X[3] = {x, y, z};
+  for (int k = 0; k < 3; ++k) {
+    HDual a[3];
+    for (int j = 0; j < 3; ++j) a[j] = (j == k) ? HDual{X[j], 1.0, 1.0, 0.0} : hd(X[j]);
+    lap += manufactured_u(g, f, a[0], a[1], a[2]).d;
+  }
+  return -lap;
+}
+
+// Physical point and Jacobian J[a][b] = dx_a/dxi_b of the map at parametric xi.
+__device__ inline void map_point(const GeomParams &g, double x1, double x2, double x3, double X[3], double J[3][3]) {
+  if (g.kind == TT_IGA_GEOM_BOX) {
+    X[0] = g.lx * x1; X[1] = g.ly * x2; X[2] = g.lz * x3;
+    for (int a = 0; a < 3; ++a)
+      for (int b = 0; b < 3; ++b) J[a][b] = 0.0;
+    J[0][0] = g.lx; J[1][1] = g.ly; J[2][2] = g.lz;
+    return;
+  }
+  const double PI = 3.141592653589793238462643383279502884;
+  // radial degree-1 B-spline
+  const double r = g.r_in * (1.0 - x1) + g.r_out * x1, dr = g.r_out - g.r_in;
+  // quarter arc: rational quadratic with control (1,0), (1,1), (0,1), weights 1, sqrt(2)/2, 1
+  const double w1 = 0.70710678118654752440;
+  const double t = x2, u = 1.0 - t;
+  const double B0 = u * u, B1 = 2.0 * t * u, B2 = t * t;
+  const double dB0 = -2.0 * u, dB1 = 2.0 * (u - t), dB2 = 2.0 * t;
+  const double W = B0 + w1 * B1 + B2, dW = dB0 + w1 * dB1 + dB2;
+  const double nx = B0 + w1 * B1, ny = w1 * B1 + B2;
+  const double dnx = dB0 + w1 * dB1, dny = w1 * dB1 + dB2;
+  const double cx = nx / W, cy = ny / W;
+  const double dcx = (dnx * W - nx * dW) / (W * W), dcy = (dny * W - ny * dW) / (W * W);
+  // axial degree-1 B-spline
+  const double z = g.height * x3, dz = g.height;
+  const double zeta = z / g.height;
+  const double phi = g.twist * zeta, dphi = g.twist / g.height;
+  double sz, cz;
+  sincos(PI * zeta, &sz, &cz);
+  const double s = 1.0 + g.swell * sz, ds = g.swell * PI * cz / g.height;
+  double sp, cp;
+  sincos(phi, &sp, &cp);
+  const double x0 = r * cx, y0 = r * cy;
+  X[0] = s * (cp * x0 - sp * y0);
+  X[1] = s * (sp * x0 + cp * y0);
+  X[2] = z;
+  const double ax[2] = {dr * cx, r * dcx}, ay[2] = {dr * cy, r * dcy};
+  for (int b = 0; b < 2; ++b) {
+    J[0][b] = s * (cp * ax[b] - sp * ay[b]);
+    J[1][b] = s * (sp * ax[b] + cp * ay[b]);
+    J[2][b] = 0.0;
+  }
+  J[0][2] = dz * (ds * (cp * x0 - sp * y0) + s * dphi * (-sp * x0 - cp * y0));
+  J[1][2] = dz * (ds * (sp * x0 + cp * y0) + s * dphi * (cp * x0 - sp * y0));
+  J[2][2] = dz;
+}
+
+// R = det J J^{-1} J^{-T}: with A = adj(J) = det J J^{-1}, R = A A^T / det J.
+__device__ inline void point_outputs(const GeomParams &g, const RhsParams &f, double x1, double x2, double x3, double *o,
+                              int *bad) {
+  double X[3], J[3][3];
+  map_point(g, x1, x2, x3, X, J);
+  double A[3][3];
+  A[0][0] = J[1][1] * J[2][2] - J[1][2] * J[2][1];
+  A[0][1] = J[0][2] * J[2][1] - J[0][1] * J[2][2];
+  A[0][2] = J[0][1] * J[1][2] - J[0][2] * J[1][1];
+  A[1][0] = J[1][2] * J[2][0] - J[1][0] * J[2][2];
+  A[1][1] = J[0][0] * J[2][2] - J[0][2] * J[2][0];
+  A[1][2] = J[0][2] * J[1][0] - J[0][0] * J[1][2];
+  A[2][0] = J[1][0] * J[2][1] - J[1][1] * J[2][0];
+  A[2][1] = J[0][1] * J[2][0] - J[0][0] * J[2][1];
+  A[2][2] = J[0][0] * J[1][1] - J[0][1] * J[1][0];
+  const double det = J[0][0] * A[0][0] + J[0][1] * A[1][0] + J[0][2] * A[2][0];
+  if (!(det > 0.0)) *bad = 1;
+  const double inv = 1.0 / det;
+  double R[3][3];
+  for (int a = 0; a < 3; ++a)
+    for (int b = a; b < 3; ++b) R[a][b] = (A[a][0] * A[b][0] + A[a][1] * A[b][1] + A[a][2] * A[b][2]) * inv;
+  o[0] = R[0][0]; o[1] = R[0][1]; o[2] = R[0][2];
+  o[3] = R[1][1]; o[4] = R[1][2]; o[5] = R[2][2];
+  o[6] = det;
+  o[7] = f.has ? source_term(g, f, X[0], X[1], X[2]) * det : 0.0;
+}
+
+
+}  // namespace ttiga

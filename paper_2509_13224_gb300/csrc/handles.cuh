@@ -1,0 +1,53 @@
+// Library-owned objects behind the opaque C handles.
+#pragma once
+#include "cross.cuh"
+#include "geom.cuh"
+
+// Geometry: discretisation of each direction and the TT cores of the six
+// unique entries of R (order R11, R12, R13, R22, R23, R33).
+struct tt_iga_geom {
+  ttiga::Ctx *ctx = nullptr;
+  tt_iga_geom_desc desc{};
+  ttiga::GeomParams gp{};
+  ttiga::Space s[3];
+  ttiga::CrossResult R[6];
+  double ms_cross = 0.0;
+};
+
+// Restricted TT system: band-stored operator with mode sizes (n_d - 2)(2p+1)
+// and one TT load vector per right-hand side with mode sizes n_d - 2.
+struct tt_iga_system {
+  ttiga::Ctx *ctx = nullptr;
+  int n[3] = {0, 0, 0};   // restricted sizes n_d - 2
+  int p = 0, b = 0;       // degree and band width 2p + 1
+  ttiga::TT3 K;
+  std::vector<ttiga::TT3> F;
+  std::vector<double> F_norm;
+};
+
+struct tt_iga_solution {
+  ttiga::Ctx *ctx = nullptr;
+  int n[3] = {0, 0, 0};   // restricted sizes
+  int p = 0;
+  ttiga::TT3 u;
+};
+
+namespace ttiga {
+
+// Output index of field (i, j), i <= j, in the R array.
+inline int field_of(int i, int j) {
+  if (i > j) { int t = i; i = j; j = t; }
+  static const int map[3][3] = {{0, 1, 2}, {1, 3, 4}, {2, 4, 5}};
+  return map[i][j];
+}
+
+void stiffness_core(Ctx *c, int n, int p, int nq, const double *wts, const double *N, const double *dN,
+                    const double *G, int r0, int r1, int test_deriv, int trial_deriv, double *M);
+void load_core(Ctx *c, int n, int p, int nq, const double *wts, const double *N, const double *G, int r0, int r1,
+               double *F);
+void assemble_system(Ctx *c, const tt_iga_geom *g, const tt_iga_rhs_desc *rhs, int n_rhs, double round_tol,
+                     tt_iga_system *out);
+// Dense restricted operator entries for (row, col) multi-index pairs (device arrays).
+void operator_entries(Ctx *c, const tt_iga_system *s, int m, const int *rows, const int *cols, double *out);
+
+}  // namespace ttiga

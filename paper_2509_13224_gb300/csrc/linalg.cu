@@ -1,0 +1,731 @@
+// Dense linear algebra kernels (FP64 unless templated): GEMM, deterministic
+// reductions, tall-skinny Householder QR (TSQR tree), one-sided Jacobi SVD and
+// maximum-volume row selection.  All sizes on this path are small to moderate
+// (ranks <= 256); GB300's FP64 pipe (about 1.2 TFLOP/s, measured) bounds
+// these kernels, so they keep FP64 work at its algorithmic minimum.
+#include <algorithm>
+#include <cfloat>
+
+#include "linalg.cuh"
+
+namespace ttiga {
+
+// ------------------------------------------------------------------ helpers
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Sum over the block (deterministic order); result returned to every thread.
+__device__ double block_sum(double v, double *red) {
+  int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+  v = warp_sum(v);
+  __syncthreads();
+  if (lane == 0) red[warp] = v;
+  __syncthreads();
+  double t = 0.0;
+  for (int w = 0; w < nw; ++w) t += red[w];
+  return t;
+}
+
+// ------------------------------------------------------------------- GEMM
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_gemm(bool ta, bool tb, int m, int n, int k, T alpha,
+                                              const T *__restrict__ A, long long lda, long long sA,
+                                              const T *__restrict__ B, long long ldb, long long sB,
+                                              T beta, T *__restrict__ C, long long ldc, long long sC) {
+  constexpr int BM = 64, BN = 64, BK = 16;
+  __shared__ T As[BK][BM + 1];
+  __shared__ T Bs[BK][BN + 1];
+  const long long b = blockIdx.z;
+  A += b * sA;
+  B += b * sB;
+  C += b * sC;
+  const int i0 = blockIdx.y * BM, j0 = blockIdx.x * BN;
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  T acc[4][4];
+#pragma unroll
+  for (int x = 0; x < 4; ++x)
+#pragma unroll
+    for (int y = 0; y < 4; ++y) acc[x][y] = T(0);
+  for (int l0 = 0; l0 < k; l0 += BK) {
+    for (int e = threadIdx.x; e < BM * BK; e += 256) {
+      int ii, ll;
+      if (!ta) { ii = e / BK; ll = e % BK; } else { ll = e / BM; ii = e % BM; }
+      const int gi = i0 + ii, gl = l0 + ll;
+      T v = T(0);
+      if (gi < m && gl < k) v = ta ? A[(long long)gl * lda + gi] : A[(long long)gi * lda + gl];
+      As[ll][ii] = v;
+    }
+    for (int e = threadIdx.x; e < BK * BN; e += 256) {
+      int ll, jj;
+      if (!tb) { ll = e / BN; jj = e % BN; } else { jj = e / BK; ll = e % BK; }
+      const int gl = l0 + ll, gj = j0 + jj;
+      T v = T(0);
+      if (gl < k && gj < n) v = tb ? B[(long long)gj * ldb + gl] : B[(long long)gl * ldb + gj];
+      Bs[ll][jj] = v;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int ll = 0; ll < BK; ++ll) {
+      T av[4], bv[4];
+#pragma unroll
+      for (int x = 0; x < 4; ++x) av[x] = As[ll][ty + 16 * x];
+#pragma unroll
+      for (int y = 0; y < 4; ++y) bv[y] = Bs[ll][tx + 16 * y];
+#pragma unroll
+      for (int x = 0; x < 4; ++x)
+#pragma unroll
+        for (int y = 0; y < 4; ++y) acc[x][y] = fma(av[x], bv[y], acc[x][y]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int x = 0; x < 4; ++x) {
+    const int gi = i0 + ty + 16 * x;
+    if (gi >= m) continue;
+#pragma unroll
+    for (int y = 0; y < 4; ++y) {
+      const int gj = j0 + tx + 16 * y;
+      if (gj >= n) continue;
+      T *cp = C + (long long)gi * ldc + gj;
+      *cp = (beta == T(0)) ? alpha * acc[x][y] : alpha * acc[x][y] + beta * (*cp);
+    }
+  }
+}
+
+template <typename T>
+__global__ void k_scale_mat(T *C, int m, int n, long long ldc, long long sC, T beta) {
+  const long long b = blockIdx.y;
+  T *Cb = C + b * sC;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < (long long)m * n;
+       e += (long long)gridDim.x * blockDim.x) {
+    T *cp = Cb + (e / n) * ldc + (e % n);
+    *cp = (beta == T(0)) ? T(0) : beta * (*cp);
+  }
+}
+
+template <typename T>
+void gemm(Ctx *c, bool ta, bool tb, int m, int n, int k, T alpha, const T *A, long long lda,
+          long long sA, const T *B, long long ldb, long long sB, T beta, T *C, long long ldc,
+          long long sC, int batch) {
+  if (m <= 0 || n <= 0 || batch <= 0) return;
+  if (k <= 0) {
+    for (int b0 = 0; b0 < batch; b0 += 65535) {
+      int nb = std::min(65535, batch - b0);
+      k_scale_mat<T><<<dim3(grid1d((long long)m * n, 256, 1024), nb), 256, 0, c->stream>>>(
+          C + b0 * sC, m, n, ldc, sC, beta);
+      TTI_LAUNCH();
+    }
+    return;
+  }
+  for (int b0 = 0; b0 < batch; b0 += 65535) {
+    int nb = std::min(65535, batch - b0);
+    dim3 grid(cdiv(n, 64), cdiv(m, 64), nb);
+    TTI_CHECK_ARG(grid.y <= 65535, "gemm: m=%d too large", m);
+    ProfScope ps(c, sizeof(T) == 8 ? PROF_GEMM64 : PROF_OFF, 2.0 * m * (double)n * k * nb);
+    k_gemm<T><<<grid, 256, 0, c->stream>>>(ta, tb, m, n, k, alpha, A + b0 * sA, lda, sA, B + b0 * sB, ldb,
+                                            sB, beta, C + b0 * sC, ldc, sC);
+    TTI_LAUNCH();
+  }
+}
+
+template void gemm<double>(Ctx *, bool, bool, int, int, int, double, const double *, long long, long long,
+                           const double *, long long, long long, double, double *, long long, long long, int);
+template void gemm<float>(Ctx *, bool, bool, int, int, int, float, const float *, long long, long long,
+                          const float *, long long, long long, float, float *, long long, long long, int);
+
+// ------------------------------------------------------------- reductions
+
+constexpr int kRedBlocks = 256;
+
+__global__ void k_partial_dot(const double *x, const double *y, long long n, double *part) {
+  __shared__ double red[32];
+  double s = 0.0;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    s += x[i] * (y ? y[i] : x[i]);
+  s = block_sum(s, red);
+  if (threadIdx.x == 0) part[blockIdx.x] = s;
+}
+
+__global__ void k_final_sum(const double *part, int np, double *out) {
+  __shared__ double red[32];
+  double s = 0.0;
+  for (int i = threadIdx.x; i < np; i += blockDim.x) s += part[i];
+  s = block_sum(s, red);
+  if (threadIdx.x == 0) *out = s;
+}
+
+void dev_dot(Ctx *c, const double *x, const double *y, long long n, double *out) {
+  int nb = (int)std::min<long long>(kRedBlocks, std::max<long long>(1, (n + 255) / 256));
+  double *part = c->dscratch + 4096;
+  k_partial_dot<<<nb, 256, 0, c->stream>>>(x, y, n, part);
+  TTI_LAUNCH();
+  k_final_sum<<<1, 256, 0, c->stream>>>(part, nb, out);
+  TTI_LAUNCH();
+}
+void dev_sumsq(Ctx *c, const double *x, long long n, double *out) { dev_dot(c, x, nullptr, n, out); }
+
+double host_dot(Ctx *c, const double *x, const double *y, long long n) {
+  dev_dot(c, x, y, n, c->dscratch);
+  double v;
+  c->d2h(&v, c->dscratch, sizeof v);
+  return v;
+}
+double host_nrm2(Ctx *c, const double *x, long long n) { return sqrt(std::max(0.0, host_dot(c, x, x, n))); }
+
+// ------------------------------------------------------- elementwise helpers
+
+template <typename T>
+__global__ void k_scale(T *x, long long n, T a) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    x[i] *= a;
+}
+template <typename T>
+__global__ void k_axpy(long long n, T a, const T *x, T *y) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    y[i] += a * x[i];
+}
+template <typename T> void scale(Ctx *c, T *x, long long n, T a) {
+  if (n <= 0) return;
+  k_scale<T><<<grid1d(n, 256), 256, 0, c->stream>>>(x, n, a);
+  TTI_LAUNCH();
+}
+template <typename T> void axpy(Ctx *c, long long n, T a, const T *x, T *y) {
+  if (n <= 0) return;
+  k_axpy<T><<<grid1d(n, 256), 256, 0, c->stream>>>(n, a, x, y);
+  TTI_LAUNCH();
+}
+template void scale<double>(Ctx *, double *, long long, double);
+template void scale<float>(Ctx *, float *, long long, float);
+template void axpy<double>(Ctx *, long long, double, const double *, double *);
+template void axpy<float>(Ctx *, long long, float, const float *, float *);
+
+__global__ void k_d2f(const double *x, float *y, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    y[i] = (float)x[i];
+}
+__global__ void k_f2d(const float *x, double *y, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    y[i] = (double)x[i];
+}
+void convert_f64_to_f32(Ctx *c, const double *x, float *y, long long n) {
+  if (n <= 0) return;
+  k_d2f<<<grid1d(n, 256), 256, 0, c->stream>>>(x, y, n);
+  TTI_LAUNCH();
+}
+void convert_f32_to_f64(Ctx *c, const float *x, double *y, long long n) {
+  if (n <= 0) return;
+  k_f2d<<<grid1d(n, 256), 256, 0, c->stream>>>(x, y, n);
+  TTI_LAUNCH();
+}
+
+__global__ void k_copy2d(double *dst, long long ldd, const double *src, long long lds, int rows, int cols) {
+  long long tot = (long long)rows * cols;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < tot; e += (long long)gridDim.x * blockDim.x) {
+    long long i = e / cols, j = e % cols;
+    dst[i * ldd + j] = src[i * lds + j];
+  }
+}
+void copy2d(Ctx *c, double *dst, long long ldd, const double *src, long long lds, int rows, int cols) {
+  if ((long long)rows * cols <= 0) return;
+  k_copy2d<<<grid1d((long long)rows * cols, 256), 256, 0, c->stream>>>(dst, ldd, src, lds, rows, cols);
+  TTI_LAUNCH();
+}
+
+__global__ void k_permute3(const double *in, double *out, int d0, int d1, int d2, int p0, int p1, int p2) {
+  const int dims[3] = {d0, d1, d2};
+  const int od1 = dims[p1], od2 = dims[p2];
+  long long tot = (long long)d0 * d1 * d2;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < tot; e += (long long)gridDim.x * blockDim.x) {
+    long long o2 = e % od2, t = e / od2;
+    long long o1 = t % od1, o0 = t / od1;
+    long long src[3];
+    src[p0] = o0;
+    src[p1] = o1;
+    src[p2] = o2;
+    out[e] = in[(src[0] * d1 + src[1]) * d2 + src[2]];
+  }
+}
+void permute3(Ctx *c, const double *in, double *out, int d0, int d1, int d2, int p0, int p1, int p2) {
+  long long tot = (long long)d0 * d1 * d2;
+  if (tot <= 0) return;
+  k_permute3<<<grid1d(tot, 256), 256, 0, c->stream>>>(in, out, d0, d1, d2, p0, p1, p2);
+  TTI_LAUNCH();
+}
+
+// ------------------------------------------------------------ TSQR (FP64)
+//
+// Level-0 blocks of mb rows are copied into block-column-major workspaces and
+// factorised by Householder reflections, one CTA per block; the stacked k x k
+// R factors form the input of the next level until one block remains.  The
+// explicit Q is built top-down: each block applies its reflectors to the
+// k x k slice of the level above padded with zeros.
+
+__global__ void k_qr_load(const double *__restrict__ A, long long lda, long long rows, int k, int mb,
+                          double *__restrict__ W) {
+  const long long blk = blockIdx.x;
+  double *Wb = W + blk * (long long)mb * k;
+  for (int e = threadIdx.x; e < mb * k; e += blockDim.x) {
+    const int i = e / k, cc = e % k;
+    const long long gr = blk * mb + i;
+    Wb[(long long)cc * mb + i] = (gr < rows) ? A[gr * lda + cc] : 0.0;
+  }
+}
+
+__global__ void __launch_bounds__(256) k_qr_panel(double *__restrict__ W, int mb, int k, double *__restrict__ tau,
+                                                  double *__restrict__ Rout) {
+  __shared__ double red[32];
+  __shared__ double sh[3];
+  const long long blk = blockIdx.x;
+  double *Wb = W + blk * (long long)mb * k;
+  double *tb = tau + blk * k;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+  for (int j = 0; j < k; ++j) {
+    double *col = Wb + (long long)j * mb;
+    double s = 0.0;
+    for (int i = j + 1 + tid; i < mb; i += blockDim.x) s += col[i] * col[i];
+    s = block_sum(s, red);
+    if (tid == 0) {
+      const double x0 = (j < mb) ? col[j] : 0.0;
+      if (s == 0.0) {
+        sh[0] = 0.0; sh[1] = x0; sh[2] = 0.0;
+      } else {
+        const double beta = -copysign(sqrt(x0 * x0 + s), x0);
+        sh[0] = (beta - x0) / beta;
+        sh[1] = beta;
+        sh[2] = 1.0 / (x0 - beta);
+      }
+      tb[j] = sh[0];
+    }
+    __syncthreads();
+    const double tj = sh[0], sc = sh[2];
+    if (tj != 0.0)
+      for (int i = j + 1 + tid; i < mb; i += blockDim.x) col[i] *= sc;
+    __syncthreads();
+    if (tid == 0 && j < mb) col[j] = sh[1];
+    if (tj != 0.0) {
+      for (int cc = j + 1 + warp; cc < k; cc += nw) {
+        double *ccol = Wb + (long long)cc * mb;
+        double w = (lane == 0) ? ccol[j] : 0.0;
+        for (int i = j + 1 + lane; i < mb; i += 32) w += col[i] * ccol[i];
+        w = warp_sum(w) * tj;
+        if (lane == 0) ccol[j] -= w;
+        for (int i = j + 1 + lane; i < mb; i += 32) ccol[i] -= w * col[i];
+      }
+    }
+    __syncthreads();
+  }
+  for (int e = tid; e < k * k; e += blockDim.x) {
+    const int row = e / k, cc = e % k;
+    Rout[(blk * k + row) * k + cc] = (cc >= row && row < mb) ? Wb[(long long)cc * mb + row] : 0.0;
+  }
+}
+
+__global__ void __launch_bounds__(256) k_qr_formq(const double *__restrict__ W, const double *__restrict__ tau,
+                                                  int mb, int k, const double *__restrict__ Cin,
+                                                  double *__restrict__ Y, double *__restrict__ Out,
+                                                  long long out_rows) {
+  const long long blk = blockIdx.x;
+  const double *Wb = W + blk * (long long)mb * k;
+  const double *tb = tau + blk * k;
+  double *Yb = Y + blk * (long long)mb * k;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+  for (int e = tid; e < mb * k; e += blockDim.x) {
+    const int cc = e / mb, i = e % mb;
+    double v = 0.0;
+    if (i < k) v = Cin ? Cin[(blk * k + i) * k + cc] : (i == cc ? 1.0 : 0.0);
+    Yb[(long long)cc * mb + i] = v;
+  }
+  __syncthreads();
+  for (int j = k - 1; j >= 0; --j) {
+    const double tj = tb[j];
+    if (tj == 0.0) continue;
+    const double *v = Wb + (long long)j * mb;
+    for (int cc = warp; cc < k; cc += nw) {
+      double *yc = Yb + (long long)cc * mb;
+      double w = (lane == 0) ? yc[j] : 0.0;
+      for (int i = j + 1 + lane; i < mb; i += 32) w += v[i] * yc[i];
+      w = warp_sum(w) * tj;
+      if (lane == 0) yc[j] -= w;
+      for (int i = j + 1 + lane; i < mb; i += 32) yc[i] -= w * v[i];
+    }
+    __syncthreads();
+  }
+  for (int e = tid; e < mb * k; e += blockDim.x) {
+    const int i = e / k, cc = e % k;
+    const long long row = blk * mb + i;
+    if (row < out_rows) Out[row * k + cc] = Yb[(long long)cc * mb + i];
+  }
+}
+
+static int qr_block_rows(long long rows, int k) {
+  int mb = std::max(4 * k, 128);
+  mb = (mb + 31) / 32 * 32;
+  if (rows <= mb) {
+    long long r = std::max<long long>(rows, k);
+    mb = (int)((r + 31) / 32 * 32);
+  }
+  return mb;
+}
+
+void qr(Ctx *c, int m, int k, const double *A, long long lda, double *Q, double *R) {
+  TTI_CHECK_ARG(m >= 1 && k >= 1 && k <= 256, "qr: bad sizes m=%d k=%d", m, k);
+  struct Level {
+    long long rows;
+    int mb, nblk;
+    DBuf W, tau, Rs;
+  };
+  std::vector<Level> lv;
+  const double *src = A;
+  long long ld = lda, rows = m;
+  for (;;) {
+    Level L;
+    L.rows = rows;
+    L.mb = qr_block_rows(rows, k);
+    L.nblk = cdiv(rows, L.mb);
+    L.W = DBuf(c, (size_t)L.nblk * L.mb * k * sizeof(double));
+    L.tau = DBuf(c, (size_t)L.nblk * k * sizeof(double));
+    L.Rs = DBuf(c, (size_t)L.nblk * k * k * sizeof(double));
+    k_qr_load<<<L.nblk, 256, 0, c->stream>>>(src, ld, rows, k, L.mb, L.W.d());
+    TTI_LAUNCH();
+    {
+      ProfScope ps(c, PROF_QR, 2.0 * L.nblk * (double)L.mb * k * k);
+      k_qr_panel<<<L.nblk, 256, 0, c->stream>>>(L.W.d(), L.mb, k, L.tau.d(), L.Rs.d());
+      TTI_LAUNCH();
+    }
+    lv.push_back(std::move(L));
+    Level &top = lv.back();
+    if (top.nblk == 1) break;
+    src = top.Rs.d();
+    ld = k;
+    rows = (long long)top.nblk * k;
+  }
+  TTI_CUDA(cudaMemcpyAsync(R, lv.back().Rs.d(), (size_t)k * k * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
+  DBuf Cbuf;
+  const double *Cin = nullptr;
+  for (int L = (int)lv.size() - 1; L >= 0; --L) {
+    Level &l = lv[L];
+    DBuf Y(c, (size_t)l.nblk * l.mb * k * sizeof(double));
+    DBuf Out;
+    double *outp;
+    long long out_rows;
+    if (L == 0) {
+      outp = Q;
+      out_rows = m;
+    } else {
+      out_rows = lv[L - 1].rows > 0 ? (long long)lv[L - 1].nblk * k : 0;
+      Out = DBuf(c, (size_t)out_rows * k * sizeof(double));
+      outp = Out.d();
+    }
+    k_qr_formq<<<l.nblk, 256, 0, c->stream>>>(l.W.d(), l.tau.d(), l.mb, k, Cin, Y.d(), outp, out_rows);
+    TTI_LAUNCH();
+    Cbuf = std::move(Out);
+    Cin = Cbuf.d();
+  }
+}
+
+// ------------------------------------------------------- one-sided Jacobi SVD
+
+__global__ void __launch_bounds__(256) k_jacobi_svd(int k, const double *__restrict__ A, double *__restrict__ U,
+                                                    double *__restrict__ S, double *__restrict__ V,
+                                                    double *Wg, double *Vg, int use_smem, int *status) {
+  extern __shared__ double smem[];
+  __shared__ int perm[256];
+  __shared__ double nrm[256];
+  const int kp = k + (k & 1);
+  double *W = use_smem ? smem : Wg;           // W[c * k + i]: column c, row i
+  double *Vw = use_smem ? smem + (size_t)kp * k : Vg;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+  for (int e = tid; e < kp * k; e += blockDim.x) {
+    const int cc = e / k, i = e % k;
+    W[e] = (cc < k) ? A[(long long)i * k + cc] : 0.0;
+    Vw[e] = (cc == i) ? 1.0 : 0.0;
+  }
+  __syncthreads();
+  int sweep = 0;
+  for (; sweep < 60; ++sweep) {
+    int rotated = 0;
+    for (int rd = 0; rd < kp - 1; ++rd) {
+      for (int pi = warp; pi < kp / 2; pi += nw) {
+        int p = (rd + pi) % (kp - 1);
+        int q = (pi == 0) ? kp - 1 : (rd - pi + kp - 1) % (kp - 1);
+        if (p > q) { int t = p; p = q; q = t; }
+        double *wp = W + (size_t)p * k, *wq = W + (size_t)q * k;
+        double a = 0.0, b = 0.0, g = 0.0;
+        for (int i = lane; i < k; i += 32) {
+          const double x = wp[i], y = wq[i];
+          a += x * x;
+          b += y * y;
+          g += x * y;
+        }
+        a = warp_sum(a);
+        b = warp_sum(b);
+        g = warp_sum(g);
+        if (g != 0.0 && a > 0.0 && b > 0.0 && fabs(g) > 1e-15 * sqrt(a) * sqrt(b)) {
+          const double zeta = (b - a) / (2.0 * g);
+          double t;
+          if (fabs(zeta) > 1e100) t = 0.5 / zeta;
+          else t = copysign(1.0, zeta) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+          const double cs = 1.0 / sqrt(1.0 + t * t), sn = cs * t;
+          for (int i = lane; i < k; i += 32) {
+            const double x = wp[i], y = wq[i];
+            wp[i] = cs * x - sn * y;
+            wq[i] = sn * x + cs * y;
+          }
+          double *vp = Vw + (size_t)p * k, *vq = Vw + (size_t)q * k;
+          for (int i = lane; i < k; i += 32) {
+            const double x = vp[i], y = vq[i];
+            vp[i] = cs * x - sn * y;
+            vq[i] = sn * x + cs * y;
+          }
+          rotated = 1;
+        }
+      }
+      __syncthreads();
+    }
+    if (!__syncthreads_or(rotated)) break;
+  }
+  if (sweep == 60 && tid == 0 && status) atomicMax(status, (int)DS_BREAKDOWN);
+  for (int cc = warp; cc < k; cc += nw) {
+    double s = 0.0;
+    for (int i = lane; i < k; i += 32) s += W[(size_t)cc * k + i] * W[(size_t)cc * k + i];
+    s = warp_sum(s);
+    if (lane == 0) nrm[cc] = sqrt(s);
+  }
+  __syncthreads();
+  if (tid == 0) {
+    for (int i = 0; i < k; ++i) perm[i] = i;
+    for (int i = 1; i < k; ++i) {  // insertion sort, descending, stable
+      int v = perm[i], j = i - 1;
+      while (j >= 0 && nrm[perm[j]] < nrm[v]) { perm[j + 1] = perm[j]; --j; }
+      perm[j + 1] = v;
+    }
+  }
+  __syncthreads();
+  for (int e = tid; e < k * k; e += blockDim.x) {
+    const int i = e / k, j = e % k;
+    const int src = perm[j];
+    const double sv = nrm[src];
+    U[e] = (sv > 0.0) ? W[(size_t)src * k + i] / sv : 0.0;
+    V[e] = Vw[(size_t)src * k + i];
+  }
+  for (int j = tid; j < k; j += blockDim.x) S[j] = nrm[perm[j]];
+}
+
+void svd_small(Ctx *c, int k, const double *A, double *U, double *s, double *V) {
+  TTI_CHECK_ARG(k >= 1 && k <= 256, "svd_small: k=%d out of range", k);
+  const int kp = k + (k & 1);
+  size_t bytes = 2 * (size_t)kp * k * sizeof(double);
+  int use_smem = bytes <= 200 * 1024;
+  DBuf Wg, Vg;
+  if (!use_smem) {
+    Wg = DBuf(c, (size_t)kp * k * sizeof(double));
+    Vg = DBuf(c, (size_t)kp * k * sizeof(double));
+    bytes = 0;
+  } else if (bytes > 48 * 1024) {
+    TTI_CUDA(cudaFuncSetAttribute(k_jacobi_svd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+  }
+  k_jacobi_svd<<<1, 256, bytes, c->stream>>>(k, A, U, s, V, Wg.d(), Vg.d(), use_smem, c->dstatus);
+  TTI_LAUNCH();
+}
+
+// ----------------------------------------------------------------- maxvol
+
+// Deterministic block argmax of |x| over candidates; ties go to the smallest index.
+__device__ void block_argmax(double v, long long idx, double *sv, long long *si, double *out_v, long long *out_i) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    double ov = __shfl_xor_sync(0xffffffffu, v, o);
+    long long oi = __shfl_xor_sync(0xffffffffu, idx, o);
+    if (ov > v || (ov == v && oi < idx)) { v = ov; idx = oi; }
+  }
+  __syncthreads();
+  if (lane == 0) { sv[warp] = v; si[warp] = idx; }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double bv = sv[0];
+    long long bi = si[0];
+    for (int w = 1; w < nw; ++w)
+      if (sv[w] > bv || (sv[w] == bv && si[w] < bi)) { bv = sv[w]; bi = si[w]; }
+    *out_v = bv;
+    *out_i = bi;
+  }
+  __syncthreads();
+}
+
+// Phase 1 (one CTA per matrix): pivot rows by Gaussian elimination with
+// partial pivoting on a copy, then the inverse of U[rows, :] by Gauss-Jordan.
+__global__ void __launch_bounds__(1024) k_maxvol_init(const int *__restrict__ mm, const int *__restrict__ rr,
+                                                      const long long *__restrict__ off, const double *__restrict__ U,
+                                                      double *__restrict__ Wk, int *__restrict__ mask,
+                                                      const long long *__restrict__ moff, int *__restrict__ rows,
+                                                      const long long *__restrict__ roff, double *__restrict__ inv,
+                                                      const long long *__restrict__ ioff, int *status) {
+  __shared__ double sv[32];
+  __shared__ long long si[32];
+  __shared__ double bv;
+  __shared__ long long bi;
+  const int b = blockIdx.x;
+  const int m = mm[b], r = rr[b];
+  const double *Ub = U + off[b];
+  double *W = Wk + off[b];
+  int *mk = mask + moff[b];
+  int *rw = rows + roff[b];
+  double *G = inv + ioff[b];  // [r][2r] augmented matrix
+  for (long long e = threadIdx.x; e < (long long)m * r; e += blockDim.x) W[e] = Ub[e];
+  for (int i = threadIdx.x; i < m; i += blockDim.x) mk[i] = 0;
+  __syncthreads();
+  for (int j = 0; j < r; ++j) {
+    double v = -1.0;
+    long long idx = 0x7fffffffffffffffLL;
+    for (int i = threadIdx.x; i < m; i += blockDim.x) {
+      if (mk[i]) continue;
+      const double a = fabs(W[(long long)i * r + j]);
+      if (a > v || (a == v && i < idx)) { v = a; idx = i; }
+    }
+    block_argmax(v, idx, sv, si, &bv, &bi);
+    if (threadIdx.x == 0) {
+      if (bi < 0 || bi >= m) {  // no finite candidate (NaN column): take the first unused row
+        bi = 0;
+        while (bi < m - 1 && mk[bi]) ++bi;
+        if (status) atomicMax(status, (int)DS_NONFINITE);
+      }
+      rw[j] = (int)bi;
+      mk[bi] = 1;
+      if (!(bv > 0.0) && status) atomicMax(status, (int)DS_BREAKDOWN);
+    }
+    __syncthreads();
+    const int piv = (int)bi;
+    const double pv = W[(long long)piv * r + j];
+    if (pv != 0.0) {
+      for (long long e = threadIdx.x; e < (long long)m * (r - j - 1); e += blockDim.x) {
+        const int i = (int)(e / (r - j - 1)), cc = j + 1 + (int)(e % (r - j - 1));
+        if (mk[i]) continue;
+        W[(long long)i * r + cc] -= W[(long long)i * r + j] / pv * W[(long long)piv * r + cc];
+      }
+    }
+    __syncthreads();
+  }
+  // Gauss-Jordan inverse of A = U[rows, :] with partial pivoting.
+  for (int e = threadIdx.x; e < r * 2 * r; e += blockDim.x) {
+    const int i = e / (2 * r), cc = e % (2 * r);
+    G[e] = (cc < r) ? Ub[(long long)rw[i] * r + cc] : ((cc - r) == i ? 1.0 : 0.0);
+  }
+  __syncthreads();
+  for (int j = 0; j < r; ++j) {
+    if (threadIdx.x == 0) {
+      int p = j;
+      double best = fabs(G[j * 2 * r + j]);
+      for (int i = j + 1; i < r; ++i)
+        if (fabs(G[i * 2 * r + j]) > best) { best = fabs(G[i * 2 * r + j]); p = i; }
+      if (p != j)
+        for (int cc = 0; cc < 2 * r; ++cc) {
+          double t = G[j * 2 * r + cc];
+          G[j * 2 * r + cc] = G[p * 2 * r + cc];
+          G[p * 2 * r + cc] = t;
+        }
+      const double d = G[j * 2 * r + j];
+      if (d == 0.0) {
+        if (status) atomicMax(status, (int)DS_BREAKDOWN);
+      } else {
+        for (int cc = 0; cc < 2 * r; ++cc) G[j * 2 * r + cc] /= d;
+      }
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < r * 2 * r; e += blockDim.x) {
+      const int i = e / (2 * r), cc = e % (2 * r);
+      if (i == j || cc == j) continue;
+      G[e] -= G[i * 2 * r + j] * G[j * 2 * r + cc];
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < r; i += blockDim.x)
+      if (i != j) G[i * 2 * r + j] = 0.0;
+    __syncthreads();
+  }
+}
+
+// Phase 3 (one CTA per matrix): greedy row swaps while max |B| > 1 + delta.
+__global__ void __launch_bounds__(1024) k_maxvol_swap(const int *__restrict__ mm, const int *__restrict__ rr,
+                                                      const long long *__restrict__ off, double *__restrict__ B,
+                                                      double *__restrict__ colbuf, int *__restrict__ rows,
+                                                      const long long *__restrict__ roff, double delta, int maxit) {
+  __shared__ double sv[32];
+  __shared__ long long si[32];
+  __shared__ double bv;
+  __shared__ long long bi;
+  __shared__ double rowi[256];
+  const int b = blockIdx.x;
+  const int m = mm[b], r = rr[b];
+  double *Bb = B + off[b];
+  double *cb = colbuf + off[b];
+  int *rw = rows + roff[b];
+  for (int it = 0; it < maxit; ++it) {
+    double v = -1.0;
+    long long idx = 0x7fffffffffffffffLL;
+    for (long long e = threadIdx.x; e < (long long)m * r; e += blockDim.x) {
+      const double a = fabs(Bb[e]);
+      if (a > v || (a == v && e < idx)) { v = a; idx = e; }
+    }
+    block_argmax(v, idx, sv, si, &bv, &bi);
+    if (!(bv > 1.0 + delta)) break;
+    const int i = (int)(bi / r), j = (int)(bi % r);
+    for (int cc = threadIdx.x; cc < r; cc += blockDim.x) rowi[cc] = Bb[(long long)i * r + cc];
+    for (int x = threadIdx.x; x < m; x += blockDim.x) cb[x] = Bb[(long long)x * r + j];
+    __syncthreads();
+    const double piv = rowi[j];
+    for (long long e = threadIdx.x; e < (long long)m * r; e += blockDim.x) {
+      const int x = (int)(e / r), cc = (int)(e % r);
+      Bb[e] -= cb[x] * (rowi[cc] - (cc == j ? 1.0 : 0.0)) / piv;
+    }
+    if (threadIdx.x == 0) rw[j] = i;
+    __syncthreads();
+  }
+}
+
+void maxvol_batched(Ctx *c, int count, const int *m, const int *r, const long long *off, const double *U,
+                    double *B, int *rows, const long long *rows_off, double delta, int maxit) {
+  if (count <= 0) return;
+  std::vector<long long> moff(count), ioff(count);
+  long long mt = 0, it = 0, tot = 0;
+  for (int b = 0; b < count; ++b) {
+    TTI_CHECK_ARG(r[b] >= 1 && r[b] <= 256 && m[b] >= r[b], "maxvol: bad sizes m=%d r=%d", m[b], r[b]);
+    moff[b] = mt;
+    mt += m[b];
+    ioff[b] = it;
+    it += (long long)r[b] * 2 * r[b];
+    tot = std::max(tot, off[b] + (long long)m[b] * r[b]);
+  }
+  std::vector<int> meta_i(2 * count);
+  std::vector<long long> meta_l(4 * count);
+  for (int b = 0; b < count; ++b) {
+    meta_i[b] = m[b];
+    meta_i[count + b] = r[b];
+    meta_l[b] = off[b];
+    meta_l[count + b] = moff[b];
+    meta_l[2 * count + b] = rows_off[b];
+    meta_l[3 * count + b] = ioff[b];
+  }
+  DBuf dmi(c, meta_i.size() * sizeof(int)), dml(c, meta_l.size() * sizeof(long long));
+  c->h2d(dmi.get(), meta_i.data(), meta_i.size() * sizeof(int));
+  c->h2d(dml.get(), meta_l.data(), meta_l.size() * sizeof(long long));
+  const int *dm = dmi.as<int>(), *dr = dm + count;
+  const long long *doff = dml.as<long long>(), *dmoff = doff + count, *droff = doff + 2 * count,
+                  *dioff = doff + 3 * count;
+  DBuf work(c, (size_t)tot * sizeof(double)), mask(c, (size_t)mt * sizeof(int)), inv(c, (size_t)it * sizeof(double));
+  k_maxvol_init<<<count, 1024, 0, c->stream>>>(dm, dr, doff, U, work.d(), mask.as<int>(), dmoff, rows, droff,
+                                               inv.d(), dioff, c->dstatus);
+  TTI_LAUNCH();
+  // B = U * inv(U[rows, :]) on the whole GPU (inverse sits in the right half of the augmented matrix)
+  for (int b = 0; b < count; ++b)
+    gemm<double>(c, false, false, m[b], r[b], r[b], 1.0, U + off[b], r[b], 0, inv.d() + ioff[b] + r[b], 2 * r[b], 0,
+                 0.0, B + off[b], r[b], 0, 1);
+  k_maxvol_swap<<<count, 1024, 0, c->stream>>>(dm, dr, doff, B, work.d(), rows, droff, delta, maxit);
+  TTI_LAUNCH();
+}
+
+}  // namespace ttiga
