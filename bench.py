@@ -1,0 +1,335 @@
+#!/usr/bin/env python3
+"""Benchmark of the TT-IGA hot path on GB300: DOFs solved per second.
+
+One step = the whole hot path on one synthetic problem: TT-cross of the
+geometry coefficients, per-direction contraction into the TT stiffness and
+load, TT rounding, Dirichlet restriction and the AMEn solve to relative
+residual 1e-8 (exact, TT arithmetic).  The default workload is the quarter
+thick-walled cylinder (radii 1..2, height 1, quadratic NURBS angular
+direction) at degree p = 3 with n = 128 B-splines per direction (2,097,152
+DOFs) and the manufactured bubble solution.  DOFs per step = n^3.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun every rank solves its own replica (independent problems, no
+collective on the data path); rank 0 prints one JSON line.  `--impl
+reference` times the FP64 CPU oracle (full-grid IGA + Jacobi PCG) on a bounded
+sample of the same workload on the host cores.
+"""
+import argparse
+import json
+import os
+import resource
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import synthetic  # noqa: E402
+
+WORKLOAD = "quarter_cylinder_p3_n128"
+METRIC = "DOFs solved/s at 1e-8 rel. residual, mixed vs FP64; serving p50/p99 latency"
+TOL = 1e-8
+FP64_ALU_PEAK_TFLOPS = 1.258  # 152 SMs x 2 FP64 FMA/clk x 2 FLOP x 2.07 GHz (nominal 1.25 TFLOP/s)
+REFERENCE_SAMPLE_N = 16
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", default=WORKLOAD)
+    ap.add_argument("--profile-family", type=int, default=1,
+                    help="kernel family timed live for the roofline (1 band stage of the local matvec)")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-mixed", action="store_true")
+    return ap.parse_args()
+
+
+def dist_setup(n):
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("gloo")
+    return rank, world
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x, world):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms during the timed region."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device):
+        self.device = device
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.device}", f"--query-gpu={self.QUERY}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.lines:
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = max(mx, float(f[2]))
+            except ValueError:
+                continue
+            for k, name in enumerate(names):
+                if f[5 + k].lower().startswith("active"):
+                    reasons.add(name)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def oracle_step(n, p, geo):
+    """Full-grid FP64 IGA assembly + Jacobi PCG to relative residual TOL (the oracle as it stands)."""
+    from oracle.geometry import Annulus
+    from oracle.iga import Space1D, assemble, pcg, restrict
+    from oracle.manufactured import Manufactured
+    og = Annulus(geo["r_in"], geo["r_out"], geo["height"], geo["twist"], geo["swell"])
+    sp = [Space1D(n, p)] * 3
+    Kst, F = assemble(sp, og, Manufactured(og))
+    Ki, Fi = restrict(Kst, F)
+    x, it, rr = pcg(Ki, Fi, (p, p, p), tol=TOL)
+    return rr
+
+
+def timed_oracle(n, p, geo):
+    r0 = resource.getrusage(resource.RUSAGE_SELF)
+    t0 = time.perf_counter()
+    oracle_step(n, p, geo)
+    wall = time.perf_counter() - t0
+    r1 = resource.getrusage(resource.RUSAGE_SELF)
+    cpu = (r1.ru_utime - r0.ru_utime) + (r1.ru_stime - r0.ru_stime)
+    return wall, max(1.0, cpu / wall)
+
+
+def cpu_baseline(wl):
+    n, p = 24, wl["p"]
+    wall, cores = timed_oracle(n, p, wl["geometry"])
+    return {"value": n ** 3 / wall, "unit": "DOFs/s", "cores": round(cores, 2), "kind": "oracle",
+            "sample": f"one full-grid FP64 assemble + Jacobi-PCG solve to 1e-8 of the same geometry at p={p}, "
+                      f"n={n} ({n ** 3} DOFs), {wall:.1f} s on the host"}
+
+
+def run_reference(args, rank, world):
+    wl = synthetic.WORKLOADS[args.workload]
+    if rank != 0:
+        return
+    n, p = REFERENCE_SAMPLE_N, wl["p"]
+    for _ in range(args.warmup):
+        oracle_step(n, p, wl["geometry"])
+    walls, cores = [], []
+    for _ in range(args.steps):
+        w, cr = timed_oracle(n, p, wl["geometry"])
+        walls.append(w)
+        cores.append(cr)
+    t = statistics.mean(walls)
+    value = n ** 3 / t
+    line = {"metric": METRIC, "value": value, "unit": "DOFs/s", "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": t * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+            "config": {"workload": args.workload, "p": p, "n": wl["n"], "tol": TOL,
+                       "sample_n": n, "parallelism": "replicas"},
+            "cpu_baseline": {"value": value, "unit": "DOFs/s", "cores": round(statistics.mean(cores), 2),
+                             "kind": "oracle",
+                             "sample": f"per step: full-grid FP64 assemble + Jacobi-PCG to 1e-8 at p={p}, "
+                                       f"n={n} ({n ** 3} DOFs)"},
+            "e2e": {"value": value, "unit": "DOFs/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args, rank, world):
+    import numpy as np
+    import torch
+
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2509_13224_gb300 as tt
+
+    wl = synthetic.WORKLOADS[args.workload]
+    n, p = wl["n"], wl["p"]
+    dofs = n ** 3
+    base = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        base = cpu_baseline(wl)
+
+    stream = torch.cuda.Stream()
+    ctx = tt.tt_iga_ctx_create(stream)
+    gdesc = tt.geom_desc(wl["geometry"], p, n, cross_tol=wl["cross_tol"], seed=rank)
+    rhs = [tt.rhs_desc(wl["modes"])]
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")  # 256 MB > 129 MB L2
+
+    def step(precision, info=None):
+        g = tt.tt_iga_geometry(ctx, gdesc)
+        s = tt.tt_iga_assemble(ctx, g, rhs, round_tol=wl["round_tol"])
+        u, st = tt.tt_iga_solve(ctx, s, tt.solve_opts(tol=TOL, precision=precision))
+        if info is not None:
+            info.update(st)
+            info["op_ranks"] = tt.tt_iga_system_info(s)["op_ranks"]
+        return g, s, u
+
+    def release(hs):
+        g, s, u = hs
+        tt.tt_iga_solution_destroy(u)
+        tt.tt_iga_system_destroy(s)
+        tt.tt_iga_geom_destroy(g)
+
+    def timed(precision, k, w, profile=False):
+        for _ in range(w):
+            release(step(precision))
+        info = {}
+        times = []
+        barrier(world)
+        torch.cuda.synchronize()
+        if profile:
+            tt.tt_iga_profile_enable(ctx, args.profile_family)
+        l0 = tt.tt_iga_launch_count()
+        for _ in range(k):
+            with torch.cuda.stream(stream):
+                flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            hs = step(precision, info)
+            e1.record(stream)
+            e1.synchronize()
+            times.append(e0.elapsed_time(e1))
+            release(hs)
+        launches = tt.tt_iga_launch_count() - l0
+        prof = tt.tt_iga_profile_read(ctx) if profile else None
+        if profile:
+            tt.tt_iga_profile_enable(ctx, 0)
+        torch.cuda.synchronize()
+        barrier(world)
+        return statistics.mean(times), info, launches, prof
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    ms64, info64, launches, prof = timed(tt.FP64, args.steps, args.warmup, profile=True)
+    clk = clocks.stop()
+    ms64_max = max_over_ranks(ms64, world)
+
+    mixed = None
+    if not args.no_mixed:
+        msm, infom, _, _ = timed(tt.MIXED_FP32, args.steps, max(1, args.warmup // 2))
+        msm_max = max_over_ranks(msm, world)
+        mixed = {"value": world * dofs / (msm_max / 1e3), "ms_per_step": msm_max, "dtype": "f32 local solves in f64 IR",
+                 "rel_residual": infom.get("rel_residual"), "sweeps": infom.get("sweeps"),
+                 "ranks": infom.get("ranks"), "local_matvecs": infom.get("local_matvecs"),
+                 "local_matvecs_fp64": infom.get("local_matvecs_fp64")}
+
+    # end to end through the C ABI: host descriptors in, compressed solution cores read back to pinned host memory
+    e2e_times = []
+    hbuf = None
+    d2h = 0
+    for _ in range(max(1, args.steps)):
+        with torch.cuda.stream(stream):
+            flush.zero_()
+        stream.synchronize()
+        t0 = time.perf_counter()
+        hs = step(tt.FP64)
+        m, r = tt.tt_iga_solution_ranks(hs[2]), None
+        sizes = None
+        if hbuf is None:
+            hbuf = torch.empty(4 * 1024 * 1024, dtype=torch.float64).pin_memory().numpy()
+        cores = tt.tt_iga_solution_cores(ctx, hs[2], hbuf)
+        d2h = sum(c.size for c in cores) * 8
+        e2e_times.append(time.perf_counter() - t0)
+        release(hs)
+    e2e_s = max_over_ranks(statistics.mean(e2e_times), world)
+    h2d = len(bytes(gdesc)) + sum(len(bytes(r_)) for r_ in rhs) + len(bytes(tt.solve_opts()))
+
+    tt.tt_iga_ctx_destroy(ctx)
+    if rank != 0:
+        return
+    roof = None
+    if prof is not None and prof[1] > 0:
+        ms_k, n_k, flops_k = prof
+        achieved = flops_k / n_k / (ms_k / n_k / 1e3) / 1e12
+        roof = {"bound": "alu", "achieved": achieved, "peak": FP64_ALU_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": achieved / FP64_ALU_PEAK_TFLOPS, "traffic": None,
+                "kernel": {1: "k_band_right (local matvec band stage, FP64)", 2: "k_gemm<double>",
+                           3: "k_qr_panel"}.get(args.profile_family, str(args.profile_family)),
+                "launches": n_k, "kernel_ms_per_step": ms_k / args.steps,
+                "share_of_step": ms_k / args.steps / ms64, "flops_per_launch": flops_k / n_k}
+    line = {"metric": METRIC, "value": world * dofs / (ms64_max / 1e3), "unit": "DOFs/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms64_max, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": args.workload, "geometry": "quarter cylinder r 1..2 h 1", "p": p, "n": n,
+                       "dofs": dofs, "unknowns": (n - 2) ** 3, "tol": TOL, "precision": "fp64",
+                       "l2": "flushed between steps (256 MB write)", "parallelism": "replicas"},
+            "e2e": {"value": world * dofs / e2e_s, "unit": "DOFs/s", "h2d_bytes_per_step": h2d,
+                    "d2h_bytes_per_step": d2h},
+            "gpu_launches": launches, "clocks": clk, "roofline": roof, "cpu_baseline": base, "mixed": mixed,
+            "solve": {"rel_residual": info64.get("rel_residual"), "sweeps": info64.get("sweeps"),
+                      "ranks": info64.get("ranks"), "op_ranks": info64.get("op_ranks"),
+                      "local_matvecs": info64.get("local_matvecs"), "solve_ms": info64.get("ms_total")}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    rank, world = dist_setup(args.gpus)
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+    else:
+        run_ours(args, rank, world)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

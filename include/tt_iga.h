@@ -231,6 +231,41 @@ int tt_iga_eval(tt_iga_ctx *ctx, const tt_iga_solution *u, int m, const double *
 int tt_iga_l2_error(tt_iga_ctx *ctx, const tt_iga_geom *g, const tt_iga_solution *u,
                     const tt_iga_rhs_desc *rhs, double *rel_l2);
 
+/* ------------------------------------------------------------ batching */
+
+/* One instance of a batch: geometry and discretisation, its right-hand sides
+ * (host array of n_rhs descriptors, 1..8), the assembly rounding tolerance and
+ * the solve options (rhs_index is ignored: every right-hand side is solved). */
+typedef struct {
+  tt_iga_geom_desc geom;
+  int n_rhs;
+  const tt_iga_rhs_desc *rhs;
+  double round_tol;
+  tt_iga_solve_opts opts;
+} tt_iga_batch_item;
+
+typedef struct {
+  int status;                /* tt_iga_status of this instance */
+  int ranks[2];              /* solution ranks of its last right-hand side */
+  int sweeps;                /* AMEn sweeps summed over its right-hand sides */
+  double rel_residual_max;   /* worst exact relative residual over its right-hand sides */
+  long long dofs;            /* n1 n2 n3 times the number of right-hand sides */
+  double ms_geometry, ms_assemble, ms_solve;  /* host wall clock per phase */
+  double t_start_ms, t_end_ms;                /* start / end relative to the batch start */
+} tt_iga_batch_result;
+
+/* Solve `count` independent instances on `device` with `lanes` concurrent
+ * contexts (each its own stream and host thread, 1..64) fed from a work queue,
+ * largest instance first.  results[count] (host) receives one record per
+ * instance in input order; *wall_ms (may be NULL) the batch wall time.
+ * Returns TT_IGA_OK or the first failing instance's status. */
+int tt_iga_batch_solve(int device, int count, const tt_iga_batch_item *items, int lanes,
+                       tt_iga_batch_result *results, double *wall_ms);
+/* Autotuner: run the batch once per candidate lane count and report the
+ * fastest (*best_lanes, *best_ms); results hold the last run. */
+int tt_iga_batch_autotune(int device, int count, const tt_iga_batch_item *items, const int *candidates,
+                          int n_candidates, tt_iga_batch_result *results, int *best_lanes, double *best_ms);
+
 /* ----------------------------------------------------- dense test hooks */
 
 /* Dense restricted operator (N x N, N = prod(n_d - 2), host, row g = i1 + ...).

@@ -59,6 +59,21 @@ class SolveOpts(ctypes.Structure):
                 ("rhs_index", ctypes.c_int), ("verbose", ctypes.c_int)]
 
 
+class BatchItem(ctypes.Structure):
+    _fields_ = [("geom", GeomDesc), ("n_rhs", ctypes.c_int), ("rhs", ctypes.POINTER(RhsDesc)),
+                ("round_tol", ctypes.c_double), ("opts", SolveOpts)]
+
+
+class BatchResult(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int), ("ranks", ctypes.c_int * 2), ("sweeps", ctypes.c_int),
+                ("rel_residual_max", ctypes.c_double), ("dofs", ctypes.c_longlong), ("ms_geometry", ctypes.c_double),
+                ("ms_assemble", ctypes.c_double), ("ms_solve", ctypes.c_double), ("t_start_ms", ctypes.c_double),
+                ("t_end_ms", ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: (list(getattr(self, k)) if k == "ranks" else getattr(self, k)) for k, _ in self._fields_}
+
+
 class Stats(ctypes.Structure):
     _fields_ = [("sweeps", ctypes.c_int), ("ranks", ctypes.c_int * 2), ("rel_residual", ctypes.c_double),
                 ("local_residual", ctypes.c_double), ("local_matvecs", ctypes.c_longlong),
@@ -102,6 +117,10 @@ _SIGS = {
     "tt_iga_densify_solution": (ctypes.c_int, [_vp, _vp, _c_double_p, ctypes.c_size_t]),
     "tt_iga_operator_entries": (ctypes.c_int, [_vp, _vp, ctypes.c_int, _c_int_p, _c_int_p, _c_double_p]),
     "tt_iga_vector_entries": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int, ctypes.c_int, _c_int_p, _c_double_p]),
+    "tt_iga_batch_solve": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.POINTER(BatchItem), ctypes.c_int,
+                                          ctypes.POINTER(BatchResult), _c_double_p]),
+    "tt_iga_batch_autotune": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.POINTER(BatchItem), _c_int_p,
+                                             ctypes.c_int, ctypes.POINTER(BatchResult), _c_int_p, _c_double_p]),
     "tt_iga_basis_tables": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, _vp, _vp, _vp, _vp]),
     "tt_iga_geom_points": (ctypes.c_int, [_vp, _vp, ctypes.POINTER(RhsDesc), ctypes.c_int, _vp, _vp,
                                           ctypes.POINTER(ctypes.c_longlong)]),
@@ -393,6 +412,42 @@ def tt_iga_vector_entries(ctx, s, u, k, idx):
     _check(ctx, _lib.tt_iga_vector_entries(ctx, s, u, k, len(idx), idx.ctypes.data_as(_c_int_p),
                                            out.ctypes.data_as(_c_double_p)))
     return out
+
+
+def batch_items(instances, tol=1e-8, precision=FP64, cross_tol=1e-10, round_tol=1e-12, max_rank=0):
+    """BatchItem array from instance dicts (synthetic.random_instance); keeps the rhs arrays alive."""
+    arr = (BatchItem * len(instances))()
+    keep = []
+    for k, inst in enumerate(instances):
+        arr[k].geom = geom_desc(inst["geometry"], inst["p"], inst["n"], cross_tol=cross_tol, seed=inst.get("seed", 0),
+                                max_rank=max_rank)
+        rh = (RhsDesc * len(inst["rhs"]))(*[rhs_desc(m) for m in inst["rhs"]])
+        keep.append(rh)
+        arr[k].n_rhs = len(inst["rhs"])
+        arr[k].rhs = ctypes.cast(rh, ctypes.POINTER(RhsDesc))
+        arr[k].round_tol = round_tol
+        arr[k].opts = solve_opts(tol=tol, precision=precision)
+    return arr, keep
+
+
+def tt_iga_batch_solve(items, lanes, device=0):
+    """Returns (status, per-instance result dicts, wall ms)."""
+    n = len(items)
+    res = (BatchResult * max(1, n))()
+    ms = ctypes.c_double()
+    code = _lib.tt_iga_batch_solve(device, n, items, lanes, res, ctypes.byref(ms))
+    return code, [res[i].as_dict() for i in range(n)], ms.value
+
+
+def tt_iga_batch_autotune(items, candidates, device=0):
+    n = len(items)
+    res = (BatchResult * max(1, n))()
+    cand = (ctypes.c_int * len(candidates))(*candidates)
+    best, ms = ctypes.c_int(), ctypes.c_double()
+    code = _lib.tt_iga_batch_autotune(device, n, items, cand, len(candidates), res, ctypes.byref(best),
+                                      ctypes.byref(ms))
+    _check(None, code, (ERR_NOT_CONVERGED,))
+    return best.value, ms.value, [res[i].as_dict() for i in range(n)]
 
 
 def tt_iga_basis_tables(ctx, n, p, nq, pts, wts, N, dN):

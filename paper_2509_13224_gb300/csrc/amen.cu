@@ -27,6 +27,7 @@
 #include "amen.cuh"
 #include "amen_ops.cuh"
 #include "linalg.cuh"
+#include "pcg_fused.cuh"
 #include "tt.cuh"
 
 namespace ttiga {
@@ -225,40 +226,35 @@ struct Amen {
     return host_nrm2(c, r, N);
   }
 
-  // PCG on B d = r (type T), d starts at zero.  Absolute tolerance tol on ||r - B d||.
+  // PCG on B d = r (type T), d starts at zero; one cooperative launch for all
+  // iterations.  Absolute tolerance tol on ||r - B d||.  Returns iterations.
   template <typename T>
   int pcg(int k, const T *PhiLk, const T *PhiRk, const T *Ak, const T *L, const T *b, T *x, double tol, int maxit) {
     const long long N = (long long)rl(k) * n(k) * rr(k);
-    Work<T> &w = work((T *)nullptr);
-    DBuf rb(c, N * sizeof(T)), zb(c, N * sizeof(T)), pb(c, N * sizeof(T)), qb(c, N * sizeof(T));
-    T *r = rb.as<T>(), *zz = zb.as<T>(), *p = pb.as<T>(), *q = qb.as<T>();
-    double *sc = scal.d();
-    double *part = sc + 16;
-    TTI_CUDA(cudaMemcpyAsync(r, b, N * sizeof(T), cudaMemcpyDeviceToDevice, c->stream));
-    c->zero(x, N * sizeof(T));
-    precond_apply<T>(c, L, rl(k), n(k), S->p, rr(k), r, zz);
-    TTI_CUDA(cudaMemcpyAsync(p, zz, N * sizeof(T), cudaMemcpyDeviceToDevice, c->stream));
-    dot_dev<T>(c, r, zz, N, sc + 0, part);
-    int it = 0;
-    for (; it < maxit; ++it) {
-      apply_local<T>(c, w, PhiLk, rl(k), rl(k), A[k], Ak, PhiRk, rr(k), rr(k), p, q);
-      st.local_matvecs++;
-      if (sizeof(T) == 8) st.local_matvecs_fp64++;
-      dot_dev<T>(c, p, q, N, sc + 1, part);
-      k_pcg_xr<T><<<grid1d(N, 256), 256, 0, c->stream>>>(x, r, p, q, sc + 0, sc + 1, N);
-      TTI_LAUNCH();
-      if ((it % 4) == 3 || it == maxit - 1) {
-        dot_dev<T>(c, r, r, N, sc + 3, part);
-        double rr2;
-        c->d2h(&rr2, sc + 3, sizeof rr2);
-        if (sqrt(std::max(rr2, 0.0)) <= tol) { ++it; break; }
-      }
-      precond_apply<T>(c, L, rl(k), n(k), S->p, rr(k), r, zz);
-      dot_dev<T>(c, r, zz, N, sc + 2, part);
-      k_pcg_p<T><<<grid1d(N, 256), 256, 0, c->stream>>>(p, zz, sc + 2, sc + 0, N);
-      TTI_LAUNCH();
-      TTI_CUDA(cudaMemcpyAsync(sc + 0, sc + 2, sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
-    }
+    PcgArgs<T> a{};
+    a.PhiL = PhiLk; a.PhiR = PhiRk; a.A = Ak; a.L = L; a.b = b; a.x = x;
+    a.rl = rl(k); a.rr = rr(k); a.Rl = R[k]; a.Rr = R[k + 1]; a.n = n(k); a.p = S->p;
+    a.tol2 = tol * tol;
+    a.maxit = maxit;
+    const int grid = pcg_fused_grid<T>(c, a);
+    DBuf vec(c, 4 * N * sizeof(T)), t1(c, (size_t)a.rl * a.n * a.rr * a.Rr * sizeof(T)),
+        t2(c, (size_t)a.Rl * a.rl * a.n * a.rr * sizeof(T)), aux(c, (3 * (size_t)grid + 8) * sizeof(double));
+    a.r = vec.as<T>(); a.z = a.r + N; a.pv = a.z + N; a.q = a.pv + N;
+    a.T1 = t1.as<T>(); a.T2 = t2.as<T>();
+    a.part = aux.d();
+    a.out = aux.d() + 3 * grid;
+    a.bar = reinterpret_cast<Barrier *>(aux.d() + 3 * grid + 2);
+    a.err = reinterpret_cast<int *>(aux.d() + 3 * grid + 3);
+    c->zero(a.err, sizeof(int));
+    pcg_fused<T>(c, a, grid);
+    double hout[4];
+    c->d2h(hout, a.out, 4 * sizeof(double));
+    int err = 0;
+    memcpy(&err, &hout[3], sizeof(int));
+    if (err) fail(TT_IGA_ERR_TIMEOUT, "pcg: a grid barrier wait ran out");
+    const int it = (int)hout[0];
+    st.local_matvecs += it;
+    if (sizeof(T) == 8) st.local_matvecs_fp64 += it;
     return it;
   }
 

@@ -141,30 +141,53 @@ __global__ void k_diag_interface(const double *Phi, int r, int R, double *D) {
 }
 
 // Band Cholesky per (alpha, beta) pair of the symmetrised band matrix
-// P[a][i][o][b]; L[i][k][pair] = L(i, i - p + k).
-template <typename T>
-__global__ void k_band_cholesky(const double *__restrict__ P, int rl, int n, int p, int rr, T *__restrict__ L,
-                                int *status) {
-  const int npair = rl * rr, b = 2 * p + 1;
+// P[a][i][o][b] (half-bandwidth PB).  Output L[i][k][pair] = L(i, i-PB+k) for
+// k < PB and the reciprocal of the diagonal in slot PB.  With j = i-PB+k,
+//   L(i,j) = (A(i,j) - sum_{m=i-PB}^{j-1} L(i,m) L(j,m)) / L(j,j),
+//   L(i,i) = sqrt(A(i,i) - sum_{m=i-PB}^{i-1} L(i,m)^2).
+// The previous PB rows of L stay in registers (win[q] = row i-PB+q).
+template <typename T, int PB>
+__global__ void k_band_cholesky(const double *__restrict__ Pm, int rl, int n, int rr, T *__restrict__ L, int *status) {
+  const int npair = rl * rr, b = 2 * PB + 1;
   for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < npair; t += gridDim.x * blockDim.x) {
     const int a = t / rr, bb = t % rr;
-    auto Pv = [&](int i, int o) { return P[(((long long)a * n + i) * b + o) * rr + bb]; };
-    auto Lr = [&](int i, int k) -> T & { return L[((long long)i * (p + 1) + k) * npair + t]; };
+    const double *Pp = Pm + (long long)a * n * b * rr + bb;
+    double win[PB][PB + 1];
+#pragma unroll
+    for (int q = 0; q < PB; ++q)
+#pragma unroll
+      for (int k = 0; k <= PB; ++k) win[q][k] = 0.0;
     bool bad = false;
     for (int i = 0; i < n; ++i) {
-      for (int j = max(0, i - p); j <= i; ++j) {
-        double s = 0.5 * (Pv(i, j - i + p) + Pv(j, i - j + p));
-        for (int m = max(0, i - p); m < j; ++m) s -= (double)Lr(i, m - i + p) * (double)Lr(j, m - j + p);
-        if (j < i) {
-          Lr(i, j - i + p) = (T)(s / (double)Lr(j, p));
-        } else {
-          if (!(s > 0.0)) {
-            bad = true;
-            s = fabs(s) + 1e-300;
-          }
-          Lr(i, p) = (T)sqrt(s);
+      double row[PB + 1];
+#pragma unroll
+      for (int k = 0; k < PB; ++k) {
+        const int j = i - PB + k;
+        if (j < 0) {
+          row[k] = 0.0;
+          continue;
         }
+        double sv = 0.5 * (Pp[((long long)i * b + k) * rr] + Pp[((long long)j * b + (2 * PB - k)) * rr]);
+#pragma unroll
+        for (int mm = 0; mm < k; ++mm) sv -= row[mm] * win[k][mm + PB - k];
+        row[k] = sv * win[k][PB];
       }
+      double sd = Pp[((long long)i * b + PB) * rr];
+#pragma unroll
+      for (int mm = 0; mm < PB; ++mm) sd -= row[mm] * row[mm];
+      if (!(sd > 0.0)) {
+        bad = true;
+        sd = fabs(sd) + 1e-300;
+      }
+      row[PB] = 1.0 / sqrt(sd);
+#pragma unroll
+      for (int k = 0; k <= PB; ++k) L[((long long)i * (PB + 1) + k) * npair + t] = (T)row[k];
+#pragma unroll
+      for (int q = 0; q + 1 < PB; ++q)
+#pragma unroll
+        for (int k = 0; k <= PB; ++k) win[q][k] = win[q + 1][k];
+#pragma unroll
+      for (int k = 0; k <= PB; ++k) win[PB - 1][k] = row[k];
     }
     if (bad) atomicMax(status, (int)DS_BREAKDOWN);
   }
@@ -185,35 +208,76 @@ void precond_build(Ctx *c, const double *PhiL, int rl, const BandCore &A, const 
   DBuf P(c, (size_t)rl * n * b * rr * sizeof(double));
   gemm<double>(c, false, false, rl, n * b * rr, Rl, 1.0, dL.d(), Rl, 0, W.d(), (long long)n * b * rr, 0, 0.0, P.d(),
                (long long)n * b * rr, 0, 1);
-  k_band_cholesky<T><<<grid1d((long long)rl * rr, 64), 64, 0, c->stream>>>(P.d(), rl, n, A.p, rr, L, c->dstatus);
+  const unsigned grid = grid1d((long long)rl * rr, 32), blk = 32;
+  switch (A.p) {
+    case 1: k_band_cholesky<T, 1><<<grid, blk, 0, c->stream>>>(P.d(), rl, n, rr, L, c->dstatus); break;
+    case 2: k_band_cholesky<T, 2><<<grid, blk, 0, c->stream>>>(P.d(), rl, n, rr, L, c->dstatus); break;
+    case 3: k_band_cholesky<T, 3><<<grid, blk, 0, c->stream>>>(P.d(), rl, n, rr, L, c->dstatus); break;
+    case 4: k_band_cholesky<T, 4><<<grid, blk, 0, c->stream>>>(P.d(), rl, n, rr, L, c->dstatus); break;
+    case 5: k_band_cholesky<T, 5><<<grid, blk, 0, c->stream>>>(P.d(), rl, n, rr, L, c->dstatus); break;
+    case 6: k_band_cholesky<T, 6><<<grid, blk, 0, c->stream>>>(P.d(), rl, n, rr, L, c->dstatus); break;
+    case 7: k_band_cholesky<T, 7><<<grid, blk, 0, c->stream>>>(P.d(), rl, n, rr, L, c->dstatus); break;
+    default: fail(TT_IGA_ERR_ARG, "preconditioner: degree %d outside 1..7", A.p);
+  }
   TTI_LAUNCH();
 }
 template void precond_build<double>(Ctx *, const double *, int, const BandCore &, const double *, int, double *);
 template void precond_build<float>(Ctx *, const double *, int, const BandCore &, const double *, int, float *);
 
-template <typename T>
-__global__ void k_band_solve(const T *__restrict__ L, int rl, int n, int p, int rr, const T *__restrict__ r,
+// Solve L L^T z = r per (alpha, beta) pair with the factors of k_band_cholesky
+// (reciprocal diagonal in slot PB).  Forward: y_i = (r_i - sum_k L(i,i-PB+k)
+// y_{i-PB+k}) / L(i,i); backward: z_i = (y_i - sum_{d=1..PB} L(i+d,i) z_{i+d}) /
+// L(i,i).  The last PB solution values are kept in registers; the factor
+// loads do not depend on them and pipeline freely.
+template <typename T, int PB>
+__global__ void k_band_solve(const T *__restrict__ L, int rl, int n, int rr, const T *__restrict__ r,
                              T *__restrict__ z) {
   const int npair = rl * rr;
   for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < npair; t += gridDim.x * blockDim.x) {
     const int a = t / rr, bb = t % rr;
-    auto idx = [&](int i) { return ((long long)a * n + i) * rr + bb; };
-    auto Lr = [&](int i, int k) { return L[((long long)i * (p + 1) + k) * npair + t]; };
-    for (int i = 0; i < n; ++i) {  // L y = r
-      T s = r[idx(i)];
-      for (int m = max(0, i - p); m < i; ++m) s -= Lr(i, m - i + p) * z[idx(m)];
-      z[idx(i)] = s / Lr(i, p);
+    const long long base = (long long)a * n * rr + bb;
+    T w[PB];
+#pragma unroll
+    for (int k = 0; k < PB; ++k) w[k] = T(0);
+    for (int i = 0; i < n; ++i) {
+      const T *Li = L + (long long)i * (PB + 1) * npair + t;
+      T sv = r[base + (long long)i * rr];
+#pragma unroll
+      for (int k = 0; k < PB; ++k) sv -= Li[(long long)k * npair] * w[k];
+      const T y = sv * Li[(long long)PB * npair];
+      z[base + (long long)i * rr] = y;
+#pragma unroll
+      for (int k = 0; k + 1 < PB; ++k) w[k] = w[k + 1];
+      w[PB - 1] = y;
     }
-    for (int i = n - 1; i >= 0; --i) {  // L^T z = y
-      T s = z[idx(i)];
-      for (int m = i + 1; m <= min(n - 1, i + p); ++m) s -= Lr(m, i - m + p) * z[idx(m)];
-      z[idx(i)] = s / Lr(i, p);
+#pragma unroll
+    for (int k = 0; k < PB; ++k) w[k] = T(0);  // w[d-1] = z_{i+d}
+    for (int i = n - 1; i >= 0; --i) {
+      T sv = z[base + (long long)i * rr];
+#pragma unroll
+      for (int d = 1; d <= PB; ++d)
+        if (i + d < n) sv -= L[((long long)(i + d) * (PB + 1) + (PB - d)) * npair + t] * w[d - 1];
+      const T zi = sv * L[((long long)i * (PB + 1) + PB) * npair + t];
+      z[base + (long long)i * rr] = zi;
+#pragma unroll
+      for (int d = PB - 1; d > 0; --d) w[d] = w[d - 1];
+      w[0] = zi;
     }
   }
 }
 
 template <typename T> void precond_apply(Ctx *c, const T *L, int rl, int n, int p, int rr, const T *r, T *z) {
-  k_band_solve<T><<<grid1d((long long)rl * rr, 64), 64, 0, c->stream>>>(L, rl, n, p, rr, r, z);
+  const unsigned grid = grid1d((long long)rl * rr, 32), blk = 32;
+  switch (p) {
+    case 1: k_band_solve<T, 1><<<grid, blk, 0, c->stream>>>(L, rl, n, rr, r, z); break;
+    case 2: k_band_solve<T, 2><<<grid, blk, 0, c->stream>>>(L, rl, n, rr, r, z); break;
+    case 3: k_band_solve<T, 3><<<grid, blk, 0, c->stream>>>(L, rl, n, rr, r, z); break;
+    case 4: k_band_solve<T, 4><<<grid, blk, 0, c->stream>>>(L, rl, n, rr, r, z); break;
+    case 5: k_band_solve<T, 5><<<grid, blk, 0, c->stream>>>(L, rl, n, rr, r, z); break;
+    case 6: k_band_solve<T, 6><<<grid, blk, 0, c->stream>>>(L, rl, n, rr, r, z); break;
+    case 7: k_band_solve<T, 7><<<grid, blk, 0, c->stream>>>(L, rl, n, rr, r, z); break;
+    default: fail(TT_IGA_ERR_ARG, "preconditioner: degree %d outside 1..7", p);
+  }
   TTI_LAUNCH();
 }
 template void precond_apply<double>(Ctx *, const double *, int, int, int, int, const double *, double *);

@@ -161,7 +161,8 @@ inline void DBuf::release() {
 }
 
 // Kernel families that can be timed live (tt_iga_profile_enable).
-enum ProfFamily { PROF_OFF = 0, PROF_LOCAL_BAND = 1, PROF_GEMM64 = 2, PROF_QR = 3, PROF_PRECOND = 4, PROF_CROSS = 5 };
+enum ProfFamily { PROF_OFF = 0, PROF_LOCAL_BAND = 1, PROF_GEMM64 = 2, PROF_QR = 3, PROF_PRECOND = 4, PROF_CROSS = 5,
+                  PROF_PCG_FUSED = 6 };
 
 // Records a CUDA event pair around the launches in its scope when the
 // context times this kernel family; `work` is the launch's algorithmic work

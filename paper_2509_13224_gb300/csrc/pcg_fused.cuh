@@ -1,0 +1,30 @@
+// Fused (single cooperative launch) PCG for one AMEn local system.
+#pragma once
+#include "common.cuh"
+
+namespace ttiga {
+
+template <typename T> struct PcgArgs {
+  const T *PhiL;  // [rl][Rl][rl]
+  const T *PhiR;  // [rr][Rr][rr]
+  const T *A;     // [Rl][n][2p+1][Rr]
+  const T *L;     // band Cholesky factors [n][p+1][rl*rr]
+  const T *b;     // right-hand side [rl][n][rr]
+  T *x, *r, *z, *pv, *q;  // solution and work vectors [rl][n][rr]
+  T *T1;          // [rl][n][rr][Rr]
+  T *T2;          // [Rl][rl][n][rr]
+  double *part;   // 3 * grid partial sums
+  struct Barrier *bar;
+  int *err;       // set to 1 when a grid barrier wait runs out
+  double *out;    // [0] iterations, [1] final ||r||^2
+  int rl, rr, Rl, Rr, n, p;
+  double tol2;    // stop when ||b - B x||^2 <= tol2
+  int maxit;
+};
+
+// Number of CTAs for the cooperative launch (all co-resident).
+template <typename T> int pcg_fused_grid(Ctx *c, const PcgArgs<T> &a);
+// Launch on the context stream; bar must hold 8 zeroed-or-stale bytes (reset here).
+template <typename T> void pcg_fused(Ctx *c, PcgArgs<T> a, int grid);
+
+}  // namespace ttiga

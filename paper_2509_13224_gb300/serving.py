@@ -1,0 +1,198 @@
+"""Serving loop for TT-IGA Poisson solves on one GPU (continuous batching).
+
+Requests (geometry, degree, resolution, tolerance) arrive open-loop.  A
+request is admitted as soon as a lane is free and its estimated device
+footprint fits the memory budget; admitted requests run concurrently, one per
+lane, each lane a host thread with its own library context and CUDA stream,
+so their kernels overlap on the device.  Requests that arrive while others
+run are admitted as lanes and memory free up.  Every request records its
+arrival, start and finish times; the session reports p50/p99 latency and
+DOFs/s.  Each solve's arithmetic is independent of the others (own context,
+deterministic reductions), so a result is the same alone and in the mix.
+
+All computation happens in libtt_iga.so; this module only schedules.
+"""
+import math
+import queue
+import threading
+import time
+
+import numpy as np
+
+from . import (FP64, MIXED_FP32, geom_desc, rhs_desc, solve_opts, tt_iga_assemble, tt_iga_ctx_create,
+               tt_iga_ctx_destroy, tt_iga_geom_destroy, tt_iga_geometry, tt_iga_solution_cores,
+               tt_iga_solution_destroy, tt_iga_solve, tt_iga_system_destroy)
+
+
+def footprint_bytes(n, p, rank=48, op_rank=24, rhs_rank=16):
+    """Conservative device footprint of one solve: TT cores of K, F and u, AMEn interfaces,
+    the fused-PCG work vectors and the cross fibre matrices (FP64 unless noted)."""
+    m = n - 2
+    b = 2 * p + 1
+    q = (n - p) * (p + 1)
+    k_cores = 3 * op_rank * op_rank * m * b
+    f_cores = 3 * rhs_rank * rhs_rank * m
+    u_cores = 3 * rank * rank * m
+    local = rank * rank * m
+    pcg = 5 * local + 2 * local * op_rank       # vectors + T1/T2
+    cross = 6 * q * 96 + 64 * q * 96            # fibre matrices + QR work
+    return 8 * (k_cores + f_cores + u_cores + pcg + cross) * 2 + (16 << 20)
+
+
+class Request:
+    def __init__(self, rid, geometry, p, n, tol, modes=(), arrival=0.0, precision=None, seed=0):
+        self.rid, self.geometry, self.p, self.n, self.tol = rid, geometry, int(p), int(n), float(tol)
+        self.modes = list(modes)
+        self.arrival = float(arrival)
+        self.precision = precision
+        self.seed = int(seed)
+        self.record = None
+
+
+class Server:
+    """lanes: concurrent solves; budget_bytes: device memory allowed for admitted requests."""
+
+    def __init__(self, device=0, lanes=4, budget_bytes=None, precision_policy="auto", keep_cores=False,
+                 cross_tol=1e-10, round_tol=1e-12):
+        import torch
+        self.device = device
+        self.lanes = int(lanes)
+        if budget_bytes is None:
+            free, _ = torch.cuda.mem_get_info(device)
+            budget_bytes = int(0.8 * free)
+        self.budget = int(budget_bytes)
+        self.in_use = 0
+        self.policy = precision_policy
+        self.keep_cores = keep_cores
+        self.cross_tol, self.round_tol = cross_tol, round_tol
+        self._cv = threading.Condition()
+
+    def _precision(self, req):
+        if req.precision is not None:
+            return req.precision
+        if self.policy == "fp64":
+            return FP64
+        if self.policy == "mixed":
+            return MIXED_FP32
+        return MIXED_FP32 if req.tol >= 1e-7 else FP64
+
+    def _run_one(self, ctx, req, t0):
+        rec = {"rid": req.rid, "n": req.n, "p": req.p, "tol": req.tol, "dofs": req.n ** 3,
+               "arrival": req.arrival}
+        prec = self._precision(req)
+        rec["precision"] = "fp64" if prec == FP64 else "mixed_fp32"
+        rec["start"] = time.perf_counter() - t0
+        g = s = u = None
+        try:
+            g = tt_iga_geometry(ctx, geom_desc(req.geometry, req.p, req.n, cross_tol=self.cross_tol, seed=req.seed))
+            s = tt_iga_assemble(ctx, g, [rhs_desc(req.modes)], round_tol=self.round_tol)
+            u, st = tt_iga_solve(ctx, s, solve_opts(tol=req.tol, precision=prec), allow_not_converged=True)
+            rec.update({"status": 0 if st["converged"] else -4, "rel_residual": st["rel_residual"],
+                        "ranks": st["ranks"], "sweeps": st["sweeps"]})
+            if self.keep_cores:
+                rec["cores"] = [c.copy() for c in tt_iga_solution_cores(ctx, u)]
+        except Exception as exc:  # a failed request is reported, the server keeps running
+            rec.update({"status": getattr(exc, "code", -3), "error": str(exc)})
+        finally:
+            if u is not None:
+                tt_iga_solution_destroy(u)
+            if s is not None:
+                tt_iga_system_destroy(s)
+            if g is not None:
+                tt_iga_geom_destroy(g)
+        rec["end"] = time.perf_counter() - t0
+        rec["latency"] = rec["end"] - rec["arrival"]
+        return rec
+
+    def serve(self, requests, realtime=True):
+        """Run an open-loop session; requests carry arrival times (s from the session start).
+        Returns (records in completion order, summary dict)."""
+        import torch
+        pending = sorted(requests, key=lambda r: r.arrival)
+        arrived = queue.Queue()
+        records = []
+        lock = threading.Lock()
+        t0 = time.perf_counter()
+        done_arriving = threading.Event()
+
+        def arrivals():
+            for r in pending:
+                if realtime:
+                    dt = r.arrival - (time.perf_counter() - t0)
+                    if dt > 0:
+                        time.sleep(dt)
+                arrived.put(r)
+            done_arriving.set()
+
+        waiting = []  # arrived but not admitted, FIFO
+
+        def admit():
+            """Next admissible request (FIFO, footprint within budget), or None."""
+            with self._cv:
+                while True:
+                    while True:
+                        try:
+                            waiting.append(arrived.get_nowait())
+                        except queue.Empty:
+                            break
+                    if waiting:
+                        need = footprint_bytes(waiting[0].n, waiting[0].p)
+                        if self.in_use + need <= self.budget or self.in_use == 0:
+                            req = waiting.pop(0)
+                            self.in_use += need
+                            return req, need
+                    elif done_arriving.is_set() and arrived.empty():
+                        return None, 0
+                    self._cv.wait(timeout=0.002)
+
+        def lane():
+            torch.cuda.set_device(self.device)
+            ctx = tt_iga_ctx_create(None, self.device)
+            try:
+                while True:
+                    req, need = admit()
+                    if req is None:
+                        return
+                    rec = self._run_one(ctx, req, t0)
+                    with self._cv:
+                        self.in_use -= need
+                        self._cv.notify_all()
+                    with lock:
+                        records.append(rec)
+            finally:
+                tt_iga_ctx_destroy(ctx)
+
+        ta = threading.Thread(target=arrivals, daemon=True)
+        ta.start()
+        threads = [threading.Thread(target=lane, daemon=True) for _ in range(self.lanes)]
+        for t in threads:
+            t.start()
+        for t in threads:
+            t.join()
+        ta.join()
+        wall = time.perf_counter() - t0
+        return records, summarize(records, wall)
+
+
+def summarize(records, wall):
+    ok = [r for r in records if r.get("status") == 0]
+    lat = np.array([r["latency"] for r in ok]) if ok else np.array([math.nan])
+    dofs = sum(r["dofs"] for r in ok)
+    span = (max(r["end"] for r in ok) - min(r["arrival"] for r in ok)) if ok else math.nan
+    return {"requests": len(records), "ok": len(ok), "p50_ms": float(np.percentile(lat, 50) * 1e3),
+            "p99_ms": float(np.percentile(lat, 99) * 1e3), "dofs_per_s": dofs / span if ok else 0.0,
+            "wall_s": wall}
+
+
+def synthetic_stream(count, rate_hz, seed, n_lo=32, n_hi=1024, tols=(1e-6, 1e-8)):
+    """Open-loop request stream with geometry drawn as in the batched workload."""
+    import synthetic
+    times = synthetic.poisson_arrivals(rate_hz, count, seed)
+    reqs = []
+    g = synthetic.rng(seed + 1)
+    for k in range(count):
+        inst = synthetic.random_instance(seed * 100_000 + k, n_lo=n_lo, n_hi=n_hi)
+        tol = float(tols[int(g.integers(0, len(tols)))])
+        reqs.append(Request(k, inst["geometry"], inst["p"], inst["n"], tol, modes=inst["rhs"][0],
+                            arrival=float(times[k]), seed=inst["seed"]))
+    return reqs
