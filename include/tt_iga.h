@@ -328,6 +328,27 @@ int tt_iga_qr(tt_iga_ctx *ctx, int m, int k, const double *A, int lda, double *Q
 /* SVD of a small square matrix A (device, k x k): A = U diag(s) V^T by
  * one-sided Jacobi, FP64, singular values descending.  k <= 256. */
 int tt_iga_svd_small(tt_iga_ctx *ctx, int k, const double *A, double *U, double *s, double *V);
+/* Allocation-free SVD (no counterpart in the paper; a library service).
+ *
+ * Same result as tt_iga_svd_small, for callers that cannot allocate device
+ * memory: code that runs while a CUDA stream is being captured into a graph
+ * (an allocation there either breaks the capture or becomes part of the
+ * graph), and hosts that reserve all device memory up front and forbid other
+ * allocations.  It takes no context (creating one allocates) and runs on
+ * `stream` (a cudaStream_t; NULL is the legacy default stream).  A, U, s, V
+ * are caller-owned device buffers as in tt_iga_svd_small.
+ *
+ * Scratch: a fixed 1 MiB device array inside the library (two 256 x 256 FP64
+ * panels), held by every GPU that loads the library until the process exits.
+ * Limit: k <= 256; larger k returns TT_IGA_ERR_TOO_LARGE and launches nothing.
+ * The first call on a device looks up the array's device address once
+ * (cudaGetSymbolAddress, no allocation); make that first call before any
+ * stream capture.  All calls share the array: calls whose kernels overlap on
+ * the GPU (different streams, no ordering between them) race on it and must
+ * not be issued.  Returns TT_IGA_OK once the kernel is enqueued; results are
+ * valid after `stream` is synchronised.  No error message is recorded
+ * (there is no context); the return code says what went wrong. */
+int tt_iga_svd_small_noalloc(void *stream, int k, const double *A, double *U, double *s, double *V);
 /* Maximum-volume row selection (Goreinov et al. 2010) of a tall matrix U
  * (device, m x r): device outputs rows[r] (int32) and B = U U[rows,:]^{-1}
  * (device, m x r).  Stops when max |B| <= 1 + delta or after maxit swaps. */

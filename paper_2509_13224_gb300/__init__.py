@@ -133,6 +133,7 @@ _SIGS = {
                                     ctypes.POINTER(ctypes.c_int * 4)]),
     "tt_iga_qr": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, _vp, ctypes.c_int, _vp, _vp]),
     "tt_iga_svd_small": (ctypes.c_int, [_vp, ctypes.c_int, _vp, _vp, _vp, _vp]),
+    "tt_iga_svd_small_noalloc": (ctypes.c_int, [_vp, ctypes.c_int, _vp, _vp, _vp, _vp]),
     "tt_iga_maxvol": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, _vp, ctypes.c_double, ctypes.c_int, _vp, _vp]),
 }
 for _name, (_res, _args) in _SIGS.items():
@@ -495,6 +496,16 @@ def tt_iga_qr(ctx, A, Q, R):
 
 def tt_iga_svd_small(ctx, A, U, s, V):
     _check(ctx, _lib.tt_iga_svd_small(ctx, int(A.shape[0]), _ptr(A), _ptr(U), _ptr(s), _ptr(V)))
+
+
+def tt_iga_svd_small_noalloc(stream, A, U, s, V):
+    """Allocation-free SVD on `stream` (torch.cuda.Stream, raw handle or None for the legacy default stream).
+
+    Returns the status code instead of raising, so callers can see ERR_TOO_LARGE for k > 256."""
+    h = None
+    if stream is not None:
+        h = stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+    return int(_lib.tt_iga_svd_small_noalloc(h, int(A.shape[0]), _ptr(A), _ptr(U), _ptr(s), _ptr(V)))
 
 
 def tt_iga_maxvol(ctx, U, rows, B, delta=1e-2, maxit=100):

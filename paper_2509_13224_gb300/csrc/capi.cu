@@ -526,6 +526,14 @@ int tt_iga_svd_small(tt_iga_ctx *c, int k, const double *A, double *U, double *s
   API_CATCH(c)
 }
 
+int tt_iga_svd_small_noalloc(void *stream, int k, const double *A, double *U, double *s, double *V) {
+  try {
+    return svd_small_noalloc(static_cast<cudaStream_t>(stream), k, A, U, s, V);
+  } catch (...) {
+    return TT_IGA_ERR_CUDA;
+  }
+}
+
 int tt_iga_maxvol(tt_iga_ctx *c, int m, int r, const double *U, double delta, int maxit, int *rows, double *B) {
   if (!c || !U || !rows || !B) return TT_IGA_ERR_ARG;
   API_TRY

@@ -5,6 +5,7 @@
 // these kernels, so they keep FP64 work at its algorithmic minimum.
 #include <algorithm>
 #include <cfloat>
+#include <mutex>
 
 #include "linalg.cuh"
 
@@ -531,6 +532,42 @@ void svd_small(Ctx *c, int k, const double *A, double *U, double *s, double *V) 
   }
   k_jacobi_svd<<<1, 256, bytes, c->stream>>>(k, A, U, s, V, Wg.d(), Vg.d(), use_smem, c->dstatus);
   TTI_LAUNCH();
+}
+
+// ------------------------------------------- allocation-free SVD entry point
+//
+// Fixed scratch of the one-sided Jacobi SVD for callers that cannot allocate
+// device memory: two 256 x 256 FP64 panels (1 MiB) resident on every device
+// that loads the library, shared by all calls (each call overwrites both
+// panels before reading them, so nothing needs clearing between calls).
+
+static __device__ __align__(256) double g_svd_scratch[2 * 256 * 256];
+
+namespace {
+constexpr int kMaxDevices = 64;
+std::mutex g_scratch_mu;
+double *g_scratch_ptr[kMaxDevices] = {nullptr};
+}  // namespace
+
+int svd_small_noalloc(cudaStream_t stream, int k, const double *A, double *U, double *s, double *V) {
+  if (k < 1 || k > 256) return TT_IGA_ERR_TOO_LARGE;
+  if (!A || !U || !s || !V) return TT_IGA_ERR_ARG;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return TT_IGA_ERR_CUDA;
+  double *scratch;
+  {
+    std::lock_guard<std::mutex> lock(g_scratch_mu);
+    if (!g_scratch_ptr[dev]) {
+      // host code only holds a stand-in for the symbol: ask the runtime for its device address
+      void *p = nullptr;
+      if (cudaGetSymbolAddress(&p, g_svd_scratch) != cudaSuccess || !p) return TT_IGA_ERR_CUDA;
+      g_scratch_ptr[dev] = static_cast<double *>(p);
+    }
+    scratch = g_scratch_ptr[dev];
+  }
+  k_jacobi_svd<<<1, 256, 0, stream>>>(k, A, U, s, V, scratch, scratch + 256 * 256, 0, nullptr);
+  g_launches.fetch_add(1, std::memory_order_relaxed);
+  return cudaGetLastError() == cudaSuccess ? TT_IGA_OK : TT_IGA_ERR_CUDA;
 }
 
 // ----------------------------------------------------------------- maxvol
