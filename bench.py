@@ -45,10 +45,15 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default=WORKLOAD)
-    ap.add_argument("--profile-family", type=int, default=1,
-                    help="kernel family timed live for the roofline (1 band stage of the local matvec)")
+    ap.add_argument("--profile-family", type=int, default=6,
+                    help="kernel family timed live for the roofline (6: fused PCG of the AMEn local solves)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-mixed", action="store_true")
+    ap.add_argument("--no-extra", action="store_true", help="skip the twisted-annulus n=512 side measurement")
+    ap.add_argument("--batch-instances", type=int, default=64, help="instances in the batched measurement (0 skips)")
+    ap.add_argument("--serve-requests", type=int, default=32, help="requests in the serving session (0 skips)")
+    ap.add_argument("--serve-rate", type=float, default=40.0, help="open-loop arrival rate (requests/s)")
+    ap.add_argument("--serve-nmax", type=int, default=256, help="largest n per direction in the serving stream")
     return ap.parse_args()
 
 
@@ -270,6 +275,34 @@ def run_ours(args, rank, world):
                  "ranks": infom.get("ranks"), "local_matvecs": infom.get("local_matvecs"),
                  "local_matvecs_fp64": infom.get("local_matvecs_fp64")}
 
+    # side measurement: the non-separable twisted annulus at p = 3, n = 512 (134M DOFs)
+    extra = None
+    if not args.no_extra and args.workload == WORKLOAD:
+        wx = synthetic.WORKLOADS["twisted_annulus_p3_n512"]
+        gx = tt.geom_desc(wx["geometry"], wx["p"], wx["n"], cross_tol=wx["cross_tol"], seed=rank)
+        extra = {"workload": "twisted_annulus_p3_n512", "dofs": wx["n"] ** 3}
+        for name, prec in (("fp64", tt.FP64), ("mixed_fp32", tt.MIXED_FP32)):
+            ts = []
+            for rep in range(3):
+                with torch.cuda.stream(stream):
+                    flush.zero_()
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                g = tt.tt_iga_geometry(ctx, gx)
+                s = tt.tt_iga_assemble(ctx, g, [tt.rhs_desc()], round_tol=wx["round_tol"])
+                u, st = tt.tt_iga_solve(ctx, s, tt.solve_opts(tol=TOL, precision=prec))
+                e1.record(stream)
+                e1.synchronize()
+                if rep > 0:
+                    ts.append(e0.elapsed_time(e1))
+                tt.tt_iga_solution_destroy(u)
+                tt.tt_iga_system_destroy(s)
+                tt.tt_iga_geom_destroy(g)
+            ms = max_over_ranks(statistics.mean(ts), world)
+            extra[name] = {"value": world * wx["n"] ** 3 / (ms / 1e3), "ms_per_step": ms,
+                           "rel_residual": st["rel_residual"], "ranks": st["ranks"], "sweeps": st["sweeps"]}
+
     # end to end through the C ABI: host descriptors in, compressed solution cores read back to pinned host memory
     e2e_times = []
     hbuf = None
@@ -292,6 +325,35 @@ def run_ours(args, rank, world):
     h2d = len(bytes(gdesc)) + sum(len(bytes(r_)) for r_ in rhs) + len(bytes(tt.solve_opts()))
 
     tt.tt_iga_ctx_destroy(ctx)
+
+    # batched: uneven random instances (geometry, p, n in [32, 256], 1-8 right-hand sides), autotuned lanes
+    batched = None
+    if args.batch_instances > 0:
+        inst = [synthetic.random_instance(1 + k + 1000 * rank) for k in range(args.batch_instances)]
+        items, keep = tt.batch_items(inst, tol=TOL, precision=tt.MIXED_FP32)
+        lanes, ms_tune, _ = tt.tt_iga_batch_autotune(items, [1, 4, 8])
+        out = {}
+        for name, prec in (("mixed_fp32", tt.MIXED_FP32), ("fp64", tt.FP64)):
+            items, keep = tt.batch_items(inst, tol=TOL, precision=prec)
+            code, res, ms = tt.tt_iga_batch_solve(items, lanes, device=local)
+            dofs_b = sum(r["dofs"] for r in res if r["status"] == 0)
+            out[name] = {"value": dofs_b / (ms / 1e3), "wall_ms": ms, "ok": sum(r["status"] == 0 for r in res),
+                         "worst_residual": max(r["rel_residual_max"] for r in res)}
+        batched = {"instances": args.batch_instances, "lanes": lanes, "rhs_total": sum(len(i["rhs"]) for i in inst),
+                   "dofs_total": sum(i["n"] ** 3 * len(i["rhs"]) for i in inst), **out}
+
+    # serving: open-loop Poisson arrivals, admission by footprint, continuous batching over lanes
+    serving = None
+    if args.serve_requests > 0:
+        from paper_2509_13224_gb300.serving import Server, synthetic_stream
+        serving = {"requests": args.serve_requests, "rate_hz": args.serve_rate, "n_range": [32, args.serve_nmax]}
+        for policy in ("mixed", "fp64", "auto"):
+            reqs = synthetic_stream(args.serve_requests, args.serve_rate, seed=11 + rank, n_lo=32, n_hi=args.serve_nmax)
+            srv = Server(device=local, lanes=4, precision_policy=policy)
+            recs, summ = srv.serve(reqs)
+            serving[policy] = {"p50_ms": summ["p50_ms"], "p99_ms": summ["p99_ms"], "dofs_per_s": summ["dofs_per_s"],
+                               "ok": summ["ok"]}
+
     if rank != 0:
         return
     roof = None
@@ -301,7 +363,8 @@ def run_ours(args, rank, world):
         roof = {"bound": "alu", "achieved": achieved, "peak": FP64_ALU_PEAK_TFLOPS, "unit": "TFLOP/s",
                 "frac": achieved / FP64_ALU_PEAK_TFLOPS, "traffic": None,
                 "kernel": {1: "k_band_right (local matvec band stage, FP64)", 2: "k_gemm<double>",
-                           3: "k_qr_panel"}.get(args.profile_family, str(args.profile_family)),
+                           3: "k_qr_panel", 6: "k_pcg_fused<double> (AMEn local PCG, one launch per solve)"}.get(
+                               args.profile_family, str(args.profile_family)),
                 "launches": n_k, "kernel_ms_per_step": ms_k / args.steps,
                 "share_of_step": ms_k / args.steps / ms64, "flops_per_launch": flops_k / n_k}
     line = {"metric": METRIC, "value": world * dofs / (ms64_max / 1e3), "unit": "DOFs/s", "n_gpus": world,
@@ -313,6 +376,7 @@ def run_ours(args, rank, world):
             "e2e": {"value": world * dofs / e2e_s, "unit": "DOFs/s", "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h},
             "gpu_launches": launches, "clocks": clk, "roofline": roof, "cpu_baseline": base, "mixed": mixed,
+            "twisted_n512": extra, "batched": batched, "serving": serving,
             "solve": {"rel_residual": info64.get("rel_residual"), "sweeps": info64.get("sweeps"),
                       "ranks": info64.get("ranks"), "op_ranks": info64.get("op_ranks"),
                       "local_matvecs": info64.get("local_matvecs"), "solve_ms": info64.get("ms_total")}}

@@ -90,7 +90,7 @@ unsigned long long tt_iga_launch_count(void);
 /* Live timing of one kernel family on the context stream, for roofline
  * reporting: every launch of the family is bracketed by a CUDA event pair.
  * family: 0 off, 1 band stage of the AMEn local matvec, 2 FP64 GEMM,
- * 3 Householder QR panel.  Enabling resets the record. */
+ * 3 Householder QR panel, 6 fused local PCG.  Enabling resets the record. */
 int tt_iga_profile_enable(tt_iga_ctx *ctx, int family);
 /* Synchronise and return the summed event time (ms), the number of timed
  * launches and their summed algorithmic FLOPs. */
@@ -320,6 +320,13 @@ int tt_iga_load_core(tt_iga_ctx *ctx, int n, int p, int nq, const double *wts, c
  * cores.  max_rank caps the result (0: none). */
 int tt_iga_round(tt_iga_ctx *ctx, const int nm[3], const int r[4], const double *const cores[3],
                  double eps, int max_rank, double *const out_cores[3], int out_r[4]);
+
+/* Dense FP64 GEMM used by the rank-by-rank contractions of the local systems:
+ * C = alpha op(A) op(B) + beta C, row-major, op(X) = X or X^T (ta, tb).
+ * op(A) is m x k with element (i, l) at A[i*lda + l] (ta = 0) or A[l*lda + i]
+ * (ta = 1); likewise B (k x n) and C (m x n, ldc).  All device pointers. */
+int tt_iga_gemm_f64(tt_iga_ctx *ctx, int ta, int tb, int m, int n, int k, double alpha, const double *A, int lda,
+                    const double *B, int ldb, double beta, double *C, int ldc);
 
 /* Tall-skinny Householder QR, FP64: A (device, m x k row-major, lda >= k)
  * = Q R with Q (device, m x k, ld k) orthonormal columns and R (device, k x k

@@ -131,6 +131,9 @@ _SIGS = {
     "tt_iga_round": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_int * 3), ctypes.POINTER(ctypes.c_int * 4),
                                     ctypes.POINTER(_vp * 3), ctypes.c_double, ctypes.c_int, ctypes.POINTER(_vp * 3),
                                     ctypes.POINTER(ctypes.c_int * 4)]),
+    "tt_iga_gemm_f64": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                       ctypes.c_double, _vp, ctypes.c_int, _vp, ctypes.c_int, ctypes.c_double, _vp,
+                                       ctypes.c_int]),
     "tt_iga_qr": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, _vp, ctypes.c_int, _vp, _vp]),
     "tt_iga_svd_small": (ctypes.c_int, [_vp, ctypes.c_int, _vp, _vp, _vp, _vp]),
     "tt_iga_svd_small_noalloc": (ctypes.c_int, [_vp, ctypes.c_int, _vp, _vp, _vp, _vp]),
@@ -208,7 +211,7 @@ def solve_opts(tol=1e-8, precision=FP64, max_sweeps=0, kickrank=0, max_rank=0, l
                verbose=False):
     o = SolveOpts()
     o.tol, o.precision, o.max_sweeps, o.kickrank = tol, precision, max_sweeps, kickrank
-    o.max_rank, o.local_maxit, o.rhs_index, o.verbose = max_rank, local_maxit, rhs_index, int(bool(verbose))
+    o.max_rank, o.local_maxit, o.rhs_index, o.verbose = max_rank, local_maxit, rhs_index, int(verbose)
     return o
 
 
@@ -487,6 +490,14 @@ def tt_iga_round(ctx, cores, eps, max_rank=0):
         cnt = rout[k] * nm[k] * rout[k + 1]
         res.append(outs[k].reshape(-1)[:cnt].reshape(rout[k], nm[k], rout[k + 1]))
     return res, [rout[k] for k in range(4)]
+
+
+def tt_iga_gemm_f64(ctx, ta, tb, alpha, A, B, beta, C):
+    """C = alpha op(A) op(B) + beta C on float64 CUDA tensors (row-major, contiguous)."""
+    m, n = int(C.shape[0]), int(C.shape[1])
+    k = int(A.shape[0] if ta else A.shape[1])
+    _check(ctx, _lib.tt_iga_gemm_f64(ctx, int(ta), int(tb), m, n, k, alpha, _ptr(A), int(A.stride(0)), _ptr(B),
+                                     int(B.stride(0)), beta, _ptr(C), int(C.stride(0))))
 
 
 def tt_iga_qr(ctx, A, Q, R):

@@ -134,6 +134,7 @@ struct Amen {
   Work<float> w32;
   tt_iga_stats st{};
   double last_local = 0.0;
+  bool last_pcg_converged = false;
   // scratch scalars on the device: [0] rz, [1] pq, [2] rz_new, [8..] partials
   DBuf scal;
 
@@ -229,30 +230,62 @@ struct Amen {
   // PCG on B d = r (type T), d starts at zero; one cooperative launch for all
   // iterations.  Absolute tolerance tol on ||r - B d||.  Returns iterations.
   template <typename T>
-  int pcg(int k, const T *PhiLk, const T *PhiRk, const T *Ak, const T *L, const T *b, T *x, double tol, int maxit) {
+  int pcg(int k, const T *PhiLk, const T *PhiRk, const T *Ak, const float *L, const T *b, T *x, double tol, int maxit) {
     const long long N = (long long)rl(k) * n(k) * rr(k);
     PcgArgs<T> a{};
-    a.PhiL = PhiLk; a.PhiR = PhiRk; a.A = Ak; a.L = L; a.b = b; a.x = x;
+    a.PhiL = PhiLk; a.PhiR = PhiRk; a.A = Ak; a.Lf = L; a.b = b; a.x = x;
     a.rl = rl(k); a.rr = rr(k); a.Rl = R[k]; a.Rr = R[k + 1]; a.n = n(k); a.p = S->p;
     a.tol2 = tol * tol;
     a.maxit = maxit;
     const int grid = pcg_fused_grid<T>(c, a);
-    DBuf vec(c, 4 * N * sizeof(T)), t1(c, (size_t)a.rl * a.n * a.rr * a.Rr * sizeof(T)),
+    DBuf vec(c, 5 * N * sizeof(T)), t1(c, (size_t)a.rl * a.n * a.rr * a.Rr * sizeof(T)),
         t2(c, (size_t)a.Rl * a.rl * a.n * a.rr * sizeof(T)), aux(c, (3 * (size_t)grid + 8) * sizeof(double));
-    a.r = vec.as<T>(); a.z = a.r + N; a.pv = a.z + N; a.q = a.pv + N;
+    a.r = vec.as<T>(); a.z = a.r + N; a.pv = a.z + N; a.pv2 = a.pv + N; a.q = a.pv2 + N;
     a.T1 = t1.as<T>(); a.T2 = t2.as<T>();
     a.part = aux.d();
     a.out = aux.d() + 3 * grid;
     a.bar = reinterpret_cast<Barrier *>(aux.d() + 3 * grid + 2);
     a.err = reinterpret_cast<int *>(aux.d() + 3 * grid + 3);
     c->zero(a.err, sizeof(int));
+    DBuf trace;
+    if (o.verbose >= 2) {
+      a.trace_cap = 2 + 4 * 64;
+      trace = DBuf(c, a.trace_cap * sizeof(unsigned long long));
+      a.trace = trace.as<unsigned long long>();
+    }
     pcg_fused<T>(c, a, grid);
     double hout[4];
     c->d2h(hout, a.out, 4 * sizeof(double));
+    if (o.verbose >= 2) {
+      std::vector<unsigned long long> tr(a.trace_cap);
+      c->d2h(tr.data(), a.trace, tr.size() * sizeof(unsigned long long));
+      const int iters = std::min((int)hout[0], 64);
+      double ph[4] = {0, 0, 0, 0};
+      for (int i = 0; i < iters; ++i) {
+        unsigned long long prev = tr[1 + 4 * i];
+        for (int q = 0; q < 4; ++q) {
+          ph[q] += (double)(tr[2 + 4 * i + q] - prev);
+          prev = tr[2 + 4 * i + q];
+        }
+      }
+      fprintf(stderr, "[tt_iga pcg] core %d %s grid %d n %d rl %d rr %d R %d/%d it %d init %.1f us, per iteration A %.1f B %.1f C %.1f E %.1f us\n",
+              k, sizeof(T) == 8 ? "fp64" : "fp32", grid, a.n, a.rl, a.rr, a.Rl, a.Rr, (int)hout[0],
+              (tr[1] - tr[0]) * 1e-3, iters ? ph[0] / iters * 1e-3 : 0.0, iters ? ph[1] / iters * 1e-3 : 0.0,
+              iters ? ph[2] / iters * 1e-3 : 0.0, iters ? ph[3] / iters * 1e-3 : 0.0);
+    }
     int err = 0;
     memcpy(&err, &hout[3], sizeof(int));
     if (err) fail(TT_IGA_ERR_TIMEOUT, "pcg: a grid barrier wait ran out");
     const int it = (int)hout[0];
+    last_pcg_converged = (it < maxit) && hout[1] <= a.tol2;
+    {
+      // algorithmic FLOPs per PCG iteration: right-interface, band and left-interface stages
+      // of the local matvec plus the two band triangular solves of the preconditioner
+      const double rl_ = a.rl, rr_ = a.rr, n_ = a.n, Rl_ = a.Rl, Rr_ = a.Rr, b_ = 2.0 * a.p + 1.0;
+      const double f_iter = 2.0 * rl_ * n_ * rr_ * Rr_ * rr_ + 2.0 * Rl_ * rl_ * n_ * rr_ * b_ * Rr_ +
+                            2.0 * rl_ * n_ * rr_ * Rl_ * rl_ + 4.0 * rl_ * rr_ * n_ * (a.p + 1) + 10.0 * N;
+      prof_set_last_work(c, PROF_PCG_FUSED, f_iter * it);
+    }
     st.local_matvecs += it;
     if (sizeof(T) == 8) st.local_matvecs_fp64 += it;
     return it;
@@ -270,12 +303,16 @@ struct Amen {
     const int maxit = o.local_maxit;
     const size_t Lsz = (size_t)n(k) * (S->p + 1) * rl(k) * rr(k);
     if (o.precision == TT_IGA_FP64) {
-      DBuf L(c, Lsz * sizeof(double)), d(c, N * sizeof(double));
-      precond_build<double>(c, PhiL[k].d(), rl(k), A[k], PhiR[k].d(), rr(k), L.d());
+      // the preconditioner's factors are computed in FP64 and applied in FP32 (see pcg_fused.cu)
+      DBuf L(c, Lsz * sizeof(float)), d(c, N * sizeof(double));
+      precond_build<float>(c, PhiL[k].d(), rl(k), A[k], PhiR[k].d(), rr(k), L.as<float>());
       // correction form: B d = r, x += d, checked in FP64
+      // correction form B d = r; in FP64 the PCG recurrence residual is the residual of
+      // x + d to working accuracy, so an explicit check is only needed when PCG stopped early
       for (int rep = 0; rep < 3; ++rep) {
-        pcg<double>(k, PhiL[k].d(), PhiR[k].d(), A[k].A, L.d(), rbuf.d(), d.d(), 0.5 * tol_abs, maxit);
+        pcg<double>(k, PhiL[k].d(), PhiR[k].d(), A[k].A, L.as<float>(), rbuf.d(), d.d(), 0.5 * tol_abs, maxit);
         axpy<double>(c, N, 1.0, d.d(), x);
+        if (last_pcg_converged) break;
         if (residual64(k, rhs, x, rbuf.d()) <= tol_abs) break;
       }
     } else {
@@ -313,13 +350,7 @@ struct Amen {
     c->d2h(s.data(), Sv.d(), b * sizeof(double));
     // SVt[j][l] = s_j V[l][j]
     DBuf SVt(c, (size_t)b * b * sizeof(double));
-    {
-      std::vector<double> hv(b * b), h(b * b);
-      c->d2h(hv.data(), V.d(), hv.size() * sizeof(double));
-      for (int j = 0; j < b; ++j)
-        for (int l = 0; l < b; ++l) h[j * b + l] = s[j] * hv[l * b + j];
-      c->h2d(SVt.d(), h.data(), h.size() * sizeof(double));
-    }
+    svt(c, Sv.d(), V.d(), b, b, SVt.d());
     DBuf QU(c, (size_t)rows * b * sizeof(double));
     gemm<double>(c, false, false, rows, b, b, 1.0, Q.d(), b, 0, Ur.d(), b, 0, 0.0, QU.d(), b, 0, 1);
     // numerical rank
@@ -422,30 +453,48 @@ struct Amen {
     int status = TT_IGA_ERR_NOT_CONVERGED;
     for (int sweep = 0; sweep < o.max_sweeps; ++sweep) {
       double maxloc = 0.0;
+      // stage timer for verbose >= 2 (synchronises, diagnosis only)
+      auto now_ms = [&]() {
+        if (o.verbose >= 2) c->sync();
+        return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now().time_since_epoch()).count();
+      };
+      double t_solve = 0, t_trunc = 0, t_iface = 0;
       for (int k = 0; k < 3; ++k) {
         const long long N = (long long)rl(k) * n(k) * rr(k);
         DBuf rhs(c, N * sizeof(double)), x(c, N * sizeof(double));
+        const double t0 = now_ms();
         rhs_local(c, w64, PsiL[k].d(), rl(k), F.core[k].d(), f[k], n(k), f[k + 1], PsiR[k].d(), rr(k), rhs.d());
         TTI_CUDA(cudaMemcpyAsync(x.d(), u.core[k].d(), N * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
         const double r0 = local_solve(k, rhs.d(), x.d(), tol_solve);
         maxloc = std::max(maxloc, r0 / Fnorm);
+        const double t1 = now_ms();
+        t_solve += t1 - t0;
         if (k < 2) {
           truncate_enrich(k, rhs.d(), x.d(), tol_trunc);
+          const double t2 = now_ms();
+          t_trunc += t2 - t1;
           left_interfaces(k);
+          t_iface += now_ms() - t2;
         } else {
           u.core[2] = std::move(x);
           last_core_z(u.core[2].d());
         }
       }
       // backward orthogonalisation of u and z, refresh right interfaces
+      const double tb0 = now_ms();
       for (int k = 2; k >= 1; --k) {
         orth_right_step(c, u, k);
         if (o.kickrank > 0) orth_right_step(c, z, k);
         right_interfaces(k);
       }
+      const double tb1 = now_ms();
       st.sweeps = sweep + 1;
       last_local = maxloc;
       const double res = exact_residual();
+      if (o.verbose >= 2)
+        fprintf(stderr, "[tt_iga amen] sweep %d stages: local solves %.2f ms, truncation+enrichment %.2f ms, "
+                        "left interfaces %.2f ms, backward pass %.2f ms, exact residual %.2f ms\n",
+                sweep + 1, t_solve, t_trunc, t_iface, tb1 - tb0, now_ms() - tb1);
       st.rel_residual = res;
       st.local_residual = maxloc;
       if (o.verbose)

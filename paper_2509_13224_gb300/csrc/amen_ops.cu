@@ -158,7 +158,22 @@ __global__ void k_band_cholesky(const double *__restrict__ Pm, int rl, int n, in
 #pragma unroll
       for (int k = 0; k <= PB; ++k) win[q][k] = 0.0;
     bool bad = false;
+    // symmetrised band entries of a row: A(i, i-PB+k) for k <= PB (loaded one row ahead)
+    auto load_row = [&](int i, double *out) {
+#pragma unroll
+      for (int k = 0; k < PB; ++k) {
+        const int j = i - PB + k;
+        out[k] = (j >= 0) ? 0.5 * (Pp[((long long)i * b + k) * rr] + Pp[((long long)j * b + (2 * PB - k)) * rr]) : 0.0;
+      }
+      out[PB] = Pp[((long long)i * b + PB) * rr];
+    };
+    double nxt[PB + 1];
+    load_row(0, nxt);
     for (int i = 0; i < n; ++i) {
+      double cur[PB + 1];
+#pragma unroll
+      for (int k = 0; k <= PB; ++k) cur[k] = nxt[k];
+      if (i + 1 < n) load_row(i + 1, nxt);
       double row[PB + 1];
 #pragma unroll
       for (int k = 0; k < PB; ++k) {
@@ -167,12 +182,12 @@ __global__ void k_band_cholesky(const double *__restrict__ Pm, int rl, int n, in
           row[k] = 0.0;
           continue;
         }
-        double sv = 0.5 * (Pp[((long long)i * b + k) * rr] + Pp[((long long)j * b + (2 * PB - k)) * rr]);
+        double sv = cur[k];
 #pragma unroll
         for (int mm = 0; mm < k; ++mm) sv -= row[mm] * win[k][mm + PB - k];
         row[k] = sv * win[k][PB];
       }
-      double sd = Pp[((long long)i * b + PB) * rr];
+      double sd = cur[PB];
 #pragma unroll
       for (int mm = 0; mm < PB; ++mm) sd -= row[mm] * row[mm];
       if (!(sd > 0.0)) {

@@ -128,7 +128,7 @@ int tt_iga_ctx_memory(const tt_iga_ctx *c, size_t *in_use, size_t *peak) {
 unsigned long long tt_iga_launch_count(void) { return ttiga::g_launches.load(); }
 
 int tt_iga_profile_enable(tt_iga_ctx *c, int family) {
-  if (!c || family < 0 || family > 5) return TT_IGA_ERR_ARG;
+  if (!c || family < 0 || family > 6) return TT_IGA_ERR_ARG;
   API_TRY
   c->sync();
   c->prof_family = family;
@@ -504,6 +504,16 @@ int tt_iga_round(tt_iga_ctx *c, const int nm[3], const int r[4], const double *c
     TTI_CUDA(cudaMemcpyAsync(out_cores[k], x.core[k].get(), x.core_elems(k) * sizeof(double),
                              cudaMemcpyDeviceToDevice, c->stream));
   for (int k = 0; k < 4; ++k) out_r[k] = x.r[k];
+  c->sync();
+  return TT_IGA_OK;
+  API_CATCH(c)
+}
+
+int tt_iga_gemm_f64(tt_iga_ctx *c, int ta, int tb, int m, int n, int k, double alpha, const double *A, int lda,
+                    const double *B, int ldb, double beta, double *C, int ldc) {
+  if (!c || !C || (k > 0 && (!A || !B)) || m < 0 || n < 0 || k < 0 || ldc < n) return TT_IGA_ERR_ARG;
+  API_TRY
+  gemm<double>(c, ta != 0, tb != 0, m, n, k, alpha, A, lda, 0, B, ldb, 0, beta, C, ldc, 0, 1);
   c->sync();
   return TT_IGA_OK;
   API_CATCH(c)

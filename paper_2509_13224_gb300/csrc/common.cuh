@@ -187,6 +187,12 @@ struct ProfScope {
   }
 };
 
+// Set the work of the most recent timed launch of `family` (when the work is
+// only known after the launch, e.g. an iteration count read back by the host).
+inline void prof_set_last_work(Ctx *c, int family, double work) {
+  if (c->prof_family == family && !c->prof_work.empty()) c->prof_work.back() = work;
+}
+
 inline int cdiv(long long a, long long b) { return (int)((a + b - 1) / b); }
 inline unsigned grid1d(long long n, int threads, int cap = 152 * 16) {
   long long g = (n + threads - 1) / threads;

@@ -33,32 +33,48 @@ __device__ double block_sum(double v, double *red) {
 
 // ------------------------------------------------------------------- GEMM
 
-template <typename T>
+// Tiled GEMM with a BM x BN block tile (256 threads, TM x TN outputs each) so
+// narrow shapes do not spend FP64 FMAs on padding; the K loop stops at the
+// real K.  With ksplit > 1, blockIdx.z selects a K chunk (batch must be 1) and
+// C points to a [ksplit][m][ldc] workspace of partial products.
+template <typename T, int BM, int BN>
 __global__ void __launch_bounds__(256) k_gemm(bool ta, bool tb, int m, int n, int k, T alpha,
                                               const T *__restrict__ A, long long lda, long long sA,
                                               const T *__restrict__ B, long long ldb, long long sB,
-                                              T beta, T *__restrict__ C, long long ldc, long long sC) {
-  constexpr int BM = 64, BN = 64, BK = 16;
+                                              T beta, T *__restrict__ C, long long ldc, long long sC,
+                                              int ksplit, int kchunk) {
+  constexpr int BK = 16;
+  // thread grid: (BM / TM) x (BN / TN) = 256
+  constexpr int TN = (BN >= 64) ? 4 : ((BN == 32) ? 2 : 1);
+  constexpr int TM = (BM * BN) / (256 * TN);
+  constexpr int NTX = BN / TN;  // threads along N
   __shared__ T As[BK][BM + 1];
   __shared__ T Bs[BK][BN + 1];
-  const long long b = blockIdx.z;
-  A += b * sA;
-  B += b * sB;
-  C += b * sC;
+  int kbeg = 0, kend = k;
+  if (ksplit > 1) {
+    kbeg = blockIdx.z * kchunk;
+    kend = min(k, kbeg + kchunk);
+    C += (long long)blockIdx.z * m * ldc;
+  } else {
+    const long long b = blockIdx.z;
+    A += b * sA;
+    B += b * sB;
+    C += b * sC;
+  }
   const int i0 = blockIdx.y * BM, j0 = blockIdx.x * BN;
-  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
-  T acc[4][4];
+  const int tx = threadIdx.x % NTX, ty = threadIdx.x / NTX;
+  T acc[TM][TN];
 #pragma unroll
-  for (int x = 0; x < 4; ++x)
+  for (int x = 0; x < TM; ++x)
 #pragma unroll
-    for (int y = 0; y < 4; ++y) acc[x][y] = T(0);
-  for (int l0 = 0; l0 < k; l0 += BK) {
+    for (int y = 0; y < TN; ++y) acc[x][y] = T(0);
+  for (int l0 = kbeg; l0 < kend; l0 += BK) {
     for (int e = threadIdx.x; e < BM * BK; e += 256) {
       int ii, ll;
       if (!ta) { ii = e / BK; ll = e % BK; } else { ll = e / BM; ii = e % BM; }
       const int gi = i0 + ii, gl = l0 + ll;
       T v = T(0);
-      if (gi < m && gl < k) v = ta ? A[(long long)gl * lda + gi] : A[(long long)gi * lda + gl];
+      if (gi < m && gl < kend) v = ta ? A[(long long)gl * lda + gi] : A[(long long)gi * lda + gl];
       As[ll][ii] = v;
     }
     for (int e = threadIdx.x; e < BK * BN; e += 256) {
@@ -66,35 +82,51 @@ __global__ void __launch_bounds__(256) k_gemm(bool ta, bool tb, int m, int n, in
       if (!tb) { ll = e / BN; jj = e % BN; } else { jj = e / BK; ll = e % BK; }
       const int gl = l0 + ll, gj = j0 + jj;
       T v = T(0);
-      if (gl < k && gj < n) v = tb ? B[(long long)gj * ldb + gl] : B[(long long)gl * ldb + gj];
+      if (gl < kend && gj < n) v = tb ? B[(long long)gj * ldb + gl] : B[(long long)gl * ldb + gj];
       Bs[ll][jj] = v;
     }
     __syncthreads();
+    const int kk = min(BK, kend - l0);
+#pragma unroll 4
+    for (int ll = 0; ll < kk; ++ll) {
+      T av[TM], bv[TN];
 #pragma unroll
-    for (int ll = 0; ll < BK; ++ll) {
-      T av[4], bv[4];
+      for (int x = 0; x < TM; ++x) av[x] = As[ll][ty + (BM / TM) * x];
 #pragma unroll
-      for (int x = 0; x < 4; ++x) av[x] = As[ll][ty + 16 * x];
+      for (int y = 0; y < TN; ++y) bv[y] = Bs[ll][tx + NTX * y];
 #pragma unroll
-      for (int y = 0; y < 4; ++y) bv[y] = Bs[ll][tx + 16 * y];
+      for (int x = 0; x < TM; ++x)
 #pragma unroll
-      for (int x = 0; x < 4; ++x)
-#pragma unroll
-        for (int y = 0; y < 4; ++y) acc[x][y] = fma(av[x], bv[y], acc[x][y]);
+        for (int y = 0; y < TN; ++y) acc[x][y] = fma(av[x], bv[y], acc[x][y]);
     }
     __syncthreads();
   }
 #pragma unroll
-  for (int x = 0; x < 4; ++x) {
-    const int gi = i0 + ty + 16 * x;
+  for (int x = 0; x < TM; ++x) {
+    const int gi = i0 + ty + (BM / TM) * x;
     if (gi >= m) continue;
 #pragma unroll
-    for (int y = 0; y < 4; ++y) {
-      const int gj = j0 + tx + 16 * y;
+    for (int y = 0; y < TN; ++y) {
+      const int gj = j0 + tx + NTX * y;
       if (gj >= n) continue;
       T *cp = C + (long long)gi * ldc + gj;
-      *cp = (beta == T(0)) ? alpha * acc[x][y] : alpha * acc[x][y] + beta * (*cp);
+      if (ksplit > 1) *cp = acc[x][y];
+      else *cp = (beta == T(0)) ? alpha * acc[x][y] : alpha * acc[x][y] + beta * (*cp);
     }
+  }
+}
+
+// C = alpha sum_s W[s] + beta C over the split-K partials (fixed order: deterministic).
+template <typename T>
+__global__ void k_splitk_reduce(const T *__restrict__ W, int ksplit, int m, int n, T alpha, T beta, T *C,
+                                long long ldc) {
+  const long long tot = (long long)m * n;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < tot; e += (long long)gridDim.x * blockDim.x) {
+    const long long i = e / n, j = e % n;
+    T acc = T(0);
+    for (int s = 0; s < ksplit; ++s) acc += W[((long long)s * m + i) * n + j];
+    T *cp = C + i * ldc + j;
+    *cp = (beta == T(0)) ? alpha * acc : alpha * acc + beta * (*cp);
   }
 }
 
@@ -123,14 +155,58 @@ void gemm(Ctx *c, bool ta, bool tb, int m, int n, int k, T alpha, const T *A, lo
     }
     return;
   }
+  // tile shape: narrow outputs get narrow tiles (no FMAs spent on padding)
+  int shape = 0;  // 0: 64x64, 1: 128x16, 2: 16x128, 3: 32x32
+  if (n <= 16 && m > 16) shape = 1;
+  else if (m <= 16 && n > 16) shape = 2;
+  else if (m <= 32 && n <= 32) shape = 3;
+  const int BMs[4] = {64, 128, 16, 32}, BNs[4] = {64, 16, 128, 32};
+  const int BM = BMs[shape], BN = BNs[shape];
+  auto launch = [&](dim3 grid, const T *A_, const T *B_, T beta_, T *C_, long long ldc_, long long sA_, long long sB_,
+                    long long sC_, int ksplit, int kchunk) {
+    switch (shape) {
+      case 0:
+        k_gemm<T, 64, 64><<<grid, 256, 0, c->stream>>>(ta, tb, m, n, k, alpha, A_, lda, sA_, B_, ldb, sB_, beta_, C_,
+                                                        ldc_, sC_, ksplit, kchunk);
+        break;
+      case 1:
+        k_gemm<T, 128, 16><<<grid, 256, 0, c->stream>>>(ta, tb, m, n, k, alpha, A_, lda, sA_, B_, ldb, sB_, beta_, C_,
+                                                         ldc_, sC_, ksplit, kchunk);
+        break;
+      case 2:
+        k_gemm<T, 16, 128><<<grid, 256, 0, c->stream>>>(ta, tb, m, n, k, alpha, A_, lda, sA_, B_, ldb, sB_, beta_, C_,
+                                                         ldc_, sC_, ksplit, kchunk);
+        break;
+      default:
+        k_gemm<T, 32, 32><<<grid, 256, 0, c->stream>>>(ta, tb, m, n, k, alpha, A_, lda, sA_, B_, ldb, sB_, beta_, C_,
+                                                        ldc_, sC_, ksplit, kchunk);
+        break;
+    }
+    TTI_LAUNCH();
+  };
+  const long long tiles = (long long)cdiv(n, BN) * cdiv(m, BM);
+  if (batch == 1 && tiles * 2 < c->num_sms && k >= 128) {
+    // few output tiles but a long K: split K over CTAs, then reduce the partials
+    int ksplit = (int)std::min<long long>(std::max<long long>(1, (2LL * c->num_sms) / tiles), (k + 63) / 64);
+    ksplit = std::max(2, std::min(ksplit, 256));
+    const int kchunk = ((k + ksplit - 1) / ksplit + 15) / 16 * 16;
+    ksplit = (k + kchunk - 1) / kchunk;
+    DBuf W(c, (size_t)ksplit * m * n * sizeof(T));
+    {
+      ProfScope ps(c, sizeof(T) == 8 ? PROF_GEMM64 : PROF_OFF, 2.0 * m * (double)n * k);
+      launch(dim3(cdiv(n, BN), cdiv(m, BM), ksplit), A, B, T(0), W.as<T>(), n, 0, 0, 0, ksplit, kchunk);
+    }
+    k_splitk_reduce<T><<<grid1d((long long)m * n, 256), 256, 0, c->stream>>>(W.as<T>(), ksplit, m, n, alpha, beta, C,
+                                                                             ldc);
+    TTI_LAUNCH();
+    return;
+  }
   for (int b0 = 0; b0 < batch; b0 += 65535) {
     int nb = std::min(65535, batch - b0);
-    dim3 grid(cdiv(n, 64), cdiv(m, 64), nb);
+    dim3 grid(cdiv(n, BN), cdiv(m, BM), nb);
     TTI_CHECK_ARG(grid.y <= 65535, "gemm: m=%d too large", m);
     ProfScope ps(c, sizeof(T) == 8 ? PROF_GEMM64 : PROF_OFF, 2.0 * m * (double)n * k * nb);
-    k_gemm<T><<<grid, 256, 0, c->stream>>>(ta, tb, m, n, k, alpha, A + b0 * sA, lda, sA, B + b0 * sB, ldb,
-                                            sB, beta, C + b0 * sC, ldc, sC);
-    TTI_LAUNCH();
+    launch(grid, A + b0 * sA, B + b0 * sB, beta, C + b0 * sC, ldc, sA, sB, sC, 1, k);
   }
 }
 
@@ -278,11 +354,18 @@ __global__ void k_qr_load(const double *__restrict__ A, long long lda, long long
 }
 
 __global__ void __launch_bounds__(256) k_qr_panel(double *__restrict__ W, int mb, int k, double *__restrict__ tau,
-                                                  double *__restrict__ Rout) {
+                                                  double *__restrict__ Rout, int use_smem) {
+  extern __shared__ double qsm[];
   __shared__ double red[32];
   __shared__ double sh[3];
   const long long blk = blockIdx.x;
-  double *Wb = W + blk * (long long)mb * k;
+  double *Wg = W + blk * (long long)mb * k;
+  double *Wb = Wg;
+  if (use_smem) {  // work on a shared-memory copy of the block, write the reflectors back at the end
+    for (int e = threadIdx.x; e < mb * k; e += blockDim.x) qsm[e] = Wg[e];
+    Wb = qsm;
+    __syncthreads();
+  }
   double *tb = tau + blk * k;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
   for (int j = 0; j < k; ++j) {
@@ -324,16 +407,19 @@ __global__ void __launch_bounds__(256) k_qr_panel(double *__restrict__ W, int mb
     const int row = e / k, cc = e % k;
     Rout[(blk * k + row) * k + cc] = (cc >= row && row < mb) ? Wb[(long long)cc * mb + row] : 0.0;
   }
+  if (use_smem)
+    for (int e = tid; e < mb * k; e += blockDim.x) Wg[e] = Wb[e];
 }
 
 __global__ void __launch_bounds__(256) k_qr_formq(const double *__restrict__ W, const double *__restrict__ tau,
                                                   int mb, int k, const double *__restrict__ Cin,
                                                   double *__restrict__ Y, double *__restrict__ Out,
-                                                  long long out_rows) {
+                                                  long long out_rows, int use_smem) {
+  extern __shared__ double qsm[];
   const long long blk = blockIdx.x;
   const double *Wb = W + blk * (long long)mb * k;
   const double *tb = tau + blk * k;
-  double *Yb = Y + blk * (long long)mb * k;
+  double *Yb = use_smem ? qsm : Y + blk * (long long)mb * k;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
   for (int e = tid; e < mb * k; e += blockDim.x) {
     const int cc = e / mb, i = e % mb;
@@ -373,8 +459,16 @@ static int qr_block_rows(long long rows, int k) {
   return mb;
 }
 
+constexpr size_t kQrSmemBytes = 160 * 1024;
+
 void qr(Ctx *c, int m, int k, const double *A, long long lda, double *Q, double *R) {
   TTI_CHECK_ARG(m >= 1 && k >= 1 && k <= 256, "qr: bad sizes m=%d k=%d", m, k);
+  static bool attr = false;
+  if (!attr) {
+    TTI_CUDA(cudaFuncSetAttribute(k_qr_panel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kQrSmemBytes));
+    TTI_CUDA(cudaFuncSetAttribute(k_qr_formq, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kQrSmemBytes));
+    attr = true;
+  }
   struct Level {
     long long rows;
     int mb, nblk;
@@ -395,7 +489,9 @@ void qr(Ctx *c, int m, int k, const double *A, long long lda, double *Q, double 
     TTI_LAUNCH();
     {
       ProfScope ps(c, PROF_QR, 2.0 * L.nblk * (double)L.mb * k * k);
-      k_qr_panel<<<L.nblk, 256, 0, c->stream>>>(L.W.d(), L.mb, k, L.tau.d(), L.Rs.d());
+      const size_t sm = (size_t)L.mb * k * sizeof(double);
+      const int use = sm <= kQrSmemBytes;
+      k_qr_panel<<<L.nblk, 256, use ? sm : 0, c->stream>>>(L.W.d(), L.mb, k, L.tau.d(), L.Rs.d(), use);
       TTI_LAUNCH();
     }
     lv.push_back(std::move(L));
@@ -422,7 +518,10 @@ void qr(Ctx *c, int m, int k, const double *A, long long lda, double *Q, double 
       Out = DBuf(c, (size_t)out_rows * k * sizeof(double));
       outp = Out.d();
     }
-    k_qr_formq<<<l.nblk, 256, 0, c->stream>>>(l.W.d(), l.tau.d(), l.mb, k, Cin, Y.d(), outp, out_rows);
+    const size_t sm = (size_t)l.mb * k * sizeof(double);
+    const int use = sm <= kQrSmemBytes;
+    k_qr_formq<<<l.nblk, 256, use ? sm : 0, c->stream>>>(l.W.d(), l.tau.d(), l.mb, k, Cin, Y.d(), outp, out_rows,
+                                                         use);
     TTI_LAUNCH();
     Cbuf = std::move(Out);
     Cin = Cbuf.d();
@@ -431,7 +530,7 @@ void qr(Ctx *c, int m, int k, const double *A, long long lda, double *Q, double 
 
 // ------------------------------------------------------- one-sided Jacobi SVD
 
-__global__ void __launch_bounds__(256) k_jacobi_svd(int k, const double *__restrict__ A, double *__restrict__ U,
+__global__ void __launch_bounds__(1024) k_jacobi_svd(int k, const double *__restrict__ A, double *__restrict__ U,
                                                     double *__restrict__ S, double *__restrict__ V,
                                                     double *Wg, double *Vg, int use_smem, int *status) {
   extern __shared__ double smem[];
@@ -441,11 +540,19 @@ __global__ void __launch_bounds__(256) k_jacobi_svd(int k, const double *__restr
   double *W = use_smem ? smem : Wg;           // W[c * k + i]: column c, row i
   double *Vw = use_smem ? smem + (size_t)kp * k : Vg;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+  __shared__ double red[32];
+  double fro = 0.0;
   for (int e = tid; e < kp * k; e += blockDim.x) {
     const int cc = e / k, i = e % k;
-    W[e] = (cc < k) ? A[(long long)i * k + cc] : 0.0;
+    const double v = (cc < k) ? A[(long long)i * k + cc] : 0.0;
+    W[e] = v;
+    fro += v * v;
     Vw[e] = (cc == i) ? 1.0 : 0.0;
   }
+  fro = block_sum(fro, red);
+  // columns whose squared norm is below this are roundoff: rotating them changes nothing
+  const double tiny = fro * 1e-32 + 1e-300;
+  const double tol = 4.0 * k * DBL_EPSILON;
   __syncthreads();
   int sweep = 0;
   for (; sweep < 60; ++sweep) {
@@ -466,7 +573,7 @@ __global__ void __launch_bounds__(256) k_jacobi_svd(int k, const double *__restr
         a = warp_sum(a);
         b = warp_sum(b);
         g = warp_sum(g);
-        if (g != 0.0 && a > 0.0 && b > 0.0 && fabs(g) > 1e-15 * sqrt(a) * sqrt(b)) {
+        if (g != 0.0 && a > tiny && b > tiny && fabs(g) > tol * sqrt(a) * sqrt(b)) {
           const double zeta = (b - a) / (2.0 * g);
           double t;
           if (fabs(zeta) > 1e100) t = 0.5 / zeta;
@@ -530,7 +637,7 @@ void svd_small(Ctx *c, int k, const double *A, double *U, double *s, double *V) 
   } else if (bytes > 48 * 1024) {
     TTI_CUDA(cudaFuncSetAttribute(k_jacobi_svd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
   }
-  k_jacobi_svd<<<1, 256, bytes, c->stream>>>(k, A, U, s, V, Wg.d(), Vg.d(), use_smem, c->dstatus);
+  k_jacobi_svd<<<1, 1024, bytes, c->stream>>>(k, A, U, s, V, Wg.d(), Vg.d(), use_smem, c->dstatus);
   TTI_LAUNCH();
 }
 
@@ -565,7 +672,7 @@ int svd_small_noalloc(cudaStream_t stream, int k, const double *A, double *U, do
     }
     scratch = g_scratch_ptr[dev];
   }
-  k_jacobi_svd<<<1, 256, 0, stream>>>(k, A, U, s, V, scratch, scratch + 256 * 256, 0, nullptr);
+  k_jacobi_svd<<<1, 1024, 0, stream>>>(k, A, U, s, V, scratch, scratch + 256 * 256, 0, nullptr);
   g_launches.fetch_add(1, std::memory_order_relaxed);
   return cudaGetLastError() == cudaSuccess ? TT_IGA_OK : TT_IGA_ERR_CUDA;
 }

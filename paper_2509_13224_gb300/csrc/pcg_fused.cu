@@ -3,13 +3,12 @@
 // One cooperative launch runs every PCG iteration of a local solve
 //   B d = r,  B = PhiL (x) A_k (x) PhiR,  preconditioner = band block-Jacobi,
 // so the local solve costs one launch instead of about a dozen launches and a
-// host read-back per iteration.  Each iteration is six grid-wide phases:
-//   A  T1 = p PhiR^T            (dense, right interface)
-//   B  T2 = band(A_k, T1)       (banded operator core)
-//   C  q  = PhiL T2,  <p, q>    (dense, left interface; partial dot)
-//   D  x += alpha p, r -= alpha q, <r, r>
-//   E  stop test; z = P^{-1} r (one thread per (alpha, beta) band system), <r, z>
-//   F  p = z + beta p
+// host read-back per iteration.  Each iteration is four grid-wide phases:
+//   A  p = z + beta p_prev (double-buffered), T1 = p PhiR^T  (right interface)
+//   B  T2 = band(A_k, T1)                                    (operator core)
+//   C  q  = PhiL T2,  <p, q>                                 (left interface)
+//   E  per (alpha, beta) band system: x += alpha p, r -= alpha q,
+//      z = P^{-1} r;  <r, r>, <r, z>; stop test after the barrier
 // Reductions are deterministic: every CTA writes one partial per phase and
 // all CTAs sum the partials in the same order.  The grid barrier spins with an
 // iteration limit; on expiry it raises an error flag and the kernel returns.
@@ -27,32 +26,49 @@ struct Barrier {
 
 namespace {
 
-constexpr long long kSpinLimit = 1LL << 24;  // x 64 ns sleep: about one second
+constexpr size_t kPcgSmemBytes = 200 * 1024;
+constexpr long long kSpinLimit = 1LL << 22;  // polls of about 0.25-0.5 us: one to two seconds
 
+__device__ __forceinline__ unsigned int ld_acquire(const unsigned int *p) {
+  unsigned int v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ unsigned int atom_add_acqrel(unsigned int *p, unsigned int v) {
+  unsigned int old;
+  asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
+  return old;
+}
+__device__ __forceinline__ void red_add_release(unsigned int *p, unsigned int v) {
+  asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ void st_relaxed(unsigned int *p, unsigned int v) {
+  asm volatile("st.relaxed.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// Grid-wide barrier over co-resident CTAs (cooperative launch): arrival counter
+// plus generation number; the last arriver resets the counter and releases the
+// generation, the others poll it with acquire loads.  A wait that exceeds the
+// poll limit sets *err and returns false instead of hanging.
 __device__ __forceinline__ bool grid_sync(Barrier *bar, unsigned int nblocks, int *err) {
   __syncthreads();
   __shared__ int ok;
   if (threadIdx.x == 0) {
     ok = 1;
-    volatile unsigned int *vgen = &bar->gen;
-    const unsigned int g = *vgen;
-    __threadfence();
-    if (atomicAdd(&bar->count, 1u) == nblocks - 1) {
-      atomicExch(&bar->count, 0u);
-      __threadfence();
-      atomicAdd(&bar->gen, 1u);
+    const unsigned int g = ld_acquire(&bar->gen);
+    if (atom_add_acqrel(&bar->count, 1u) == nblocks - 1) {
+      st_relaxed(&bar->count, 0u);
+      red_add_release(&bar->gen, 1u);
     } else {
       long long spins = 0;
-      while (*vgen == g) {
+      while (ld_acquire(&bar->gen) == g) {
         if (++spins > kSpinLimit) {
           atomicExch(err, 1);
           ok = 0;
           break;
         }
-        __nanosleep(64);
       }
     }
-    __threadfence();
     if (*(volatile int *)err) ok = 0;
   }
   __syncthreads();
@@ -73,13 +89,15 @@ __device__ __forceinline__ void cta_partial(double v, double *part) {
   __syncthreads();
 }
 
-// Same-order sum of the partials, broadcast to the CTA.
+// Sum of the per-CTA partials, identical on every CTA (fixed lane assignment and
+// shuffle order), broadcast to the CTA.  Warp 0 loads the partials in parallel.
 __device__ __forceinline__ double grid_total(const double *part) {
   __shared__ double tot;
-  if (threadIdx.x == 0) {
+  if (threadIdx.x < 32) {
     double t = 0.0;
-    for (unsigned int b = 0; b < gridDim.x; ++b) t += ((volatile const double *)part)[b];
-    tot = t;
+    for (unsigned int b = threadIdx.x; b < gridDim.x; b += 32) t += ((volatile const double *)part)[b];
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+    if (threadIdx.x == 0) tot = t;
   }
   __syncthreads();
   const double v = tot;
@@ -87,152 +105,208 @@ __device__ __forceinline__ double grid_total(const double *part) {
   return v;
 }
 
+// Phase timestamps of CTA 0 (global timer, ns) when a trace buffer is given.
+__device__ __forceinline__ void trace_mark(unsigned long long *trace, int cap, int &slot) {
+  if (trace && blockIdx.x == 0 && threadIdx.x == 0 && slot < cap) {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    trace[slot] = t;
+  }
+  ++slot;
+}
+
+// The (alpha, beta) band systems of the preconditioner, `slots` at a time per
+// CTA.  All threads of the CTA gather each system's factor rows (FP32) and its
+// entries of r, q, p, x, apply x += alpha p, r -= alpha q (or x = 0, r = b when
+// init) in parallel, and stage r in shared memory; lane 0 of warp w then runs
+// system w's forward / backward substitution in FP32 out of shared memory
+// (the only sequential part; on GB300 a dependent FP64 operation costs about
+// 64 cycles against 4.5 for FP32, and a preconditioner needs no accuracy);
+// finally the CTA scatters z in the working precision and accumulates <r, r>
+// and <r, z> in FP64 with every thread on its own chain.
+// Shared layout per slot: L[n][PB+1] (float), r[n] (float).
 template <typename T, int PB>
-__device__ __forceinline__ double band_solve_pair(const T *__restrict__ L, int rl, int n, int rr, const T *r, T *z,
-                                                  int t) {
-  // forward / backward substitution of one (alpha, beta) band system; returns <r, z> over it
+__device__ __forceinline__ void band_systems(const PcgArgs<T> &a, const T *__restrict__ pcur, double alpha, bool init,
+                                             double &rr_out, double &rz_out) {
+  extern __shared__ unsigned char esm_raw[];
+  float *esm = reinterpret_cast<float *>(esm_raw);
+  const int rl = a.rl, rr = a.rr, n = a.n, slots = a.slots;
   const int npair = rl * rr;
-  const int a = t / rr, bb = t % rr;
-  const long long base = (long long)a * n * rr + bb;
-  T w[PB];
+  const int per = n * (PB + 2);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (long long t0 = (long long)blockIdx.x * slots; t0 < npair; t0 += (long long)gridDim.x * slots) {
+    const int cnt = (int)((npair - t0 < slots) ? (npair - t0) : slots);
+    for (int e = threadIdx.x; e < cnt * n * (PB + 1); e += blockDim.x) {
+      const int s_ = e / (n * (PB + 1)), rem = e - s_ * (n * (PB + 1));
+      const int i = rem / (PB + 1), k = rem - i * (PB + 1);
+      esm[s_ * per + rem] = a.Lf[((long long)i * (PB + 1) + k) * npair + t0 + s_];
+    }
+    double rr_th = 0.0;
+    for (int e = threadIdx.x; e < cnt * n; e += blockDim.x) {
+      const int s_ = e / n, i = e - s_ * n;
+      const long long t = t0 + s_;
+      const long long idx = ((t / rr) * n + i) * rr + (t % rr);
+      T r;
+      if (init) {
+        r = a.b[idx];
+        a.x[idx] = T(0);
+      } else {
+        a.x[idx] += (T)alpha * pcur[idx];
+        r = a.r[idx] - (T)alpha * a.q[idx];
+      }
+      a.r[idx] = r;
+      rr_th += (double)r * (double)r;
+      esm[s_ * per + n * (PB + 1) + i] = (float)r;
+    }
+    rr_out += rr_th;
+    __syncthreads();
+    if (warp < cnt && lane == 0) {
+      const float *Ls = esm + warp * per;
+      float *rs = esm + warp * per + n * (PB + 1);  // overwritten by z
+      float w[PB];
 #pragma unroll
-  for (int k = 0; k < PB; ++k) w[k] = T(0);
-  for (int i = 0; i < n; ++i) {
-    const T *Li = L + (long long)i * (PB + 1) * npair + t;
-    T sv = r[base + (long long)i * rr];
+      for (int k = 0; k < PB; ++k) w[k] = 0.f;
+      for (int i = 0; i < n; ++i) {
+        const float *Li = Ls + i * (PB + 1);
+        float sv = rs[i];
 #pragma unroll
-    for (int k = 0; k < PB; ++k) sv -= Li[(long long)k * npair] * w[k];
-    const T y = sv * Li[(long long)PB * npair];
-    z[base + (long long)i * rr] = y;
+        for (int k = 0; k < PB; ++k) sv -= Li[k] * w[k];
+        const float y = sv * Li[PB];
+        rs[i] = y;
 #pragma unroll
-    for (int k = 0; k + 1 < PB; ++k) w[k] = w[k + 1];
-    w[PB - 1] = y;
+        for (int k = 0; k + 1 < PB; ++k) w[k] = w[k + 1];
+        w[PB - 1] = y;
+      }
+#pragma unroll
+      for (int k = 0; k < PB; ++k) w[k] = 0.f;  // w[d-1] = z_{i+d}
+      for (int i = n - 1; i >= 0; --i) {
+        float sv = rs[i];
+#pragma unroll
+        for (int d = 1; d <= PB; ++d)
+          if (i + d < n) sv -= Ls[(i + d) * (PB + 1) + (PB - d)] * w[d - 1];
+        const float zi = sv * Ls[i * (PB + 1) + PB];
+        rs[i] = zi;
+#pragma unroll
+        for (int d = PB - 1; d > 0; --d) w[d] = w[d - 1];
+        w[0] = zi;
+      }
+    }
+    __syncthreads();
+    double rz_th = 0.0;
+    for (int e = threadIdx.x; e < cnt * n; e += blockDim.x) {
+      const int s_ = e / n, i = e - s_ * n;
+      const long long t = t0 + s_;
+      const long long idx = ((t / rr) * n + i) * rr + (t % rr);
+      const T zi = (T)esm[s_ * per + n * (PB + 1) + i];
+      a.z[idx] = zi;
+      rz_th += (double)a.r[idx] * (double)zi;
+    }
+    rz_out += rz_th;
+    __syncthreads();
   }
-#pragma unroll
-  for (int k = 0; k < PB; ++k) w[k] = T(0);
-  double rz = 0.0;
-  for (int i = n - 1; i >= 0; --i) {
-    T sv = z[base + (long long)i * rr];
-#pragma unroll
-    for (int d = 1; d <= PB; ++d)
-      if (i + d < n) sv -= L[((long long)(i + d) * (PB + 1) + (PB - d)) * npair + t] * w[d - 1];
-    const T zi = sv * L[((long long)i * (PB + 1) + PB) * npair + t];
-    z[base + (long long)i * rr] = zi;
-    rz += (double)r[base + (long long)i * rr] * (double)zi;
-#pragma unroll
-    for (int d = PB - 1; d > 0; --d) w[d] = w[d - 1];
-    w[0] = zi;
-  }
-  return rz;
 }
 
 template <typename T, int PB>
-__global__ void __launch_bounds__(256) k_pcg_fused(PcgArgs<T> a) {
+__global__ void __launch_bounds__(256, 1) k_pcg_fused(PcgArgs<T> a) {
   const int rl = a.rl, rr = a.rr, Rl = a.Rl, Rr = a.Rr, n = a.n, b = 2 * PB + 1;
   const long long N = (long long)rl * n * rr;
   const long long nA = (long long)rl * n * rr * Rr, nB = (long long)Rl * rl * n * rr;
-  const int npair = rl * rr;
   const long long tid = blockIdx.x * (long long)blockDim.x + threadIdx.x, nth = (long long)gridDim.x * blockDim.x;
   const unsigned int G = gridDim.x;
   double *p_pq = a.part, *p_rr = a.part + G, *p_rz = a.part + 2 * G;
+  (void)N;
 
-  // x = 0, r = b
-  for (long long e = tid; e < N; e += nth) {
-    a.x[e] = T(0);
-    a.r[e] = a.b[e];
-  }
-  if (!grid_sync(a.bar, G, a.err)) return;
-  double rz_loc = 0.0;
-  for (long long t = tid; t < npair; t += nth) rz_loc += band_solve_pair<T, PB>(a.L, rl, n, rr, a.r, a.z, (int)t);
-  double rr_loc = 0.0;
-  for (long long e = tid; e < N; e += nth) rr_loc += (double)a.r[e] * (double)a.r[e];
-  cta_partial(rz_loc, p_rz);
+  int slot = 0;
+  trace_mark(a.trace, a.trace_cap, slot);
+  // r = b, x = 0, z = P^{-1} r;  <r, r>, <r, z>
+  double rr_loc = 0.0, rz_loc = 0.0;
+  band_systems<T, PB>(a, nullptr, 0.0, true, rr_loc, rz_loc);
   cta_partial(rr_loc, p_rr);
+  cta_partial(rz_loc, p_rz);
   if (!grid_sync(a.bar, G, a.err)) return;
-  double rz = grid_total(p_rz);
+  trace_mark(a.trace, a.trace_cap, slot);
   double res2 = grid_total(p_rr);
-  for (long long e = tid; e < N; e += nth) a.pv[e] = a.z[e];
+  double rz = grid_total(p_rz), rz_prev = 1.0;
   int it = 0;
-  if (res2 > a.tol2) {
-    if (!grid_sync(a.bar, G, a.err)) return;
-    for (; it < a.maxit; ++it) {
-      // A: T1[(aa, j)][(c, d)] = sum_e p[aa][j][e] PhiR[c][d][e]
-      for (long long e = tid; e < nA; e += nth) {
-        const int d = (int)(e % Rr);
-        long long t = e / Rr;
-        const int c = (int)(t % rr);
-        const long long row = t / rr;  // aa * n + j
-        const T *pr = a.pv + row * rr;
-        const T *ph = a.PhiR + ((long long)c * Rr + d) * rr;
-        T s = T(0);
-        for (int f = 0; f < rr; ++f) s += pr[f] * ph[f];
-        a.T1[e] = s;
+  for (; it < a.maxit && res2 > a.tol2; ++it) {
+    const double beta = (it == 0 || rz_prev == 0.0) ? 0.0 : rz / rz_prev;
+    T *pcur = (it & 1) ? a.pv2 : a.pv;
+    const T *pprev = (it & 1) ? a.pv : a.pv2;
+    // A: p = z + beta p_prev (rows written once), T1[(aa, j)][(c, d)] = sum_f p[aa][j][f] PhiR[c][d][f]
+    for (long long e = tid; e < nA; e += nth) {
+      const int d = (int)(e % Rr);
+      long long t = e / Rr;
+      const int c = (int)(t % rr);
+      const long long row = t / rr;  // aa * n + j
+      const T *zr = a.z + row * rr;
+      const T *pr = pprev + row * rr;
+      const T *ph = a.PhiR + ((long long)c * Rr + d) * rr;
+      const bool writer = (c == 0 && d == 0);
+      T s = T(0);
+      for (int f = 0; f < rr; ++f) {
+        const T pf = (it == 0) ? zr[f] : zr[f] + (T)beta * pr[f];
+        if (writer) pcur[row * rr + f] = pf;
+        s += pf * ph[f];
       }
-      if (!grid_sync(a.bar, G, a.err)) return;
-      // B: T2[g][aa][i][c] = sum_{o, d} A[g][i][o][d] T1[aa][i+o-p][c][d]
-      for (long long e = tid; e < nB; e += nth) {
-        const int c = (int)(e % rr);
-        long long t = e / rr;
-        const int i = (int)(t % n);
-        t /= n;
-        const int aa = (int)(t % rl);
-        const int g = (int)(t / rl);
-        const T *Ar = a.A + ((long long)g * n + i) * b * Rr;
-        T s = T(0);
-#pragma unroll
-        for (int o = 0; o < b; ++o) {
-          const int j = i + o - PB;
-          if (j < 0 || j >= n) continue;
-          const T *Ao = Ar + o * Rr;
-          const T *Tj = a.T1 + (((long long)aa * n + j) * rr + c) * Rr;
-          for (int d = 0; d < Rr; ++d) s += Ao[d] * Tj[d];
-        }
-        a.T2[e] = s;
-      }
-      if (!grid_sync(a.bar, G, a.err)) return;
-      // C: q[al][i][c] = sum_{g, aa} PhiL[al][g][aa] T2[g][aa][i][c];  <p, q>
-      double pq_loc = 0.0;
-      for (long long e = tid; e < N; e += nth) {
-        const long long ic = e % ((long long)n * rr);
-        const int al = (int)(e / ((long long)n * rr));
-        const T *ph = a.PhiL + (long long)al * Rl * rl;
-        T s = T(0);
-        for (int g = 0; g < Rl; ++g)
-          for (int aa = 0; aa < rl; ++aa) s += ph[g * rl + aa] * a.T2[((long long)g * rl + aa) * n * rr + ic];
-        a.q[e] = s;
-        pq_loc += (double)a.pv[e] * (double)s;
-      }
-      cta_partial(pq_loc, p_pq);
-      if (!grid_sync(a.bar, G, a.err)) return;
-      // D: x += alpha p, r -= alpha q;  <r, r>
-      const double pq = grid_total(p_pq);
-      const double alpha = (pq != 0.0) ? rz / pq : 0.0;
-      rr_loc = 0.0;
-      for (long long e = tid; e < N; e += nth) {
-        a.x[e] += (T)alpha * a.pv[e];
-        const T rv = a.r[e] - (T)alpha * a.q[e];
-        a.r[e] = rv;
-        rr_loc += (double)rv * (double)rv;
-      }
-      cta_partial(rr_loc, p_rr);
-      if (!grid_sync(a.bar, G, a.err)) return;
-      // E: stop test, z = P^{-1} r, <r, z>
-      res2 = grid_total(p_rr);
-      if (res2 <= a.tol2 || !(pq > 0.0)) {
-        ++it;
-        break;
-      }
-      rz_loc = 0.0;
-      for (long long t = tid; t < npair; t += nth) rz_loc += band_solve_pair<T, PB>(a.L, rl, n, rr, a.r, a.z, (int)t);
-      cta_partial(rz_loc, p_rz);
-      if (!grid_sync(a.bar, G, a.err)) return;
-      // F: p = z + beta p
-      const double rz_new = grid_total(p_rz);
-      const double beta = (rz != 0.0) ? rz_new / rz : 0.0;
-      rz = rz_new;
-      for (long long e = tid; e < N; e += nth) a.pv[e] = a.z[e] + (T)beta * a.pv[e];
-      if (!grid_sync(a.bar, G, a.err)) return;
+      a.T1[e] = s;
     }
+    if (!grid_sync(a.bar, G, a.err)) return;
+    trace_mark(a.trace, a.trace_cap, slot);
+    // B: T2[g][aa][i][c] = sum_{o, d} A[g][i][o][d] T1[aa][i+o-p][c][d]
+    for (long long e = tid; e < nB; e += nth) {
+      const int c = (int)(e % rr);
+      long long t = e / rr;
+      const int i = (int)(t % n);
+      t /= n;
+      const int aa = (int)(t % rl);
+      const int g = (int)(t / rl);
+      const T *Ar = a.A + ((long long)g * n + i) * b * Rr;
+      T s0 = T(0), s1 = T(0);  // two chains: halves the dependent FMA latency
+#pragma unroll
+      for (int o = 0; o < b; ++o) {
+        const int j = i + o - PB;
+        if (j < 0 || j >= n) continue;
+        const T *Ao = Ar + o * Rr;
+        const T *Tj = a.T1 + (((long long)aa * n + j) * rr + c) * Rr;
+        if (o & 1)
+          for (int d = 0; d < Rr; ++d) s1 += Ao[d] * Tj[d];
+        else
+          for (int d = 0; d < Rr; ++d) s0 += Ao[d] * Tj[d];
+      }
+      a.T2[e] = s0 + s1;
+    }
+    if (!grid_sync(a.bar, G, a.err)) return;
+    trace_mark(a.trace, a.trace_cap, slot);
+    // C: q[al][i][c] = sum_{g, aa} PhiL[al][g][aa] T2[g][aa][i][c];  <p, q>
+    double pq_loc = 0.0;
+    for (long long e = tid; e < (long long)rl * n * rr; e += nth) {
+      const long long ic = e % ((long long)n * rr);
+      const int al = (int)(e / ((long long)n * rr));
+      const T *ph = a.PhiL + (long long)al * Rl * rl;
+      T s4[4] = {T(0), T(0), T(0), T(0)};  // four chains over the (g, aa) sum
+      const int ga = Rl * rl;
+      for (int q = 0; q < ga; ++q) s4[q & 3] += ph[q] * a.T2[(long long)q * n * rr + ic];
+      const T s = (s4[0] + s4[1]) + (s4[2] + s4[3]);
+      a.q[e] = s;
+      pq_loc += (double)pcur[e] * (double)s;
+    }
+    cta_partial(pq_loc, p_pq);
+    if (!grid_sync(a.bar, G, a.err)) return;
+    trace_mark(a.trace, a.trace_cap, slot);
+    // E: x += alpha p, r -= alpha q, z = P^{-1} r per band system;  <r, r>, <r, z>
+    const double pq = grid_total(p_pq);
+    if (!(pq > 0.0)) break;
+    const double alpha = rz / pq;
+    rr_loc = 0.0;
+    rz_loc = 0.0;
+    band_systems<T, PB>(a, pcur, alpha, false, rr_loc, rz_loc);
+    cta_partial(rr_loc, p_rr);
+    cta_partial(rz_loc, p_rz);
+    if (!grid_sync(a.bar, G, a.err)) return;
+    trace_mark(a.trace, a.trace_cap, slot);
+    res2 = grid_total(p_rr);
+    rz_prev = rz;
+    rz = grid_total(p_rz);
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     a.out[0] = (double)it;
@@ -257,16 +331,28 @@ template <typename T> const void *pick(int p) {
 
 }  // namespace
 
-template <typename T> int pcg_fused_grid(Ctx *c, const PcgArgs<T> &a) {
-  // One thread per output of the widest phase (the band stage or the right-interface
-  // stage), all CTAs co-resident; the FP64 pipe needs every SM, so small systems
-  // still spread over the whole GPU while the work allows at least one output per thread.
+// Band systems staged per CTA at a time (one warp each) and the shared memory they need.
+template <typename T> static int band_slots(const PcgArgs<T> &a) {
+  const size_t per = (size_t)a.n * (a.p + 2) * sizeof(float);
+  int slots = (int)std::min<size_t>(8, kPcgSmemBytes / std::max<size_t>(per, 1));
+  return std::max(1, slots);
+}
+
+template <typename T> int pcg_fused_grid(Ctx *c, PcgArgs<T> &a) {
+  // One thread per output of the widest dense phase, at least enough CTAs for the
+  // band systems, all CTAs co-resident.
   const void *k = pick<T>(a.p);
+  a.slots = band_slots(a);
+  a.smem = (int)((size_t)a.slots * a.n * (a.p + 2) * sizeof(float));
+  TTI_CHECK_ARG((size_t)a.n * (a.p + 2) * sizeof(float) <= kPcgSmemBytes, "pcg: n=%d too large for one band system",
+                a.n);
+  TTI_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kPcgSmemBytes));
   int per_sm = 0;
-  TTI_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, 256, 0));
+  TTI_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, 256, a.smem));
+  TTI_CHECK_ARG(per_sm >= 1, "pcg: kernel does not fit on an SM");
   const long long nA = (long long)a.rl * a.n * a.rr * a.Rr, nB = (long long)a.Rl * a.rl * a.n * a.rr;
-  const long long work = std::max(nA, nB);
-  long long g = (work + 255) / 256;
+  const long long npair = (long long)a.rl * a.rr;
+  long long g = std::max((std::max(nA, nB) + 255) / 256, (npair + a.slots - 1) / a.slots);
   const long long cap = (long long)c->num_sms * std::max(1, std::min(per_sm, 2));
   g = std::max<long long>(1, std::min(g, cap));
   return (int)g;
@@ -278,13 +364,13 @@ template <typename T> void pcg_fused(Ctx *c, PcgArgs<T> a, int grid) {
   void *args[] = {&a};
   {
     ProfScope ps(c, PROF_PCG_FUSED, 0.0);
-    TTI_CUDA(cudaLaunchCooperativeKernel(k, dim3(grid), dim3(256), args, 0, c->stream));
+    TTI_CUDA(cudaLaunchCooperativeKernel(k, dim3(grid), dim3(256), args, (size_t)a.smem, c->stream));
   }
   g_launches.fetch_add(1, std::memory_order_relaxed);
 }
 
-template int pcg_fused_grid<double>(Ctx *, const PcgArgs<double> &);
-template int pcg_fused_grid<float>(Ctx *, const PcgArgs<float> &);
+template int pcg_fused_grid<double>(Ctx *, PcgArgs<double> &);
+template int pcg_fused_grid<float>(Ctx *, PcgArgs<float> &);
 template void pcg_fused<double>(Ctx *, PcgArgs<double>, int);
 template void pcg_fused<float>(Ctx *, PcgArgs<float>, int);
 

@@ -8,22 +8,26 @@ template <typename T> struct PcgArgs {
   const T *PhiL;  // [rl][Rl][rl]
   const T *PhiR;  // [rr][Rr][rr]
   const T *A;     // [Rl][n][2p+1][Rr]
-  const T *L;     // band Cholesky factors [n][p+1][rl*rr]
+  const float *Lf;  // band Cholesky factors [n][p+1][rl*rr] (FP32; reciprocal diagonal in slot p)
   const T *b;     // right-hand side [rl][n][rr]
-  T *x, *r, *z, *pv, *q;  // solution and work vectors [rl][n][rr]
+  T *x, *r, *z, *pv, *pv2, *q;  // solution and work vectors [rl][n][rr] (pv, pv2: p double buffer)
   T *T1;          // [rl][n][rr][Rr]
   T *T2;          // [Rl][rl][n][rr]
   double *part;   // 3 * grid partial sums
   struct Barrier *bar;
   int *err;       // set to 1 when a grid barrier wait runs out
   double *out;    // [0] iterations, [1] final ||r||^2
+  unsigned long long *trace;  // optional phase timestamps of CTA 0 (null: off)
+  int trace_cap;
   int rl, rr, Rl, Rr, n, p;
   double tol2;    // stop when ||b - B x||^2 <= tol2
   int maxit;
+  int slots;      // band systems staged per CTA at a time (set by pcg_fused_grid)
+  int smem;       // dynamic shared memory bytes (set by pcg_fused_grid)
 };
 
 // Number of CTAs for the cooperative launch (all co-resident).
-template <typename T> int pcg_fused_grid(Ctx *c, const PcgArgs<T> &a);
+template <typename T> int pcg_fused_grid(Ctx *c, PcgArgs<T> &a);
 // Launch on the context stream; bar must hold 8 zeroed-or-stale bytes (reset here).
 template <typename T> void pcg_fused(Ctx *c, PcgArgs<T> a, int grid);
 

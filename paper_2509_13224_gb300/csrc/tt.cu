@@ -83,6 +83,12 @@ __global__ void k_svt(const double *S, const double *V, int k, int r, double *W)
   }
 }
 
+void svt(Ctx *c, const double *S, const double *V, int k, int r, double *W) {
+  if (r <= 0 || k <= 0) return;
+  k_svt<<<grid1d((long long)r * k, 256), 256, 0, c->stream>>>(S, V, k, r, W);
+  TTI_LAUNCH();
+}
+
 // Orthogonalise core k (k = 2 or 1, 0-based 2 / 1) from the right: core_k = L Q
 // with Q orthonormal rows; L merged into core_{k-1}.
 void orth_right_step(Ctx *c, TT3 &x, int k) {

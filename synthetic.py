@@ -23,6 +23,8 @@ WORKLOADS = {
                                 "round_tol": 1e-12, "modes": []},
     "quarter_cylinder_p3_n128": {"geometry": QUARTER_CYLINDER, "p": 3, "n": 128, "cross_tol": 1e-12,
                                  "round_tol": 1e-12, "modes": [], "sweep": [16, 32, 64, 128]},
+    "quarter_cylinder_p3_n64": {"geometry": QUARTER_CYLINDER, "p": 3, "n": 64, "cross_tol": 1e-12,
+                                "round_tol": 1e-12, "modes": []},
     "twisted_annulus_p3_n512": {"geometry": TWISTED_ANNULUS, "p": 3, "n": 512, "cross_tol": 1e-10,
                                 "round_tol": 1e-10, "modes": []},
 }

@@ -116,6 +116,22 @@ def test_stiffness_and_load_cores_match_definition(tt, ctx, n, p, r0, r1):
     assert np.max(np.abs(F.cpu().numpy() - ref)) < 1e-13 * np.max(np.abs(ref))
 
 
+@pytest.mark.parametrize("m,n,k", [(1260, 18, 9), (10, 1134, 30), (10, 20, 1260), (4, 30, 504), (70, 70, 70),
+                                   (300, 5, 2000), (3, 3, 100000), (129, 257, 33), (1, 1, 1), (64, 64, 0)])
+@pytest.mark.parametrize("ta,tb", [(0, 0), (1, 0), (0, 1), (1, 1)])
+def test_gemm_matches_numpy(tt, ctx, m, n, k, ta, tb):
+    """Every tile shape (64x64, 128x16, 16x128, 32x32), split-K and both transposes."""
+    import torch
+    rng = np.random.default_rng(m * 7 + n * 3 + k + 11 * ta + 5 * tb)
+    A = rng.standard_normal((k, m) if ta else (m, k))
+    B = rng.standard_normal((n, k) if tb else (k, n))
+    C0 = rng.standard_normal((m, n))
+    C = _t(C0.copy())
+    tt.tt_iga_gemm_f64(ctx, ta, tb, 1.5, _t(A), _t(B), -0.5, C)
+    ref = 1.5 * (A.T if ta else A) @ (B.T if tb else B) - 0.5 * C0
+    assert np.max(np.abs(C.cpu().numpy() - ref)) <= 1e-13 * max(1.0, np.sqrt(k)) * max(1.0, np.max(np.abs(ref)))
+
+
 @pytest.mark.parametrize("m,k", [(1000, 37), (100000, 16), (5000, 128), (7, 20), (300, 1), (2048, 256)])
 def test_qr(tt, ctx, m, k):
     import torch
