@@ -174,11 +174,13 @@ int tt_iga_system_info(const tt_iga_system *s, int op_ranks[2], int n_rhs_max, i
 enum { TT_IGA_FP64 = 0, TT_IGA_MIXED_FP32 = 1, TT_IGA_MIXED_TF32 = 2 };
 
 /* AMEn options (Section 4.1.2).  tol: target relative residual
- * ||F - K u||_2 / ||F||_2.  precision FP64: every contraction in FP64;
- * MIXED_*: local linear solves run in FP32 (SIMT) or TF32 (tensor cores, FP32
- * accumulation) inside FP64 iterative refinement of each local system, while
- * interfaces, residuals, QR/SVD truncation stay FP64.  Zero fields take the
- * defaults in brackets. */
+ * ||F - K u||_2 / ||F||_2.  precision FP64: every operator application,
+ * inner product, residual and update in FP64 (the band block-Jacobi
+ * preconditioner of the local PCG is factorised in FP64 and applied in FP32;
+ * it shapes the iteration only).  MIXED_FP32: the local PCG runs in FP32
+ * inside FP64 iterative refinement of each local system; interfaces,
+ * residuals and QR/SVD truncation stay FP64.  MIXED_TF32 is reserved and
+ * returns TT_IGA_ERR_ARG.  Zero fields take the defaults in brackets. */
 typedef struct {
   double tol;       /* [1e-8] */
   int precision;    /* [TT_IGA_FP64] */

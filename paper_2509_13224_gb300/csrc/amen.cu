@@ -238,8 +238,8 @@ struct Amen {
     a.tol2 = tol * tol;
     a.maxit = maxit;
     const int grid = pcg_fused_grid<T>(c, a);
-    DBuf vec(c, 5 * N * sizeof(T)), t1(c, (size_t)a.rl * a.n * a.rr * a.Rr * sizeof(T)),
-        t2(c, (size_t)a.Rl * a.rl * a.n * a.rr * sizeof(T)), aux(c, (3 * (size_t)grid + 8) * sizeof(double));
+    DBuf vec(c, 5 * N * sizeof(T)), t1(c, (size_t)grid * a.t1_stride * sizeof(T)),
+        t2(c, (size_t)grid * a.t2_stride * sizeof(T)), aux(c, (3 * (size_t)grid + 8) * sizeof(double));
     a.r = vec.as<T>(); a.z = a.r + N; a.pv = a.z + N; a.pv2 = a.pv + N; a.q = a.pv2 + N;
     a.T1 = t1.as<T>(); a.T2 = t2.as<T>();
     a.part = aux.d();
@@ -249,7 +249,7 @@ struct Amen {
     c->zero(a.err, sizeof(int));
     DBuf trace;
     if (o.verbose >= 2) {
-      a.trace_cap = 2 + 4 * 64;
+      a.trace_cap = 2 + 2 * 128;
       trace = DBuf(c, a.trace_cap * sizeof(unsigned long long));
       a.trace = trace.as<unsigned long long>();
     }
@@ -259,19 +259,16 @@ struct Amen {
     if (o.verbose >= 2) {
       std::vector<unsigned long long> tr(a.trace_cap);
       c->d2h(tr.data(), a.trace, tr.size() * sizeof(unsigned long long));
-      const int iters = std::min((int)hout[0], 64);
-      double ph[4] = {0, 0, 0, 0};
+      const int iters = std::min((int)hout[0], 128);
+      double ph[2] = {0, 0};
       for (int i = 0; i < iters; ++i) {
-        unsigned long long prev = tr[1 + 4 * i];
-        for (int q = 0; q < 4; ++q) {
-          ph[q] += (double)(tr[2 + 4 * i + q] - prev);
-          prev = tr[2 + 4 * i + q];
-        }
+        ph[0] += (double)(tr[2 + 2 * i] - tr[1 + 2 * i]);
+        ph[1] += (double)(tr[3 + 2 * i] - tr[2 + 2 * i]);
       }
-      fprintf(stderr, "[tt_iga pcg] core %d %s grid %d n %d rl %d rr %d R %d/%d it %d init %.1f us, per iteration A %.1f B %.1f C %.1f E %.1f us\n",
-              k, sizeof(T) == 8 ? "fp64" : "fp32", grid, a.n, a.rl, a.rr, a.Rl, a.Rr, (int)hout[0],
-              (tr[1] - tr[0]) * 1e-3, iters ? ph[0] / iters * 1e-3 : 0.0, iters ? ph[1] / iters * 1e-3 : 0.0,
-              iters ? ph[2] / iters * 1e-3 : 0.0, iters ? ph[3] / iters * 1e-3 : 0.0);
+      fprintf(stderr, "[tt_iga pcg] core %d %s grid %d slab %d n %d rl %d rr %d R %d/%d it %d init %.1f us, per iteration "
+                      "dense %.1f band %.1f us\n",
+              k, sizeof(T) == 8 ? "fp64" : "fp32", grid, a.slab, a.n, a.rl, a.rr, a.Rl, a.Rr, (int)hout[0],
+              (tr[1] - tr[0]) * 1e-3, iters ? ph[0] / iters * 1e-3 : 0.0, iters ? ph[1] / iters * 1e-3 : 0.0);
     }
     int err = 0;
     memcpy(&err, &hout[3], sizeof(int));

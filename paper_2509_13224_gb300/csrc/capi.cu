@@ -280,8 +280,8 @@ int tt_iga_solve(tt_iga_ctx *c, const tt_iga_system *s, const tt_iga_solve_opts 
   if (o.max_rank <= 0) o.max_rank = 256;
   o.max_rank = std::min(o.max_rank, 240);
   if (o.local_maxit <= 0) o.local_maxit = 500;
-  TTI_CHECK_ARG(o.precision >= TT_IGA_FP64 && o.precision <= TT_IGA_MIXED_TF32, "solve: unknown precision %d",
-                o.precision);
+  TTI_CHECK_ARG(o.precision == TT_IGA_FP64 || o.precision == TT_IGA_MIXED_FP32,
+                "solve: precision %d not available (FP64 and MIXED_FP32 are built)", o.precision);
   TTI_CHECK_ARG(o.rhs_index >= 0 && o.rhs_index < (int)s->F.size(), "solve: rhs_index %d out of range", o.rhs_index);
   auto *U = new tt_iga_solution();
   std::unique_ptr<tt_iga_solution> guard(U);

@@ -502,6 +502,7 @@ void qr(Ctx *c, int m, int k, const double *A, long long lda, double *Q, double 
     rows = (long long)top.nblk * k;
   }
   TTI_CUDA(cudaMemcpyAsync(R, lv.back().Rs.d(), (size_t)k * k * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
+  if (!Q) return;  // R only: the orthogonal factor is not formed
   DBuf Cbuf;
   const double *Cin = nullptr;
   for (int L = (int)lv.size() - 1; L >= 0; --L) {

@@ -20,7 +20,8 @@ double host_nrm2(Ctx *c, const double *x, long long n);
 double host_dot(Ctx *c, const double *x, const double *y, long long n);
 
 // Tall-skinny QR: A (m x k, row-major, lda) = Q (m x k, ld k) R (k x k upper).
-// For m < k the columns m..k-1 of Q and rows m..k-1 of R are zero.
+// For m < k the columns m..k-1 of Q and rows m..k-1 of R are zero.  Q may be
+// null: then only R is computed (the form-Q tree is skipped).
 void qr(Ctx *c, int m, int k, const double *A, long long lda, double *Q, double *R);
 
 // SVD of a k x k row-major matrix: A = U diag(s) V^T, s descending (k <= 256).

@@ -209,12 +209,8 @@ __device__ __forceinline__ void band_systems(const PcgArgs<T> &a, const T *__res
 template <typename T, int PB>
 __global__ void __launch_bounds__(256, 1) k_pcg_fused(PcgArgs<T> a) {
   const int rl = a.rl, rr = a.rr, Rl = a.Rl, Rr = a.Rr, n = a.n, b = 2 * PB + 1;
-  const long long N = (long long)rl * n * rr;
-  const long long nA = (long long)rl * n * rr * Rr, nB = (long long)Rl * rl * n * rr;
-  const long long tid = blockIdx.x * (long long)blockDim.x + threadIdx.x, nth = (long long)gridDim.x * blockDim.x;
   const unsigned int G = gridDim.x;
   double *p_pq = a.part, *p_rr = a.part + G, *p_rz = a.part + 2 * G;
-  (void)N;
 
   int slot = 0;
   trace_mark(a.trace, a.trace_cap, slot);
@@ -232,63 +228,83 @@ __global__ void __launch_bounds__(256, 1) k_pcg_fused(PcgArgs<T> a) {
     const double beta = (it == 0 || rz_prev == 0.0) ? 0.0 : rz / rz_prev;
     T *pcur = (it & 1) ? a.pv2 : a.pv;
     const T *pprev = (it & 1) ? a.pv : a.pv2;
-    // A: p = z + beta p_prev (rows written once), T1[(aa, j)][(c, d)] = sum_f p[aa][j][f] PhiR[c][d][f]
-    for (long long e = tid; e < nA; e += nth) {
-      const int d = (int)(e % Rr);
-      long long t = e / Rr;
-      const int c = (int)(t % rr);
-      const long long row = t / rr;  // aa * n + j
-      const T *zr = a.z + row * rr;
-      const T *pr = pprev + row * rr;
-      const T *ph = a.PhiR + ((long long)c * Rr + d) * rr;
-      const bool writer = (c == 0 && d == 0);
-      T s = T(0);
-      for (int f = 0; f < rr; ++f) {
-        const T pf = (it == 0) ? zr[f] : zr[f] + (T)beta * pr[f];
-        if (writer) pcur[row * rr + f] = pf;
-        s += pf * ph[f];
-      }
-      a.T1[e] = s;
-    }
-    if (!grid_sync(a.bar, G, a.err)) return;
-    trace_mark(a.trace, a.trace_cap, slot);
-    // B: T2[g][aa][i][c] = sum_{o, d} A[g][i][o][d] T1[aa][i+o-p][c][d]
-    for (long long e = tid; e < nB; e += nth) {
-      const int c = (int)(e % rr);
-      long long t = e / rr;
-      const int i = (int)(t % n);
-      t /= n;
-      const int aa = (int)(t % rl);
-      const int g = (int)(t / rl);
-      const T *Ar = a.A + ((long long)g * n + i) * b * Rr;
-      T s0 = T(0), s1 = T(0);  // two chains: halves the dependent FMA latency
-#pragma unroll
-      for (int o = 0; o < b; ++o) {
-        const int j = i + o - PB;
-        if (j < 0 || j >= n) continue;
-        const T *Ao = Ar + o * Rr;
-        const T *Tj = a.T1 + (((long long)aa * n + j) * rr + c) * Rr;
-        if (o & 1)
-          for (int d = 0; d < Rr; ++d) s1 += Ao[d] * Tj[d];
-        else
-          for (int d = 0; d < Rr; ++d) s0 += Ao[d] * Tj[d];
-      }
-      a.T2[e] = s0 + s1;
-    }
-    if (!grid_sync(a.bar, G, a.err)) return;
-    trace_mark(a.trace, a.trace_cap, slot);
-    // C: q[al][i][c] = sum_{g, aa} PhiL[al][g][aa] T2[g][aa][i][c];  <p, q>
+    // A+B+C on slabs of S mode rows, one slab per CTA at a time, so only CTA barriers
+    // are needed: T1 on the slab plus its +-p halo rows (recomputed from z and p_prev),
+    // T2 and q on the slab rows, <p, q> partial.  p rows of the slab are written once.
     double pq_loc = 0.0;
-    for (long long e = tid; e < (long long)rl * n * rr; e += nth) {
-      const long long ic = e % ((long long)n * rr);
-      const int al = (int)(e / ((long long)n * rr));
-      const T *ph = a.PhiL + (long long)al * Rl * rl;
-      T s4[4] = {T(0), T(0), T(0), T(0)};  // four chains over the (g, aa) sum
-      const int ga = Rl * rl;
-      for (int q = 0; q < ga; ++q) s4[q & 3] += ph[q] * a.T2[(long long)q * n * rr + ic];
-      const T s = (s4[0] + s4[1]) + (s4[2] + s4[3]);
-      a.q[e] = s;
-      pq_loc += (double)pcur[e] * (double)s;
+    {
+      const int S = a.slab, nslab = (n + S - 1) / S;
+      T *T1s = a.T1 + (long long)blockIdx.x * a.t1_stride;
+      T *T2s = a.T2 + (long long)blockIdx.x * a.t2_stride;
+      for (int sl = blockIdx.x; sl < nslab; sl += G) {
+        const int i0 = sl * S, i1 = min(n, i0 + S);
+        const int j0 = max(0, i0 - PB), j1 = min(n, i1 + PB);
+        const int nj = j1 - j0, ni = i1 - i0;
+        // A: T1s[aa][jj][c][d] = sum_f p[aa][j][f] PhiR[c][d][f], p = z + beta p_prev
+        const int nA1 = rl * nj * rr * Rr;
+        for (int e = threadIdx.x; e < nA1; e += blockDim.x) {
+          const int d = e % Rr;
+          int t = e / Rr;
+          const int c = t % rr;
+          t /= rr;
+          const int jj = t % nj, aa = t / nj;
+          const int j = j0 + jj;
+          const long long row = (long long)aa * n + j;
+          const T *zr = a.z + row * rr;
+          const T *pr = pprev + row * rr;
+          const T *ph = a.PhiR + ((long long)c * Rr + d) * rr;
+          const bool writer = (c == 0 && d == 0 && j >= i0 && j < i1);
+          T s0 = T(0), s1 = T(0);
+          for (int f = 0; f < rr; ++f) {
+            const T pf = (it == 0) ? zr[f] : zr[f] + (T)beta * pr[f];
+            if (writer) pcur[row * rr + f] = pf;
+            if (f & 1) s1 += pf * ph[f]; else s0 += pf * ph[f];
+          }
+          T1s[e] = s0 + s1;
+        }
+        __syncthreads();
+        // B: T2s[g][aa][ii][c] = sum_{o, d} A[g][i][o][d] T1s[aa][i+o-p-j0][c][d]
+        const int nB1 = Rl * rl * ni * rr;
+        for (int e = threadIdx.x; e < nB1; e += blockDim.x) {
+          const int c = e % rr;
+          int t = e / rr;
+          const int ii = t % ni;
+          t /= ni;
+          const int aa = t % rl, g = t / rl;
+          const int i = i0 + ii;
+          const T *Ar = a.A + ((long long)g * n + i) * b * Rr;
+          T s0 = T(0), s1 = T(0);
+#pragma unroll
+          for (int o = 0; o < b; ++o) {
+            const int j = i + o - PB;
+            if (j < 0 || j >= n) continue;
+            const T *Ao = Ar + o * Rr;
+            const T *Tj = T1s + (((long long)aa * nj + (j - j0)) * rr + c) * Rr;
+            if (o & 1)
+              for (int d = 0; d < Rr; ++d) s1 += Ao[d] * Tj[d];
+            else
+              for (int d = 0; d < Rr; ++d) s0 += Ao[d] * Tj[d];
+          }
+          T2s[e] = s0 + s1;
+        }
+        __syncthreads();
+        // C: q[al][i][c] = sum_{g, aa} PhiL[al][g][aa] T2s[g][aa][ii][c];  <p, q>
+        const int nC1 = rl * ni * rr;
+        const int ga = Rl * rl;
+        for (int e = threadIdx.x; e < nC1; e += blockDim.x) {
+          const int c = e % rr;
+          const int t = e / rr;
+          const int ii = t % ni, al = t / ni;
+          const T *ph = a.PhiL + (long long)al * ga;
+          T s4[4] = {T(0), T(0), T(0), T(0)};
+          for (int q = 0; q < ga; ++q) s4[q & 3] += ph[q] * T2s[((long long)q * ni + ii) * rr + c];
+          const T sv = (s4[0] + s4[1]) + (s4[2] + s4[3]);
+          const long long idx = ((long long)al * n + i0 + ii) * rr + c;
+          a.q[idx] = sv;
+          pq_loc += (double)pcur[idx] * (double)sv;
+        }
+        __syncthreads();
+      }
     }
     cta_partial(pq_loc, p_pq);
     if (!grid_sync(a.bar, G, a.err)) return;
@@ -339,8 +355,8 @@ template <typename T> static int band_slots(const PcgArgs<T> &a) {
 }
 
 template <typename T> int pcg_fused_grid(Ctx *c, PcgArgs<T> &a) {
-  // One thread per output of the widest dense phase, at least enough CTAs for the
-  // band systems, all CTAs co-resident.
+  // Slabs of S mode rows for the dense phase (at least 256 band-stage outputs
+  // each), enough CTAs for the slabs and for the band systems, all co-resident.
   const void *k = pick<T>(a.p);
   a.slots = band_slots(a);
   a.smem = (int)((size_t)a.slots * a.n * (a.p + 2) * sizeof(float));
@@ -350,11 +366,17 @@ template <typename T> int pcg_fused_grid(Ctx *c, PcgArgs<T> &a) {
   int per_sm = 0;
   TTI_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, 256, a.smem));
   TTI_CHECK_ARG(per_sm >= 1, "pcg: kernel does not fit on an SM");
-  const long long nA = (long long)a.rl * a.n * a.rr * a.Rr, nB = (long long)a.Rl * a.rl * a.n * a.rr;
-  const long long npair = (long long)a.rl * a.rr;
-  long long g = std::max((std::max(nA, nB) + 255) / 256, (npair + a.slots - 1) / a.slots);
   const long long cap = (long long)c->num_sms * std::max(1, std::min(per_sm, 2));
+  const long long row_out = (long long)a.Rl * a.rl * a.rr;
+  long long S = std::max<long long>((256 + row_out - 1) / row_out, (a.n + cap - 1) / cap);
+  S = std::max<long long>(1, std::min<long long>(S, a.n));
+  a.slab = (int)S;
+  const long long nslab = (a.n + S - 1) / S;
+  const long long npair = (long long)a.rl * a.rr;
+  long long g = std::max(nslab, (npair + a.slots - 1) / a.slots);
   g = std::max<long long>(1, std::min(g, cap));
+  a.t1_stride = (long long)a.rl * (S + 2 * a.p) * a.rr * a.Rr;
+  a.t2_stride = (long long)a.Rl * a.rl * S * a.rr;
   return (int)g;
 }
 

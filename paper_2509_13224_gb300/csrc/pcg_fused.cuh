@@ -11,8 +11,8 @@ template <typename T> struct PcgArgs {
   const float *Lf;  // band Cholesky factors [n][p+1][rl*rr] (FP32; reciprocal diagonal in slot p)
   const T *b;     // right-hand side [rl][n][rr]
   T *x, *r, *z, *pv, *pv2, *q;  // solution and work vectors [rl][n][rr] (pv, pv2: p double buffer)
-  T *T1;          // [rl][n][rr][Rr]
-  T *T2;          // [Rl][rl][n][rr]
+  T *T1;          // per-CTA slab scratch, grid x t1_stride: [rl][S+2p][rr][Rr]
+  T *T2;          // per-CTA slab scratch, grid x t2_stride: [Rl][rl][S][rr]
   double *part;   // 3 * grid partial sums
   struct Barrier *bar;
   int *err;       // set to 1 when a grid barrier wait runs out
@@ -23,6 +23,8 @@ template <typename T> struct PcgArgs {
   double tol2;    // stop when ||b - B x||^2 <= tol2
   int maxit;
   int slots;      // band systems staged per CTA at a time (set by pcg_fused_grid)
+  int slab;       // mode rows per slab of the dense phase (set by pcg_fused_grid)
+  long long t1_stride, t2_stride;  // per-CTA scratch sizes in elements (set by pcg_fused_grid)
   int smem;       // dynamic shared memory bytes (set by pcg_fused_grid)
 };
 

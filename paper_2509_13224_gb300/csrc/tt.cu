@@ -112,10 +112,24 @@ double tt_orth_rl(Ctx *c, TT3 &x) {
   return host_nrm2(c, x.core[0].d(), (long long)x.core_elems(0));
 }
 
+// ||X||_F by a right-to-left sweep of R factors only: core 3 = L3 Q3 (R of the
+// transposed core), core 2 <- core 2 L3, core 2 = L2 Q2, core 1 <- core 1 L2,
+// ||X|| = ||core 1||.  The orthogonal factors are never formed.
 double tt_norm(Ctx *c, const TT3 &x) {
-  TT3 y;
-  tt_copy(c, x, y);
-  return tt_orth_rl(c, y);
+  const int m1 = x.m[0], m2 = x.m[1], m3 = x.m[2], r1 = x.r[1], r2 = x.r[2];
+  // core 3 is r2 x m3: QR of its transpose (m3 x r2) gives R3; core 3 = R3^T Q3^T
+  DBuf T3(c, (size_t)m3 * r2 * sizeof(double)), R3(c, (size_t)r2 * r2 * sizeof(double));
+  transpose(c, x.core[2].d(), T3.d(), r2, m3);
+  qr(c, m3, r2, T3.d(), r2, nullptr, R3.d());
+  // core 2 (r1 m2 x r2) times R3^T
+  DBuf C2(c, (size_t)r1 * m2 * r2 * sizeof(double));
+  gemm<double>(c, false, true, r1 * m2, r2, r2, 1.0, x.core[1].d(), r2, 0, R3.d(), r2, 0, 0.0, C2.d(), r2, 0, 1);
+  DBuf T2(c, (size_t)m2 * r2 * r1 * sizeof(double)), R2(c, (size_t)r1 * r1 * sizeof(double));
+  transpose(c, C2.d(), T2.d(), r1, (long long)m2 * r2);
+  qr(c, m2 * r2, r1, T2.d(), r1, nullptr, R2.d());
+  DBuf C1(c, (size_t)m1 * r1 * sizeof(double));
+  gemm<double>(c, false, true, m1, r1, r1, 1.0, x.core[0].d(), r1, 0, R2.d(), r1, 0, 0.0, C1.d(), r1, 0, 1);
+  return host_nrm2(c, C1.d(), (long long)m1 * r1);
 }
 
 // Left-to-right truncation step at core k (0 or 1) with absolute threshold delta.
