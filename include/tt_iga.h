@@ -70,7 +70,10 @@ typedef struct {
                   * library creates its own non-blocking stream */
   int device;    /* CUDA device ordinal */
   /* Optional device allocator (both or neither).  NULL: stream-ordered
-   * cudaMallocAsync / cudaFreeAsync on the context stream. */
+   * cudaMallocAsync / cudaFreeAsync on the context stream.  Returned pointers
+   * must be 256-byte aligned, as cudaMalloc's are (bulk copies into shared
+   * memory need 16); a misaligned pointer is handed back to free_fn and the
+   * call fails with TT_IGA_ERR_ARG. */
   void *(*alloc_fn)(size_t bytes, void *stream, void *user);
   void (*free_fn)(void *ptr, void *stream, void *user);
   void *alloc_user;

@@ -26,6 +26,7 @@
 
 #include "amen.cuh"
 #include "amen_ops.cuh"
+#include "bbprec.cuh"
 #include "linalg.cuh"
 #include "pcg_fused.cuh"
 #include "tt.cuh"
@@ -230,10 +231,16 @@ struct Amen {
   // PCG on B d = r (type T), d starts at zero; one cooperative launch for all
   // iterations.  Absolute tolerance tol on ||r - B d||.  Returns iterations.
   template <typename T>
-  int pcg(int k, const T *PhiLk, const T *PhiRk, const T *Ak, const float *L, const T *b, T *x, double tol, int maxit) {
+  int pcg(int k, const T *PhiLk, const T *PhiRk, const T *Ak, const float *L, const BBPrec *bb, const T *b, T *x,
+          double tol, int maxit) {
     const long long N = (long long)rl(k) * n(k) * rr(k);
     PcgArgs<T> a{};
     a.PhiL = PhiLk; a.PhiR = PhiRk; a.A = Ak; a.Lf = L; a.b = b; a.x = x;
+    if (bb) {
+      a.edge = 1;
+      a.bbLinv = bb->Linv.as<float>(); a.bbG = bb->G.as<float>(); a.bbH = bb->H.as<float>();
+      a.bbM = bb->M;
+    }
     a.rl = rl(k); a.rr = rr(k); a.Rl = R[k]; a.Rr = R[k + 1]; a.n = n(k); a.p = S->p;
     a.tol2 = tol * tol;
     a.maxit = maxit;
@@ -249,7 +256,7 @@ struct Amen {
     c->zero(a.err, sizeof(int));
     DBuf trace;
     if (o.verbose >= 2) {
-      a.trace_cap = 2 + 2 * 128;
+      a.trace_cap = 2 + 2 * 128 + 8;
       trace = DBuf(c, a.trace_cap * sizeof(unsigned long long));
       a.trace = trace.as<unsigned long long>();
     }
@@ -265,22 +272,32 @@ struct Amen {
         ph[0] += (double)(tr[2 + 2 * i] - tr[1 + 2 * i]);
         ph[1] += (double)(tr[3 + 2 * i] - tr[2 + 2 * i]);
       }
-      fprintf(stderr, "[tt_iga pcg] core %d %s grid %d slab %d n %d rl %d rr %d R %d/%d it %d init %.1f us, per iteration "
-                      "dense %.1f band %.1f us\n",
-              k, sizeof(T) == 8 ? "fp64" : "fp32", grid, a.slab, a.n, a.rl, a.rr, a.Rl, a.Rr, (int)hout[0],
+      fprintf(stderr, "[tt_iga pcg] core %d %s %s grid %d slab %d n %d rl %d rr %d R %d/%d it %d init %.1f us, per "
+                      "iteration dense %.1f precond %.1f us\n",
+              k, sizeof(T) == 8 ? "fp64" : "fp32", a.edge ? "block-band" : "band-jacobi", grid, a.slab, a.n, a.rl, a.rr,
+              a.Rl, a.Rr, (int)hout[0],
               (tr[1] - tr[0]) * 1e-3, iters ? ph[0] / iters * 1e-3 : 0.0, iters ? ph[1] / iters * 1e-3 : 0.0);
+      if (a.edge) {
+        const unsigned long long *sb = tr.data() + 2 + 2 * 128;
+        fprintf(stderr, "[tt_iga pcg]   block-band apply: update %.1f, L^-1 r %.1f, forward %.1f, L^-T y %.1f, "
+                        "backward %.1f, scatter %.1f us\n",
+                (sb[1] - sb[0]) * 1e-3, (sb[2] - sb[1]) * 1e-3, (sb[3] - sb[2]) * 1e-3, (sb[4] - sb[3]) * 1e-3,
+                (sb[5] - sb[4]) * 1e-3, (sb[6] - sb[5]) * 1e-3);
+      }
     }
     int err = 0;
     memcpy(&err, &hout[3], sizeof(int));
-    if (err) fail(TT_IGA_ERR_TIMEOUT, "pcg: a grid barrier wait ran out");
+    if (err) fail(TT_IGA_ERR_TIMEOUT, "pcg: a %s wait ran out", err == 2 ? "staging copy" : "grid barrier");
     const int it = (int)hout[0];
     last_pcg_converged = (it < maxit) && hout[1] <= a.tol2;
     {
       // algorithmic FLOPs per PCG iteration: right-interface, band and left-interface stages
       // of the local matvec plus the two band triangular solves of the preconditioner
       const double rl_ = a.rl, rr_ = a.rr, n_ = a.n, Rl_ = a.Rl, Rr_ = a.Rr, b_ = 2.0 * a.p + 1.0;
+      const double m_ = rl_ * rr_;
+      const double f_prec = a.edge ? 4.0 * n_ * (a.p + 1) * m_ * m_ : 4.0 * m_ * n_ * (a.p + 1);
       const double f_iter = 2.0 * rl_ * n_ * rr_ * Rr_ * rr_ + 2.0 * Rl_ * rl_ * n_ * rr_ * b_ * Rr_ +
-                            2.0 * rl_ * n_ * rr_ * Rl_ * rl_ + 4.0 * rl_ * rr_ * n_ * (a.p + 1) + 10.0 * N;
+                            2.0 * rl_ * n_ * rr_ * Rl_ * rl_ + f_prec + 10.0 * N;
       prof_set_last_work(c, PROF_PCG_FUSED, f_iter * it);
     }
     st.local_matvecs += it;
@@ -299,23 +316,54 @@ struct Amen {
     if (res0 <= tol_abs) return res0;
     const int maxit = o.local_maxit;
     const size_t Lsz = (size_t)n(k) * (S->p + 1) * rl(k) * rr(k);
-    if (o.precision == TT_IGA_FP64) {
-      // the preconditioner's factors are computed in FP64 and applied in FP32 (see pcg_fused.cu)
-      DBuf L(c, Lsz * sizeof(float)), d(c, N * sizeof(double));
+    // Small interface blocks (m = rl rr <= 16): exact block-band preconditioner.
+    // Otherwise band block-Jacobi over the interface pairs.
+    const bool edge = bb_eligible(rl(k) * rr(k), n(k), S->p);
+    BBPrec bb;
+    DBuf L;
+    if (edge) {
+      cudaEvent_t ev[2] = {nullptr, nullptr};
+      DBuf clk;
+      if (o.verbose >= 2) {
+        clk = DBuf(c, 4 * sizeof(unsigned long long));
+        TTI_CUDA(cudaEventCreate(&ev[0]));
+        TTI_CUDA(cudaEventCreate(&ev[1]));
+        TTI_CUDA(cudaEventRecord(ev[0], c->stream));
+      }
+      bb_prec_build(c, PhiL[k].d(), rl(k), A[k], PhiR[k].d(), rr(k), bb, clk.as<unsigned long long>());
+      if (o.verbose >= 2) {
+        float ms = 0.f;
+        unsigned long long ck[3];
+        TTI_CUDA(cudaEventRecord(ev[1], c->stream));
+        TTI_CUDA(cudaEventSynchronize(ev[1]));
+        TTI_CUDA(cudaEventElapsedTime(&ms, ev[0], ev[1]));
+        c->d2h(ck, clk.get(), sizeof(ck));
+        fprintf(stderr, "[tt_iga pcg] core %d block-band preconditioner (m %d n %d): build+factor+post %.1f us; "
+                        "factor cycles/step: diagonal %.0f panel %.0f update %.0f\n", k, rl(k) * rr(k), n(k),
+                ms * 1e3, (double)ck[0] / n(k), (double)ck[1] / n(k), (double)ck[2] / n(k));
+        cudaEventDestroy(ev[0]);
+        cudaEventDestroy(ev[1]);
+      }
+    } else {
+      L = DBuf(c, Lsz * sizeof(float));
       precond_build<float>(c, PhiL[k].d(), rl(k), A[k], PhiR[k].d(), rr(k), L.as<float>());
+    }
+    const BBPrec *bbp = edge ? &bb : nullptr;
+    if (o.precision == TT_IGA_FP64) {
+      // preconditioner factors in FP32 (see pcg_fused.cu, bbprec.cu)
+      DBuf d(c, N * sizeof(double));
       // correction form: B d = r, x += d, checked in FP64
       // correction form B d = r; in FP64 the PCG recurrence residual is the residual of
       // x + d to working accuracy, so an explicit check is only needed when PCG stopped early
       for (int rep = 0; rep < 3; ++rep) {
-        pcg<double>(k, PhiL[k].d(), PhiR[k].d(), A[k].A, L.as<float>(), rbuf.d(), d.d(), 0.5 * tol_abs, maxit);
+        pcg<double>(k, PhiL[k].d(), PhiR[k].d(), A[k].A, L.as<float>(), bbp, rbuf.d(), d.d(), 0.5 * tol_abs, maxit);
         axpy<double>(c, N, 1.0, d.d(), x);
         if (last_pcg_converged) break;
         if (residual64(k, rhs, x, rbuf.d()) <= tol_abs) break;
       }
     } else {
       // FP32 PCG on the correction inside FP64 iterative refinement.
-      DBuf L(c, Lsz * sizeof(float)), d32(c, N * sizeof(float)), r32(c, N * sizeof(float)), d64(c, N * sizeof(double));
-      precond_build<float>(c, PhiL[k].d(), rl(k), A[k], PhiR[k].d(), rr(k), L.as<float>());
+      DBuf d32(c, N * sizeof(float)), r32(c, N * sizeof(float)), d64(c, N * sizeof(double));
       const long long nl = (long long)rl(k) * R[k] * rl(k), nr = (long long)rr(k) * R[k + 1] * rr(k);
       DBuf pl(c, nl * sizeof(float)), pr(c, nr * sizeof(float));
       convert_f64_to_f32(c, PhiL[k].d(), pl.as<float>(), nl);
@@ -325,7 +373,7 @@ struct Amen {
         // scale the residual to unit norm so FP32 keeps its relative precision
         convert_f64_to_f32(c, rbuf.d(), r32.as<float>(), N);
         scale<float>(c, r32.as<float>(), N, (float)(1.0 / res));
-        pcg<float>(k, pl.as<float>(), pr.as<float>(), A[k].A32, L.as<float>(), r32.as<float>(), d32.as<float>(),
+        pcg<float>(k, pl.as<float>(), pr.as<float>(), A[k].A32, L.as<float>(), bbp, r32.as<float>(), d32.as<float>(),
                    std::max(1e-5, 0.5 * tol_abs / res), maxit);
         convert_f32_to_f64(c, d32.as<float>(), d64.d(), N);
         axpy<double>(c, N, res, d64.d(), x);

@@ -145,58 +145,69 @@ __global__ void k_diag_interface(const double *Phi, int r, int R, double *D) {
 // k < PB and the reciprocal of the diagonal in slot PB.  With j = i-PB+k,
 //   L(i,j) = (A(i,j) - sum_{m=i-PB}^{j-1} L(i,m) L(j,m)) / L(j,j),
 //   L(i,i) = sqrt(A(i,i) - sum_{m=i-PB}^{i-1} L(i,m)^2).
+// The arithmetic runs in the factor's own type T: the row-to-row recurrence is
+// a chain of dependent operations, and in FP32 each link costs a few cycles
+// instead of the tens to hundreds of an FP64 FMA, square root or divide.  A
+// pivot that cancellation drives to zero or below is replaced by the row's
+// diagonal entry (the factor stays SPD; PCG convergence is checked in FP64);
+// a diagonal entry that is itself not positive flags a breakdown.
 // The previous PB rows of L stay in registers (win[q] = row i-PB+q).
+template <typename T> __device__ __forceinline__ T recip_sqrt(T v);
+template <> __device__ __forceinline__ float recip_sqrt<float>(float v) { return rsqrtf(v); }
+template <> __device__ __forceinline__ double recip_sqrt<double>(double v) { return 1.0 / sqrt(v); }
+
 template <typename T, int PB>
 __global__ void k_band_cholesky(const double *__restrict__ Pm, int rl, int n, int rr, T *__restrict__ L, int *status) {
   const int npair = rl * rr, b = 2 * PB + 1;
   for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < npair; t += gridDim.x * blockDim.x) {
     const int a = t / rr, bb = t % rr;
     const double *Pp = Pm + (long long)a * n * b * rr + bb;
-    double win[PB][PB + 1];
+    T win[PB][PB + 1];
 #pragma unroll
     for (int q = 0; q < PB; ++q)
 #pragma unroll
-      for (int k = 0; k <= PB; ++k) win[q][k] = 0.0;
+      for (int k = 0; k <= PB; ++k) win[q][k] = T(0);
     bool bad = false;
     // symmetrised band entries of a row: A(i, i-PB+k) for k <= PB (loaded one row ahead)
-    auto load_row = [&](int i, double *out) {
+    auto load_row = [&](int i, T *out) {
 #pragma unroll
       for (int k = 0; k < PB; ++k) {
         const int j = i - PB + k;
-        out[k] = (j >= 0) ? 0.5 * (Pp[((long long)i * b + k) * rr] + Pp[((long long)j * b + (2 * PB - k)) * rr]) : 0.0;
+        out[k] = (j >= 0) ? (T)(0.5 * (Pp[((long long)i * b + k) * rr] + Pp[((long long)j * b + (2 * PB - k)) * rr]))
+                          : T(0);
       }
-      out[PB] = Pp[((long long)i * b + PB) * rr];
+      out[PB] = (T)Pp[((long long)i * b + PB) * rr];
     };
-    double nxt[PB + 1];
+    T nxt[PB + 1];
     load_row(0, nxt);
     for (int i = 0; i < n; ++i) {
-      double cur[PB + 1];
+      T cur[PB + 1];
 #pragma unroll
       for (int k = 0; k <= PB; ++k) cur[k] = nxt[k];
       if (i + 1 < n) load_row(i + 1, nxt);
-      double row[PB + 1];
+      T row[PB + 1];
 #pragma unroll
       for (int k = 0; k < PB; ++k) {
         const int j = i - PB + k;
         if (j < 0) {
-          row[k] = 0.0;
+          row[k] = T(0);
           continue;
         }
-        double sv = cur[k];
+        T sv = cur[k];
 #pragma unroll
         for (int mm = 0; mm < k; ++mm) sv -= row[mm] * win[k][mm + PB - k];
         row[k] = sv * win[k][PB];
       }
-      double sd = cur[PB];
+      T sd = cur[PB];
 #pragma unroll
       for (int mm = 0; mm < PB; ++mm) sd -= row[mm] * row[mm];
-      if (!(sd > 0.0)) {
-        bad = true;
-        sd = fabs(sd) + 1e-300;
+      if (!(sd > T(1e-6) * cur[PB])) {
+        if (!(cur[PB] > T(0))) bad = true;
+        sd = (cur[PB] > T(0)) ? cur[PB] : T(1);
       }
-      row[PB] = 1.0 / sqrt(sd);
+      row[PB] = recip_sqrt<T>(sd);
 #pragma unroll
-      for (int k = 0; k <= PB; ++k) L[((long long)i * (PB + 1) + k) * npair + t] = (T)row[k];
+      for (int k = 0; k <= PB; ++k) L[((long long)i * (PB + 1) + k) * npair + t] = row[k];
 #pragma unroll
       for (int q = 0; q + 1 < PB; ++q)
 #pragma unroll

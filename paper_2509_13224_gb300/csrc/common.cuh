@@ -118,6 +118,10 @@ struct Ctx {
     if (alloc_fn) {
       p = alloc_fn(bytes, stream, alloc_user);
       if (!p) fail(TT_IGA_ERR_OOM, "allocator callback failed for %zu bytes", bytes);
+      if (reinterpret_cast<uintptr_t>(p) & 255) {
+        free_fn(p, stream, alloc_user);
+        fail(TT_IGA_ERR_ARG, "allocator callback returned a pointer that is not 256-byte aligned");
+      }
     } else {
       cudaError_t e = cudaMallocAsync(&p, bytes, stream);
       if (e != cudaSuccess) fail(TT_IGA_ERR_OOM, "cudaMallocAsync(%zu): %s", bytes, cudaGetErrorString(e));

@@ -15,6 +15,7 @@
 #include <algorithm>
 
 #include "amen_ops.cuh"
+#include "bbprec.cuh"
 #include "pcg_fused.cuh"
 
 namespace ttiga {
@@ -206,6 +207,350 @@ __device__ __forceinline__ void band_systems(const PcgArgs<T> &a, const T *__res
   }
 }
 
+// ---- block-band preconditioner (small interface blocks, CTA 0 only)
+
+__device__ __forceinline__ unsigned smem_u32(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(unsigned long long *bar) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ void mbar_inval(unsigned long long *bar) {
+  asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+// One bulk copy global -> shared of `bytes` (multiple of 16, both addresses
+// 16-byte aligned) completing on `bar`, after the arrival that expects it.
+__device__ __forceinline__ void bulk_load(void *dst, const void *src, unsigned bytes, unsigned long long *bar) {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_u32(dst)),
+               "l"(src), "r"(bytes), "r"(smem_u32(bar))
+               : "memory");
+}
+// Wait for the phase of `bar` with the given parity to complete; false when the
+// poll limit runs out.
+__device__ __forceinline__ bool mbar_wait(unsigned long long *bar, unsigned parity) {
+  const unsigned addr = smem_u32(bar);
+  for (long long spin = 0; spin < kSpinLimit; ++spin) {
+    unsigned done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+        : "=r"(done)
+        : "r"(addr), "r"(parity)
+        : "memory");
+    if (done) return true;
+  }
+  return false;
+}
+
+// Sub-phase timestamp of the block-band apply (init call only, verbose trace).
+__device__ __forceinline__ void bb_mark(unsigned long long *trace, int cap, bool on, int k) {
+  if (on && trace && threadIdx.x == 0 && cap >= 2 + 2 * 128 + 8) {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    trace[2 + 2 * 128 + k] = t;
+  }
+}
+
+// Chunk sequence of one block-band apply: chunks 0..nch-1 hold the forward
+// blocks G (block rows ascending), chunks nch..2nch-1 the backward blocks H
+// (block rows descending), each `ch` block rows of PB blocks [M][S].  Chunk q
+// goes to staging buffer q & 1 and completes on barrier q & 1; ph carries the
+// two barriers' phase parities across applies.
+struct BBStream {
+  const float *G, *H;
+  int n, ch, nch;
+  float *st0, *st1;
+  unsigned long long *bars;
+  unsigned ph;
+};
+
+__device__ __forceinline__ void bb_rows(const BBStream &s, int q, int &lo, int &hi) {
+  if (q < s.nch) {
+    lo = q * s.ch;
+    hi = min(s.n, lo + s.ch);
+  } else {
+    hi = s.n - (q - s.nch) * s.ch;
+    lo = max(0, hi - s.ch);
+  }
+}
+
+// Issue chunk q (one thread).  Its buffer was last read two chunks earlier.
+template <int PB, int M> __device__ __forceinline__ void bb_issue(const BBStream &s, int q) {
+  constexpr int RF = PB * M * bb_stride(M);  // floats per block row
+  int lo, hi;
+  bb_rows(s, q, lo, hi);
+  const float *base = (q < s.nch) ? s.G : s.H;
+  bulk_load((q & 1) ? s.st1 : s.st0, base + (long long)lo * RF, (unsigned)(hi - lo) * RF * sizeof(float),
+            s.bars + (q & 1));
+}
+
+// k >= 2 terms of row i: sum_{k=2..PB} M_ik v_{i-+k} for lane e's row.  Mi is
+// that row in block 1 of row i.  Rows outside 0..n-1 are clamped: their blocks
+// are zero, so the loads need no branch.
+template <int PB, int M>
+__device__ __forceinline__ float bb_far(const float *Mi, const float *v, int i, int n, bool fwd) {
+  constexpr int S = bb_stride(M);
+  float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
+#pragma unroll
+  for (int k = 2; k <= PB; ++k) {
+    const int j = min(max(fwd ? i - k : i + k, 0), n - 1);
+    const float4 *mk = reinterpret_cast<const float4 *>(Mi + (k - 1) * M * S);
+    const float4 *vj = reinterpret_cast<const float4 *>(v + j * M);
+#pragma unroll
+    for (int f4 = 0; f4 < M / 4; ++f4) {
+      const float4 g = mk[f4], w = vj[f4];
+      a0 += g.x * w.x;
+      a1 += g.y * w.y;
+      a2 += g.z * w.z;
+      a3 += g.w * w.w;
+    }
+  }
+  return (a0 + a1) + (a2 + a3);
+}
+
+// Block substitution run by warp 0 over the chunks of one pass: for each block
+// row i (ascending when fwd, else descending), v_i -= sum_{k=1..PB} M_ik v_{i-+k}.
+// Lane e (< M) owns entry e of the row (the other lanes mirror them and do not
+// store).  Only the k = 1 term depends on the row finished in the previous
+// step: the k >= 2 terms and the next row's k = 1 block row are loaded and
+// summed before the warp synchronises, so the dependent path of a step is one
+// read of the previous row, M FMAs in four chains and a store.
+template <int PB, int M> __device__ bool bb_chain(float *v, BBStream &s, bool fwd) {
+  constexpr int S = bb_stride(M), RF = PB * M * S;
+  const int lane = threadIdx.x & 31, e = lane % M;
+  const int q0 = fwd ? 0 : s.nch;
+  const int n = s.n;
+  for (int c = 0; c < s.nch; ++c) {
+    const int q = q0 + c;
+    if (lane == 0 && q + 1 < 2 * s.nch) bb_issue<PB, M>(s, q + 1);
+    const int bsel = q & 1;
+    // warp-uniform outcome: every lane polls, all lanes take the same branch
+    if (!__all_sync(0xffffffffu, mbar_wait(s.bars + bsel, (s.ph >> bsel) & 1u))) {
+      // give the copies in flight one more bounded wait before giving up
+      mbar_wait(s.bars + bsel, (s.ph >> bsel) & 1u);
+      if (q + 1 < 2 * s.nch) mbar_wait(s.bars + (bsel ^ 1), (s.ph >> (bsel ^ 1)) & 1u);
+      return false;
+    }
+    s.ph ^= 1u << bsel;
+    const float *Ms = bsel ? s.st1 : s.st0;
+    int lo, hi;
+    bb_rows(s, q, lo, hi);
+    const int rows = hi - lo;
+    auto row_i = [&](int t) { return fwd ? lo + t : hi - 1 - t; };
+    int i = row_i(0);
+    const float *Mi = Ms + (i - lo) * RF + e * S;
+    float far = bb_far<PB, M>(Mi, v, i, n, fwd);
+    float4 g1[M / 4];
+#pragma unroll
+    for (int f4 = 0; f4 < M / 4; ++f4) g1[f4] = reinterpret_cast<const float4 *>(Mi)[f4];
+    float self = v[i * M + e];
+    for (int t = 0; t < rows; ++t) {
+      const int j1 = min(max(fwd ? i - 1 : i + 1, 0), n - 1);
+      const float4 *vj = reinterpret_cast<const float4 *>(v + j1 * M);
+      float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
+#pragma unroll
+      for (int f4 = 0; f4 < M / 4; ++f4) {
+        const float4 w = vj[f4];
+        a0 += g1[f4].x * w.x;
+        a1 += g1[f4].y * w.y;
+        a2 += g1[f4].z * w.z;
+        a3 += g1[f4].w * w.w;
+      }
+      const float y = self - (far + ((a0 + a1) + (a2 + a3)));
+      if (lane < M) v[i * M + e] = y;
+      if (t + 1 < rows) {
+        // next row: its k >= 2 rows and its own entry are final already
+        i = row_i(t + 1);
+        Mi = Ms + (i - lo) * RF + e * S;
+        far = bb_far<PB, M>(Mi, v, i, n, fwd);
+#pragma unroll
+        for (int f4 = 0; f4 < M / 4; ++f4) g1[f4] = reinterpret_cast<const float4 *>(Mi)[f4];
+        self = v[i * M + e];
+      }
+      __syncwarp();
+    }
+  }
+  return true;
+}
+
+// E phase with the block-band preconditioner, run by CTA 0 alone (the other
+// CTAs contribute zero partials): x += alpha p, r -= alpha q (or x = 0, r = b),
+// then z = L^{-T} L^{-1} r by the two block substitutions; <r, r>, <r, z>.
+// Shared layout: rs[n][M], ys[n][M], two staging buffers of bb_ch block rows.
+// The element loops load a batch of kU entries per thread before computing, so
+// a thread waits for one memory latency per batch rather than per entry.
+constexpr int kU = 4;
+
+template <typename T, int PB, int M>
+__device__ bool bb_apply(const PcgArgs<T> &a, const T *__restrict__ pcur, double alpha, bool init, double &rr_out,
+                         double &rz_out, unsigned long long *bars, unsigned &ph) {
+  constexpr int S = bb_stride(M);
+  bb_mark(a.trace, a.trace_cap, init, 0);
+  extern __shared__ float4 esm4[];
+  const int n = a.n, rr = a.rr, m = a.rl * a.rr, tot = n * M, B = blockDim.x;
+  float *rs = reinterpret_cast<float *>(esm4);
+  float *ys = rs + n * M;
+  BBStream s;
+  s.G = a.bbG;
+  s.H = a.bbH;
+  s.n = n;
+  s.ch = a.bb_ch;
+  s.nch = (n + a.bb_ch - 1) / a.bb_ch;
+  s.st0 = ys + n * M;
+  s.st1 = s.st0 + a.bb_ch * PB * M * S;
+  s.bars = bars;
+  s.ph = ph;
+  if (threadIdx.x == 0) bb_issue<PB, M>(s, 0);  // lands while the element loops run
+  auto index_of = [&](int e) { return ((long long)((e % M) / rr) * n + e / M) * rr + ((e % M) % rr); };
+  double rr_th = 0.0;
+  for (int e0 = threadIdx.x; e0 < tot; e0 += kU * B) {
+    T bx[kU], bq[kU], bp[kU], br[kU];
+#pragma unroll
+    for (int u = 0; u < kU; ++u) {
+      const int e = e0 + u * B;
+      bx[u] = bq[u] = bp[u] = br[u] = T(0);
+      if (e < tot && (e % M) < m) {
+        const long long idx = index_of(e);
+        if (init) {
+          br[u] = a.b[idx];
+        } else {
+          bx[u] = a.x[idx];
+          bp[u] = pcur[idx];
+          br[u] = a.r[idx];
+          bq[u] = a.q[idx];
+        }
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < kU; ++u) {
+      const int e = e0 + u * B;
+      if (e >= tot) continue;
+      float rv = 0.f;
+      if ((e % M) < m) {
+        const long long idx = index_of(e);
+        T r;
+        if (init) {
+          r = br[u];
+          a.x[idx] = T(0);
+        } else {
+          a.x[idx] = bx[u] + (T)alpha * bp[u];
+          r = br[u] - (T)alpha * bq[u];
+        }
+        a.r[idx] = r;
+        rr_th += (double)r * (double)r;
+        rv = (float)r;
+      }
+      rs[e] = rv;
+    }
+  }
+  rr_out += rr_th;
+  __syncthreads();
+  bb_mark(a.trace, a.trace_cap, init, 1);
+  // s_i = L_ii^{-1} r_i
+  for (int e0 = threadIdx.x; e0 < tot; e0 += kU * B) {
+    float4 l4[kU][M / 4];
+#pragma unroll
+    for (int u = 0; u < kU; ++u) {
+      const int e = min(e0 + u * B, tot - 1);
+      const float4 *Li = reinterpret_cast<const float4 *>(a.bbLinv + (long long)(e / M) * M * M + (e % M) * M);
+#pragma unroll
+      for (int f = 0; f < M / 4; ++f) l4[u][f] = Li[f];
+    }
+#pragma unroll
+    for (int u = 0; u < kU; ++u) {
+      const int e = e0 + u * B;
+      if (e >= tot) continue;
+      const float4 *ri = reinterpret_cast<const float4 *>(rs + (e / M) * M);
+      float s0 = 0.f, s1 = 0.f;
+#pragma unroll
+      for (int f = 0; f < M / 4; ++f) {
+        const float4 r4 = ri[f];
+        s0 += l4[u][f].x * r4.x + l4[u][f].z * r4.z;
+        s1 += l4[u][f].y * r4.y + l4[u][f].w * r4.w;
+      }
+      ys[e] = s0 + s1;
+    }
+  }
+  __syncthreads();
+  __shared__ int chain_ok;
+  bb_mark(a.trace, a.trace_cap, init, 2);
+  if (threadIdx.x < 32) {
+    const bool ok = bb_chain<PB, M>(ys, s, true);
+    if (threadIdx.x == 0) chain_ok = ok;
+  }
+  __syncthreads();
+  bb_mark(a.trace, a.trace_cap, init, 3);
+  // t_i = L_ii^{-T} y_i
+  for (int e0 = threadIdx.x; e0 < tot; e0 += kU * B) {
+    float lc[kU][M];
+#pragma unroll
+    for (int u = 0; u < kU; ++u) {
+      const int e = min(e0 + u * B, tot - 1);
+      const float *Li = a.bbLinv + (long long)(e / M) * M * M + (e % M);
+#pragma unroll
+      for (int f = 0; f < M; ++f) lc[u][f] = Li[f * M];
+    }
+#pragma unroll
+    for (int u = 0; u < kU; ++u) {
+      const int e = e0 + u * B;
+      if (e >= tot) continue;
+      const float *yi = ys + (e / M) * M;
+      float s0 = 0.f, s1 = 0.f;
+#pragma unroll
+      for (int f = 0; f < M; f += 2) {
+        s0 += lc[u][f] * yi[f];
+        s1 += lc[u][f + 1] * yi[f + 1];
+      }
+      rs[e] = s0 + s1;
+    }
+  }
+  __syncthreads();
+  bb_mark(a.trace, a.trace_cap, init, 4);
+  if (threadIdx.x < 32 && chain_ok) {
+    const bool ok = bb_chain<PB, M>(rs, s, false);
+    if (threadIdx.x == 0) chain_ok = ok;
+  }
+  if (threadIdx.x < 32) ph = s.ph;  // every lane of warp 0 polls with these parities next time
+  __syncthreads();
+  bb_mark(a.trace, a.trace_cap, init, 5);
+  double rz_th = 0.0;
+  for (int e0 = threadIdx.x; e0 < tot; e0 += kU * B) {
+    T br[kU];
+#pragma unroll
+    for (int u = 0; u < kU; ++u) {
+      const int e = e0 + u * B;
+      br[u] = T(0);
+      if (e < tot && (e % M) < m) br[u] = a.r[index_of(e)];
+    }
+#pragma unroll
+    for (int u = 0; u < kU; ++u) {
+      const int e = e0 + u * B;
+      if (e < tot && (e % M) < m) {
+        const T zi = (T)rs[e];
+        a.z[index_of(e)] = zi;
+        rz_th += (double)br[u] * (double)zi;
+      }
+    }
+  }
+  rz_out += rz_th;
+  const bool ok = chain_ok != 0;
+  __syncthreads();
+  bb_mark(a.trace, a.trace_cap, init, 6);
+  if (!ok && threadIdx.x == 0) atomicExch(a.err, 2);
+  return ok;
+}
+
+// Block-band E phase for the block size of this system (CTA 0 only).
+template <typename T, int PB>
+__device__ __forceinline__ void bb_phase(const PcgArgs<T> &a, const T *pcur, double alpha, bool init, double &rr_out,
+                                         double &rz_out, unsigned long long *bars, unsigned &ph) {
+  if (blockIdx.x != 0) return;
+  if (a.bbM == 4) bb_apply<T, PB, 4>(a, pcur, alpha, init, rr_out, rz_out, bars, ph);
+  else if (a.bbM == 8) bb_apply<T, PB, 8>(a, pcur, alpha, init, rr_out, rz_out, bars, ph);
+  else bb_apply<T, PB, 16>(a, pcur, alpha, init, rr_out, rz_out, bars, ph);
+}
+
 template <typename T, int PB>
 __global__ void __launch_bounds__(256, 1) k_pcg_fused(PcgArgs<T> a) {
   const int rl = a.rl, rr = a.rr, Rl = a.Rl, Rr = a.Rr, n = a.n, b = 2 * PB + 1;
@@ -214,9 +559,20 @@ __global__ void __launch_bounds__(256, 1) k_pcg_fused(PcgArgs<T> a) {
 
   int slot = 0;
   trace_mark(a.trace, a.trace_cap, slot);
+  __shared__ __align__(8) unsigned long long bb_bars[2];
+  unsigned bb_ph = 0;
+  if (a.edge && blockIdx.x == 0) {
+    if (threadIdx.x == 0) {
+      mbar_init(&bb_bars[0]);
+      mbar_init(&bb_bars[1]);
+      asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+  }
   // r = b, x = 0, z = P^{-1} r;  <r, r>, <r, z>
   double rr_loc = 0.0, rz_loc = 0.0;
-  band_systems<T, PB>(a, nullptr, 0.0, true, rr_loc, rz_loc);
+  if (a.edge) bb_phase<T, PB>(a, nullptr, 0.0, true, rr_loc, rz_loc, bb_bars, bb_ph);
+  else band_systems<T, PB>(a, nullptr, 0.0, true, rr_loc, rz_loc);
   cta_partial(rr_loc, p_rr);
   cta_partial(rz_loc, p_rz);
   if (!grid_sync(a.bar, G, a.err)) return;
@@ -315,7 +671,8 @@ __global__ void __launch_bounds__(256, 1) k_pcg_fused(PcgArgs<T> a) {
     const double alpha = rz / pq;
     rr_loc = 0.0;
     rz_loc = 0.0;
-    band_systems<T, PB>(a, pcur, alpha, false, rr_loc, rz_loc);
+    if (a.edge) bb_phase<T, PB>(a, pcur, alpha, false, rr_loc, rz_loc, bb_bars, bb_ph);
+    else band_systems<T, PB>(a, pcur, alpha, false, rr_loc, rz_loc);
     cta_partial(rr_loc, p_rr);
     cta_partial(rz_loc, p_rz);
     if (!grid_sync(a.bar, G, a.err)) return;
@@ -327,6 +684,10 @@ __global__ void __launch_bounds__(256, 1) k_pcg_fused(PcgArgs<T> a) {
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     a.out[0] = (double)it;
     a.out[1] = res2;
+    if (a.edge) {
+      mbar_inval(&bb_bars[0]);
+      mbar_inval(&bb_bars[1]);
+    }
   }
 }
 
@@ -358,10 +719,20 @@ template <typename T> int pcg_fused_grid(Ctx *c, PcgArgs<T> &a) {
   // Slabs of S mode rows for the dense phase (at least 256 band-stage outputs
   // each), enough CTAs for the slabs and for the band systems, all co-resident.
   const void *k = pick<T>(a.p);
-  a.slots = band_slots(a);
-  a.smem = (int)((size_t)a.slots * a.n * (a.p + 2) * sizeof(float));
-  TTI_CHECK_ARG((size_t)a.n * (a.p + 2) * sizeof(float) <= kPcgSmemBytes, "pcg: n=%d too large for one band system",
-                a.n);
+  if (a.edge) {
+    // block-band preconditioner: rs, ys [n][16] and two staging buffers of bb_ch block rows
+    const size_t vec = 2 * (size_t)a.n * a.bbM * sizeof(float),
+                 row = (size_t)a.p * a.bbM * bb_stride(a.bbM) * sizeof(float);
+    TTI_CHECK_ARG(vec + 2 * row <= kPcgSmemBytes, "pcg: n=%d too large for the block-band preconditioner", a.n);
+    a.bb_ch = (int)std::min<size_t>(32, (kPcgSmemBytes - vec) / (2 * row));
+    a.slots = 1;
+    a.smem = (int)(vec + 2 * (size_t)a.bb_ch * row);
+  } else {
+    a.slots = band_slots(a);
+    a.smem = (int)((size_t)a.slots * a.n * (a.p + 2) * sizeof(float));
+    TTI_CHECK_ARG((size_t)a.n * (a.p + 2) * sizeof(float) <= kPcgSmemBytes,
+                  "pcg: n=%d too large for one band system", a.n);
+  }
   TTI_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kPcgSmemBytes));
   int per_sm = 0;
   TTI_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, 256, a.smem));
@@ -372,7 +743,7 @@ template <typename T> int pcg_fused_grid(Ctx *c, PcgArgs<T> &a) {
   S = std::max<long long>(1, std::min<long long>(S, a.n));
   a.slab = (int)S;
   const long long nslab = (a.n + S - 1) / S;
-  const long long npair = (long long)a.rl * a.rr;
+  const long long npair = a.edge ? 1 : (long long)a.rl * a.rr;
   long long g = std::max(nslab, (npair + a.slots - 1) / a.slots);
   g = std::max<long long>(1, std::min(g, cap));
   a.t1_stride = (long long)a.rl * (S + 2 * a.p) * a.rr * a.Rr;
