@@ -316,7 +316,7 @@ struct Amen {
     if (res0 <= tol_abs) return res0;
     const int maxit = o.local_maxit;
     const size_t Lsz = (size_t)n(k) * (S->p + 1) * rl(k) * rr(k);
-    // Small interface blocks (m = rl rr <= 16): exact block-band preconditioner.
+    // Small interface blocks (m = rl rr <= 8): exact block-band preconditioner.
     // Otherwise band block-Jacobi over the interface pairs.
     const bool edge = bb_eligible(rl(k) * rr(k), n(k), S->p);
     BBPrec bb;

@@ -2,8 +2,8 @@
 // assembly of the symmetric block band (FP64 contractions, FP32 result), the
 // sequential right-looking block Cholesky in one CTA, and the parallel
 // post-pass that turns the factor into the blocks the substitutions use.
-// Block size M (4, 8 or 16) is m = rl * rr rounded up; padding rows and
-// columns carry the identity.
+// Block size M (4 or 8) is m = rl * rr rounded up; padding rows and columns
+// carry the identity.
 #include "bbprec.cuh"
 
 namespace ttiga {
@@ -46,127 +46,153 @@ __global__ void k_bb_build(const double *__restrict__ PhiL, int rl, int Rl, cons
   }
 }
 
-// Right-looking block Cholesky of the block band, one CTA of 256 threads.
+// Right-looking block Cholesky of the block band by one warp.
 // The live blocks (i+k, i+l), 0 <= l <= k <= p, sit in a ring of (p+1)^2 block
 // slots indexed by absolute block row and column modulo p+1, so nothing moves
-// between steps.  Step i: (a) warp 0 factors the diagonal block in registers
-// (lane r owns row r; column j broadcast by shuffles); (b) the panel
-// X_k = W(i+k, i) L_ii^{-T} by row-wise forward substitution; (c) the trailing
-// update W(i+k, i+l) -= X_k X_l^T in 4 x 4 register tiles, and block row
-// i+1+p (prefetched into registers at the start of the step) enters the slots
-// of row i.  FP32 throughout: each step is a chain of dependent operations,
-// and this is a preconditioner.  A pivot that cancellation drives below 1e-6 of
-// the diagonal entry is replaced by that entry (the factor stays SPD; PCG
-// checks convergence).  Outputs: Ld[i] = L_ii (zero above), Lx[i][k-1] = L(i+k, i).
+// between steps.  Step i: (a) every lane factors the M x M diagonal block
+// redundantly in its own registers (no shuffles on the dependent path; the
+// reciprocal pivots are the rsqrt results); (b) the panel X_k = W(i+k, i)
+// L_ii^{-T} by row-wise forward substitution against the register copy of
+// L_ii; (c) the trailing update W(i+k, i+l) -= X_k X_l^T in 4 x 4 register
+// tiles, and block row i+1+p (loaded into registers at the start of the step)
+// enters the slots of row i.  FP32 throughout: each step is a chain of
+// dependent operations, and this is a preconditioner.  A pivot that
+// cancellation drives below 1e-6 of the diagonal entry is replaced by that
+// entry (the factor stays SPD; PCG checks convergence).
+// Outputs: Ld[i] = L_ii (zero above), Lx[i][k-1] = L(i+k, i).
 template <int M>
-__global__ void __launch_bounds__(256) k_bb_factor(const float *__restrict__ Blow, int n, int p, int m,
-                                                    float *__restrict__ Ld, float *__restrict__ Lx,
-                                                    unsigned long long *phase_clk) {
-  // phase_clk (optional): SM clock cycles thread 0 spends in each phase of all steps
-  unsigned long long ck[4] = {0, 0, 0, 0}, t0 = 0;
+__global__ void __launch_bounds__(32) k_bb_factor(const float *__restrict__ Blow, int n, int p, int m,
+                                                   float *__restrict__ Ld, float *__restrict__ Lx,
+                                                   unsigned long long *phase_clk) {
+  constexpr int BS = M * M, T4 = M / 4, TB = T4 * T4, PE = (BS + 31) / 32;
+  // phase_clk (optional): SM clock cycles lane 0 spends in each phase of all steps
+  unsigned long long ck0 = 0, ck1 = 0, ck2 = 0, t0 = 0;
   const bool prof = phase_clk != nullptr && threadIdx.x == 0;
-  auto tick = [&](int ph) {
+  auto stamp = [&](unsigned long long &acc) {
     if (prof) {
       const unsigned long long t1 = clock64();
-      if (ph >= 0) ck[ph] += t1 - t0;
+      acc += t1 - t0;
       t0 = t1;
     }
   };
   extern __shared__ float4 fsm4[];
   float *fsm = reinterpret_cast<float *>(fsm4);
-  constexpr int BS = M * M;
-  const int nb = p + 1, P = p * M;
-  float *Wr = fsm;               // nb x nb ring of M x M blocks
-  float *Ls = Wr + nb * nb * BS;  // L_ii [M][M]
-  float *invd = Ls + BS;          // 1 / L_ii(r, r), [16]
-  float *Xs = invd + 16;          // panel [p M][M]
-  const int tid = threadIdx.x;
-  auto blk = [&](int ra, int ca) { return Wr + ((ra % nb) * nb + (ca % nb)) * BS; };
+  const int nb = p + 1, P = p * M, npairs = p * (p + 1) / 2;
+  float *Wr = fsm;                // nb x nb ring of M x M blocks
+  float *Xs = Wr + nb * nb * BS;  // panel [p M][M]
+  int *pairs = reinterpret_cast<int *>(Xs + P * M);  // (kb, lb) of pair index, [28][2]
+  const int lane = threadIdx.x;
+  auto wrap = [nb](int v) { return v >= nb ? v - nb : v; };  // v < 2 nb
+  auto slot = [&](int sr, int sc) { return Wr + (sr * nb + sc) * BS; };
   auto ident = [](int e) { return (e / M == e % M) ? 1.f : 0.f; };
+  if (lane == 0)
+    for (int kb = 1, q = 0; kb <= p; ++kb)
+      for (int lb = 1; lb <= kb; ++lb, ++q) {
+        pairs[2 * q] = kb;
+        pairs[2 * q + 1] = lb;
+      }
   for (int k = 0; k < nb; ++k)
     for (int l = 0; l <= k; ++l) {
-      float *dst = blk(k, l);
-      for (int e = tid; e < BS; e += blockDim.x)
+      float *dst = slot(k, l);
+      for (int e = lane; e < BS; e += 32)
         dst[e] = (k < n) ? Blow[((long long)k * nb + (p - k + l)) * BS + e] : (l == k ? ident(e) : 0.f);
     }
-  __syncthreads();
-  for (int i = 0; i < n; ++i) {
-    tick(-1);
+  __syncwarp();
+  int s0 = 0;  // slot of block row / column i
+  for (int i = 0; i < n; ++i, s0 = wrap(s0 + 1)) {
+    if (prof) t0 = clock64();
     const int inew = i + 1 + p;
-    float pre[8];
+    float pre[8][PE];
 #pragma unroll
-    for (int l = 0; l < 8; ++l) {
-      pre[l] = 0.f;
-      if (l < nb && tid < BS)
-        pre[l] = (inew < n) ? Blow[((long long)inew * nb + l) * BS + tid] : (l == p ? ident(tid) : 0.f);
-    }
-    // (a) diagonal block
-    if (tid < 32) {
-      const int r = tid % M;
-      const float *D = blk(i, i);
-      float row[M];
+    for (int l = 0; l < 8; ++l)
 #pragma unroll
-      for (int s = 0; s < M; ++s) row[s] = D[r * M + s];
+      for (int u = 0; u < PE; ++u) {
+        const int e = lane + u * 32;
+        pre[l][u] = 0.f;
+        if (l < nb && e < BS)
+          pre[l][u] = (inew < n) ? Blow[((long long)inew * nb + l) * BS + e] : (l == p ? ident(e) : 0.f);
+      }
+    // (a) diagonal block, factored by every lane
+    float Lr[M][M], ir[M];
+    {
+      const float4 *D4 = reinterpret_cast<const float4 *>(slot(s0, s0));
+#pragma unroll
+      for (int r = 0; r < M; ++r)
+#pragma unroll
+        for (int c4 = 0; c4 < T4; ++c4) {
+          const float4 v = D4[r * T4 + c4];
+          Lr[r][4 * c4 + 0] = v.x;
+          Lr[r][4 * c4 + 1] = v.y;
+          Lr[r][4 * c4 + 2] = v.z;
+          Lr[r][4 * c4 + 3] = v.w;
+        }
 #pragma unroll
       for (int j = 0; j < M; ++j) {
+        ir[j] = 1.f;
         if (j < m) {
-          float piv = __shfl_sync(0xffffffffu, row[j], j);
-          const float d0 = D[j * (M + 1)];
+          float piv = Lr[j][j];
+          const float d0 = slot(s0, s0)[j * (M + 1)];
           if (!(piv > 1e-6f * d0)) piv = (d0 > 0.f) ? d0 : 1.f;
           const float inv = rsqrtf(piv);
-          const float lrj = (r == j) ? piv * inv : ((r > j) ? row[j] * inv : 0.f);
-          row[j] = lrj;
+          ir[j] = inv;
+          Lr[j][j] = piv * inv;
 #pragma unroll
-          for (int s = j + 1; s < M; ++s) {
-            const float ls = __shfl_sync(0xffffffffu, lrj, s);
-            if (r >= s) row[s] -= lrj * ls;
-          }
+          for (int r = j + 1; r < M; ++r) Lr[r][j] *= inv;
+#pragma unroll
+          for (int r = j + 1; r < M; ++r)
+#pragma unroll
+            for (int c = j + 1; c <= r; ++c) Lr[r][c] -= Lr[r][j] * Lr[c][j];
         }
       }
-      if (tid < M) {
+      if (lane == 0) {
+        float4 *dst = reinterpret_cast<float4 *>(Ld + (long long)i * BS);
 #pragma unroll
-        for (int s = 0; s < M; ++s) {
-          const float v = (s <= r) ? row[s] : 0.f;
-          Ls[r * M + s] = v;
-          Ld[(long long)i * BS + r * M + s] = v;
-        }
-        invd[r] = 1.f / row[r];
+        for (int r = 0; r < M; ++r)
+#pragma unroll
+          for (int c4 = 0; c4 < T4; ++c4)
+            dst[r * T4 + c4] = make_float4(4 * c4 + 0 <= r ? Lr[r][4 * c4 + 0] : 0.f,
+                                           4 * c4 + 1 <= r ? Lr[r][4 * c4 + 1] : 0.f,
+                                           4 * c4 + 2 <= r ? Lr[r][4 * c4 + 2] : 0.f,
+                                           4 * c4 + 3 <= r ? Lr[r][4 * c4 + 3] : 0.f);
       }
     }
-    __syncthreads();
-    tick(0);
+    stamp(ck0);
     // (b) panel rows: x (row e of X_k) solves L_ii x = w
-    if (tid < P) {
-      const int k = 1 + tid / M, e = tid % M;
-      const float *w = blk(i + k, i) + e * M;
+    for (int t = lane; t < P; t += 32) {
+      const int k = 1 + t / M, e = t % M;
+      const float4 *w4 = reinterpret_cast<const float4 *>(slot(wrap(s0 + k), s0) + e * M);
       float x[M];
 #pragma unroll
-      for (int f = 0; f < M; ++f) x[f] = w[f];
+      for (int c4 = 0; c4 < T4; ++c4) {
+        const float4 v = w4[c4];
+        x[4 * c4 + 0] = v.x;
+        x[4 * c4 + 1] = v.y;
+        x[4 * c4 + 2] = v.z;
+        x[4 * c4 + 3] = v.w;
+      }
 #pragma unroll
       for (int cc = 0; cc < M; ++cc) {
-        x[cc] *= invd[cc];
+        x[cc] *= ir[cc];
 #pragma unroll
-        for (int s = cc + 1; s < M; ++s) x[s] -= Ls[s * M + cc] * x[cc];
+        for (int c = cc + 1; c < M; ++c) x[c] -= Lr[c][cc] * x[cc];
       }
-      float *xg = Lx + (((long long)i * p + (k - 1)) * M + e) * M;
+      float4 *xs = reinterpret_cast<float4 *>(Xs + t * M);
+      float4 *xg = reinterpret_cast<float4 *>(Lx + (((long long)i * p + (k - 1)) * M + e) * M);
 #pragma unroll
-      for (int f = 0; f < M; ++f) {
-        Xs[tid * M + f] = x[f];
-        xg[f] = x[f];
+      for (int c4 = 0; c4 < T4; ++c4) {
+        const float4 v = make_float4(x[4 * c4], x[4 * c4 + 1], x[4 * c4 + 2], x[4 * c4 + 3]);
+        xs[c4] = v;
+        xg[c4] = v;
       }
     }
-    __syncthreads();
-    tick(1);
+    __syncwarp();
+    stamp(ck1);
     // (c) trailing update in 4 x 4 tiles over block pairs (kb, lb), 1 <= lb <= kb <= p
-    constexpr int T4 = M / 4, TB = T4 * T4;
-    const int npairs = p * (p + 1) / 2;
-    for (int t = tid; t < npairs * TB; t += blockDim.x) {
+    for (int t = lane; t < npairs * TB; t += 32) {
       const int pr = t / TB, tt = t % TB;
-      int kb = 1;
-      while ((kb + 1) * kb / 2 <= pr) ++kb;
-      const int lb = pr - kb * (kb - 1) / 2 + 1;
+      const int kb = pairs[2 * pr], lb = pairs[2 * pr + 1];
       const int tr = tt / T4, tc = tt % T4;
-      float *dst = blk(i + kb, i + lb) + (4 * tr) * M + 4 * tc;
+      float *dst = slot(wrap(s0 + kb), wrap(s0 + lb)) + (4 * tr) * M + 4 * tc;
       const float *xa = Xs + ((kb - 1) * M + 4 * tr) * M;
       const float *xb = Xs + ((lb - 1) * M + 4 * tc) * M;
       float acc[4][4];
@@ -196,16 +222,25 @@ __global__ void __launch_bounds__(256) k_bb_factor(const float *__restrict__ Blo
       for (int a = 0; a < 4; ++a)
         *reinterpret_cast<float4 *>(dst + a * M) = make_float4(acc[a][0], acc[a][1], acc[a][2], acc[a][3]);
     }
-    if (tid < BS) {
+    // block row i+1+p takes the slots of row i: slot row s0, slot columns s0+1+l
 #pragma unroll
-      for (int l = 0; l < 8; ++l)
-        if (l < nb) blk(inew, i + 1 + l)[tid] = pre[l];
-    }
-    __syncthreads();
-    tick(2);
+    for (int l = 0; l < 8; ++l)
+      if (l < nb) {
+        float *dst = slot(s0, wrap(s0 + 1 + l));
+#pragma unroll
+        for (int u = 0; u < PE; ++u) {
+          const int e = lane + u * 32;
+          if (e < BS) dst[e] = pre[l][u];
+        }
+      }
+    __syncwarp();
+    stamp(ck2);
   }
-  if (prof)
-    for (int k = 0; k < 3; ++k) phase_clk[k] = ck[k];
+  if (prof) {
+    phase_clk[0] = ck0;
+    phase_clk[1] = ck1;
+    phase_clk[2] = ck2;
+  }
 }
 
 // Per block row: Linv = L_ii^{-1}, G_k = L_ii^{-1} L(i, i-k), H_k = L_ii^{-T} L(i+k, i)^T
@@ -267,7 +302,7 @@ constexpr size_t kFactorSmemMax = 200 * 1024;
 
 size_t factor_smem(int M, int p) {
   const size_t nb = (size_t)p + 1, BS = (size_t)M * M;
-  return (nb * nb * BS + BS + 16 + (size_t)p * M * M) * sizeof(float);
+  return (nb * nb * BS + (size_t)p * M * M) * sizeof(float) + 2 * 28 * sizeof(int);
 }
 
 template <int M>
@@ -287,8 +322,7 @@ void build_m(Ctx *c, const double *PhiL, int rl, const BandCore &A, const double
     const size_t smem = factor_smem(M, p);
     TTI_CUDA(cudaFuncSetAttribute(k_bb_factor<M>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFactorSmemMax));
     ProfScope ps(c, PROF_PRECOND, 0.0);
-    k_bb_factor<M><<<1, 256, smem, c->stream>>>(Blow.as<float>(), n, p, m, Ld.as<float>(), Lx.as<float>(),
-                                               phase_clk);
+    k_bb_factor<M><<<1, 32, smem, c->stream>>>(Blow.as<float>(), n, p, m, Ld.as<float>(), Lx.as<float>(), phase_clk);
     TTI_LAUNCH();
   }
   P.Linv = DBuf(c, (size_t)n * BS * sizeof(float));
@@ -302,7 +336,7 @@ void build_m(Ctx *c, const double *PhiL, int rl, const BandCore &A, const double
 }  // namespace
 
 bool bb_eligible(int m, int n, int p) {
-  return m >= 1 && m <= 16 && n >= 1 && n <= 1024 && p >= 1 && p <= 7 &&
+  return m >= 1 && m <= kBBMaxM && n >= 1 && n <= 1024 && p >= 1 && p <= 7 &&
          factor_smem(bb_pad(m), p) <= kFactorSmemMax;
 }
 
@@ -314,11 +348,8 @@ void bb_prec_build(Ctx *c, const double *PhiL, int rl, const BandCore &A, const 
   P.p = A.p;
   P.m = m;
   P.M = bb_pad(m);
-  switch (P.M) {
-    case 4: build_m<4>(c, PhiL, rl, A, PhiR, rr, P, phase_clk); break;
-    case 8: build_m<8>(c, PhiL, rl, A, PhiR, rr, P, phase_clk); break;
-    default: build_m<16>(c, PhiL, rl, A, PhiR, rr, P, phase_clk); break;
-  }
+  if (P.M == 4) build_m<4>(c, PhiL, rl, A, PhiR, rr, P, phase_clk);
+  else build_m<8>(c, PhiL, rl, A, PhiR, rr, P, phase_clk);
 }
 
 }  // namespace ttiga

@@ -3,7 +3,7 @@
 //
 // With the unknowns of a local system x[a][i][c] taken mode-index-major, the
 // local matrix B = sum_{g,d} PhiL_g (x) A_k[g, d] (x) PhiR_d is block banded:
-// n block rows of m unknowns (padded to M = 4, 8 or 16), half-bandwidth p
+// n block rows of m unknowns (padded to M = 4 or 8), half-bandwidth p
 // blocks, because the operator core A_k is banded in the mode index.  Its block
 // Cholesky factor B ~ L L^T (FP32) is an exact preconditioner up to FP32
 // rounding, so PCG on these systems converges in a few iterations whatever the
@@ -21,8 +21,11 @@
 
 namespace ttiga {
 
-__host__ __device__ constexpr int bb_stride(int M) { return M == 16 ? 20 : (M == 8 ? 12 : 8); }
-__host__ __device__ constexpr int bb_pad(int m) { return m <= 4 ? 4 : (m <= 8 ? 8 : 16); }
+// Largest interface block handled: past m = 8 the sequential factorisation costs
+// more than the band block-Jacobi iterations it saves.
+constexpr int kBBMaxM = 8;
+__host__ __device__ constexpr int bb_stride(int M) { return M == 8 ? 12 : 8; }
+__host__ __device__ constexpr int bb_pad(int m) { return m <= 4 ? 4 : 8; }
 
 struct BBPrec {
   DBuf Linv, G, H;

@@ -547,8 +547,7 @@ __device__ __forceinline__ void bb_phase(const PcgArgs<T> &a, const T *pcur, dou
                                          double &rz_out, unsigned long long *bars, unsigned &ph) {
   if (blockIdx.x != 0) return;
   if (a.bbM == 4) bb_apply<T, PB, 4>(a, pcur, alpha, init, rr_out, rz_out, bars, ph);
-  else if (a.bbM == 8) bb_apply<T, PB, 8>(a, pcur, alpha, init, rr_out, rz_out, bars, ph);
-  else bb_apply<T, PB, 16>(a, pcur, alpha, init, rr_out, rz_out, bars, ph);
+  else bb_apply<T, PB, 8>(a, pcur, alpha, init, rr_out, rz_out, bars, ph);
 }
 
 template <typename T, int PB>
