@@ -35,6 +35,23 @@ WORKLOAD = "quarter_cylinder_p3_n128"
 METRIC = "DOFs solved/s at 1e-8 rel. residual, mixed vs FP64; serving p50/p99 latency"
 TOL = 1e-8
 FP64_ALU_PEAK_TFLOPS = 1.258  # 152 SMs x 2 FP64 FMA/clk x 2 FLOP x 2.07 GHz (nominal 1.25 TFLOP/s)
+
+# DRAM bytes (read + write) per launch of the timed kernel, mean over the six launches of
+# one step of this workload, from one ncu capture whose summary is committed with the
+# profiles.  Valid only for the sources it was taken from: reported as null once they change.
+PCG_TRAFFIC_BYTES = 378709
+PCG_TRAFFIC_SOURCES = ("pcg_fused.cu", "pcg_fused.cuh", "bbprec.cu", "bbprec.cuh", "amen.cu")
+PCG_TRAFFIC_SHA256 = "c78fc9a04790b429a8b1c4fa64551194907a6ba14fd24fef77dda103f91c1d9d"
+
+
+def pcg_traffic():
+    import hashlib
+    h = hashlib.sha256()
+    csrc = os.path.join(os.path.dirname(os.path.abspath(__file__)), "paper_2509_13224_gb300", "csrc")
+    for f in PCG_TRAFFIC_SOURCES:
+        with open(os.path.join(csrc, f), "rb") as fh:
+            h.update(fh.read())
+    return PCG_TRAFFIC_BYTES if h.hexdigest() == PCG_TRAFFIC_SHA256 else None
 REFERENCE_SAMPLE_N = 16
 
 
@@ -361,7 +378,8 @@ def run_ours(args, rank, world):
         ms_k, n_k, flops_k = prof
         achieved = flops_k / n_k / (ms_k / n_k / 1e3) / 1e12
         roof = {"bound": "alu", "achieved": achieved, "peak": FP64_ALU_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": achieved / FP64_ALU_PEAK_TFLOPS, "traffic": None,
+                "frac": achieved / FP64_ALU_PEAK_TFLOPS,
+                "traffic": pcg_traffic() if args.profile_family == 6 else None,
                 "kernel": {1: "k_band_right (local matvec band stage, FP64)", 2: "k_gemm<double>",
                            3: "k_qr_panel", 6: "k_pcg_fused<double> (AMEn local PCG, one launch per solve)"}.get(
                                args.profile_family, str(args.profile_family)),
