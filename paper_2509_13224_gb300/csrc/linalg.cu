@@ -155,12 +155,20 @@ void gemm(Ctx *c, bool ta, bool tb, int m, int n, int k, T alpha, const T *A, lo
     }
     return;
   }
-  // tile shape: narrow outputs get narrow tiles (no FMAs spent on padding)
-  int shape = 0;  // 0: 64x64, 1: 128x16, 2: 16x128, 3: 32x32
-  if (n <= 16 && m > 16) shape = 1;
-  else if (m <= 16 && n > 16) shape = 2;
-  else if (m <= 32 && n <= 32) shape = 3;
-  const int BMs[4] = {64, 128, 16, 32}, BNs[4] = {64, 16, 128, 32};
+  // Tile shape by CTA count.  GB300 executes about 2 FP64 FMAs per clock per SM,
+  // so a GEMM of this path is as fast as the number of SMs its FMAs are spread
+  // over: the largest tile that still gives every SM about two CTAs, down to
+  // 16 x 16 (one output per thread).  FP32 (mixed precision) uses the same rule.
+  const long long batch_tiles = batch;
+  auto ntiles = [&](int bm, int bn) { return (long long)cdiv(n, bn) * cdiv(m, bm) * batch_tiles; };
+  const long long want = 2LL * c->num_sms;
+  int shape;  // 0: 64x64, 1: 128x16, 2: 16x128, 3: 32x32, 4: 16x16
+  if (ntiles(64, 64) >= want && m > 32 && n > 32) shape = 0;
+  else if (ntiles(32, 32) >= want && m > 16 && n > 16) shape = 3;
+  else if (n <= 16 && ntiles(128, 16) >= want) shape = 1;
+  else if (m <= 16 && ntiles(16, 128) >= want) shape = 2;
+  else shape = 4;
+  const int BMs[5] = {64, 128, 16, 32, 16}, BNs[5] = {64, 16, 128, 32, 16};
   const int BM = BMs[shape], BN = BNs[shape];
   auto launch = [&](dim3 grid, const T *A_, const T *B_, T beta_, T *C_, long long ldc_, long long sA_, long long sB_,
                     long long sC_, int ksplit, int kchunk) {
@@ -177,17 +185,21 @@ void gemm(Ctx *c, bool ta, bool tb, int m, int n, int k, T alpha, const T *A, lo
         k_gemm<T, 16, 128><<<grid, 256, 0, c->stream>>>(ta, tb, m, n, k, alpha, A_, lda, sA_, B_, ldb, sB_, beta_, C_,
                                                          ldc_, sC_, ksplit, kchunk);
         break;
-      default:
+      case 3:
         k_gemm<T, 32, 32><<<grid, 256, 0, c->stream>>>(ta, tb, m, n, k, alpha, A_, lda, sA_, B_, ldb, sB_, beta_, C_,
+                                                        ldc_, sC_, ksplit, kchunk);
+        break;
+      default:
+        k_gemm<T, 16, 16><<<grid, 256, 0, c->stream>>>(ta, tb, m, n, k, alpha, A_, lda, sA_, B_, ldb, sB_, beta_, C_,
                                                         ldc_, sC_, ksplit, kchunk);
         break;
     }
     TTI_LAUNCH();
   };
   const long long tiles = (long long)cdiv(n, BN) * cdiv(m, BM);
-  if (batch == 1 && tiles * 2 < c->num_sms && k >= 128) {
-    // few output tiles but a long K: split K over CTAs, then reduce the partials
-    int ksplit = (int)std::min<long long>(std::max<long long>(1, (2LL * c->num_sms) / tiles), (k + 63) / 64);
+  if (batch == 1 && tiles * 2 < c->num_sms && k >= 64) {
+    // few output tiles but a long K: split K over CTAs (chunks of at least 32), then reduce the partials
+    int ksplit = (int)std::min<long long>(std::max<long long>(1, want / tiles), (k + 31) / 32);
     ksplit = std::max(2, std::min(ksplit, 256));
     const int kchunk = ((k + ksplit - 1) / ksplit + 15) / 16 * 16;
     ksplit = (k + kchunk - 1) / kchunk;
