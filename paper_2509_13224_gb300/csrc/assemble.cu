@@ -126,6 +126,8 @@ static void restrict_tt(Ctx *c, TT3 &x, const int n[3], int p, bool band) {
   }
 }
 
+// The operator (sum of the K_ab terms, rounded after every addition) and each
+// load vector are independent and are built concurrently on helper contexts.
 void assemble_system(Ctx *c, const tt_iga_geom *g, const tt_iga_rhs_desc *rhs, int n_rhs, double round_tol,
                      tt_iga_system *out) {
   const int p = g->desc.p;
@@ -133,36 +135,70 @@ void assemble_system(Ctx *c, const tt_iga_geom *g, const tt_iga_rhs_desc *rhs, i
   int n[3];
   for (int d = 0; d < 3; ++d) n[d] = g->s[d].n;
   TT3 K;
-  bool have = false;
-  static const int pairs[6][2] = {{0, 0}, {1, 1}, {2, 2}, {0, 1}, {0, 2}, {1, 2}};
-  for (auto &pr : pairs) {
-    const int i = pr[0], j = pr[1];
-    const CrossResult &R = g->R[field_of(i, j)];
-    if (R.zero) continue;
-    const int nterms = (i == j) ? 1 : 2;
-    for (int t = 0; t < nterms; ++t) {
-      const int a = t == 0 ? i : j, bb = t == 0 ? j : i;  // K_ab: derivative on test index in direction a
-      TT3 T;
-      for (int d = 0; d < 3; ++d) T.m[d] = n[d] * b;
-      for (int k = 0; k < 4; ++k) T.r[k] = R.tt.r[k];
-      T.alloc(c);
-      for (int d = 0; d < 3; ++d)
-        stiffness_core(c, n[d], p, g->s[d].nq, g->s[d].wts.d(), g->s[d].N.d(), g->s[d].dN.d(), R.tt.core[d].d(),
-                       R.tt.r[d], R.tt.r[d + 1], d == a, d == bb, T.core[d].d());
-      if (!have) {
-        K = std::move(T);
-        have = true;
-      } else {
-        TT3 S;
-        tt_sum(c, K, 1.0, T, 1.0, S);
-        tt_round(c, S, round_tol, 0);
-        K = std::move(S);
+  std::vector<TT3> F(n_rhs);
+  std::vector<double> F_norm(n_rhs, 0.0);
+
+  auto build_operator = [&](Ctx *h) {
+    bool have = false;
+    static const int pairs[6][2] = {{0, 0}, {1, 1}, {2, 2}, {0, 1}, {0, 2}, {1, 2}};
+    for (auto &pr : pairs) {
+      const int i = pr[0], j = pr[1];
+      const CrossResult &R = g->R[field_of(i, j)];
+      if (R.zero) continue;
+      const int nterms = (i == j) ? 1 : 2;
+      for (int t = 0; t < nterms; ++t) {
+        const int a = t == 0 ? i : j, bb = t == 0 ? j : i;  // K_ab: derivative on test index in direction a
+        TT3 T;
+        for (int d = 0; d < 3; ++d) T.m[d] = n[d] * b;
+        for (int k = 0; k < 4; ++k) T.r[k] = R.tt.r[k];
+        T.alloc(h);
+        for (int d = 0; d < 3; ++d)
+          stiffness_core(h, n[d], p, g->s[d].nq, g->s[d].wts.d(), g->s[d].N.d(), g->s[d].dN.d(), R.tt.core[d].d(),
+                         R.tt.r[d], R.tt.r[d + 1], d == a, d == bb, T.core[d].d());
+        if (!have) {
+          K = std::move(T);
+          have = true;
+        } else {
+          TT3 S;
+          tt_sum(h, K, 1.0, T, 1.0, S);
+          tt_round(h, S, round_tol, 0);
+          K = std::move(S);
+        }
       }
     }
-  }
-  TTI_CHECK_ARG(have, "assemble: every coefficient field vanished");
-  restrict_tt(c, K, n, p, true);
-  tt_round(c, K, round_tol, 0);
+    TTI_CHECK_ARG(have, "assemble: every coefficient field vanished");
+    restrict_tt(h, K, n, p, true);
+    tt_round(h, K, round_tol, 0);
+    for (int d = 0; d < 3; ++d) K.core[d].rehome(c);
+  };
+
+  auto build_load = [&](int k, Ctx *h) {
+    RhsParams rp = rhs_params(&rhs[k]);
+    CrossResult fj;
+    cross3(h, g->s, g->gp, rp, 7, g->desc.cross_tol, g->desc.max_rank, g->desc.seed + 7919ULL * (k + 1), 0.0, fj);
+    TT3 &Fk = F[k];
+    for (int d = 0; d < 3; ++d) Fk.m[d] = n[d];
+    if (fj.zero) {
+      Fk.r[1] = Fk.r[2] = 1;
+      Fk.alloc(h);
+      for (int d = 0; d < 3; ++d) h->zero(Fk.core[d].get(), Fk.core_elems(d) * sizeof(double));
+    } else {
+      for (int q = 0; q < 4; ++q) Fk.r[q] = fj.tt.r[q];
+      Fk.alloc(h);
+      for (int d = 0; d < 3; ++d)
+        load_core(h, n[d], p, g->s[d].nq, g->s[d].wts.d(), g->s[d].N.d(), fj.tt.core[d].d(), fj.tt.r[d],
+                  fj.tt.r[d + 1], Fk.core[d].d());
+    }
+    restrict_tt(h, Fk, n, p, false);
+    F_norm[k] = tt_round(h, Fk, round_tol, 0);
+    for (int d = 0; d < 3; ++d) Fk.core[d].rehome(c);
+  };
+
+  run_concurrent(c, 1 + n_rhs, [&](int task, Ctx *h) {
+    if (task == 0) build_operator(h);
+    else build_load(task - 1, h);
+  });
+
   out->ctx = c;
   out->p = p;
   out->b = b;
@@ -171,26 +207,8 @@ void assemble_system(Ctx *c, const tt_iga_geom *g, const tt_iga_rhs_desc *rhs, i
   out->F.clear();
   out->F_norm.clear();
   for (int k = 0; k < n_rhs; ++k) {
-    RhsParams rp = rhs_params(&rhs[k]);
-    CrossResult fj;
-    cross3(c, g->s, g->gp, rp, 7, g->desc.cross_tol, g->desc.max_rank, g->desc.seed + 7919ULL * (k + 1), 0.0, fj);
-    TT3 F;
-    for (int d = 0; d < 3; ++d) F.m[d] = n[d];
-    if (fj.zero) {
-      F.r[1] = F.r[2] = 1;
-      F.alloc(c);
-      for (int d = 0; d < 3; ++d) c->zero(F.core[d].get(), F.core_elems(d) * sizeof(double));
-    } else {
-      for (int q = 0; q < 4; ++q) F.r[q] = fj.tt.r[q];
-      F.alloc(c);
-      for (int d = 0; d < 3; ++d)
-        load_core(c, n[d], p, g->s[d].nq, g->s[d].wts.d(), g->s[d].N.d(), fj.tt.core[d].d(), fj.tt.r[d],
-                  fj.tt.r[d + 1], F.core[d].d());
-    }
-    restrict_tt(c, F, n, p, false);
-    double nrm = tt_round(c, F, round_tol, 0);
-    out->F.push_back(std::move(F));
-    out->F_norm.push_back(nrm);
+    out->F.push_back(std::move(F[k]));
+    out->F_norm.push_back(F_norm[k]);
   }
 }
 

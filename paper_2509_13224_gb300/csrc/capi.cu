@@ -105,6 +105,7 @@ int tt_iga_ctx_create(tt_iga_ctx **out, const tt_iga_ctx_opts *o) {
 void tt_iga_ctx_destroy(tt_iga_ctx *c) {
   if (!c) return;
   cudaStreamSynchronize(c->stream);
+  c->release_subs();
   if (c->dstatus) cudaFree(c->dstatus);
   if (c->dscratch) cudaFree(c->dscratch);
   if (c->pinned) cudaFreeHost(c->pinned);
@@ -184,18 +185,24 @@ int tt_iga_geometry(tt_iga_ctx *c, const tt_iga_geom_desc *g, tt_iga_geom **out)
   for (int d = 0; d < 3; ++d) build_space(c, G->s[d], g->n[d], g->p, nq);
   RhsParams none = rhs_params(nullptr);
   const int diag[3] = {0, 3, 5}, off[3] = {1, 2, 4};
+  // The three diagonal fields are independent of each other and run concurrently;
+  // the off-diagonal ones then use the largest diagonal magnitude as their zero
+  // reference.  Every field has its own seed, so the result does not depend on
+  // the order in which the fields finish.
+  auto cross_field = [&](int f, double zero_scale, Ctx *h) {
+    cross3(h, G->s, G->gp, none, f, G->desc.cross_tol, G->desc.max_rank, G->desc.seed + 101ULL * (f + 1), zero_scale,
+           G->R[f]);
+    for (int k = 0; k < 3; ++k) G->R[f].tt.core[k].rehome(c);
+  };
+  run_concurrent(c, 3, [&](int i, Ctx *h) { cross_field(diag[i], 0.0, h); });
   double scale = 0.0;
   bool conv = true;
   for (int f : diag) {
-    cross3(c, G->s, G->gp, none, f, G->desc.cross_tol, G->desc.max_rank, G->desc.seed + 101ULL * (f + 1), 0.0, G->R[f]);
     scale = std::max(scale, G->R[f].scale);
     conv = conv && G->R[f].converged;
   }
-  for (int f : off) {
-    cross3(c, G->s, G->gp, none, f, G->desc.cross_tol, G->desc.max_rank, G->desc.seed + 101ULL * (f + 1), scale,
-           G->R[f]);
-    conv = conv && G->R[f].converged;
-  }
+  run_concurrent(c, 3, [&](int i, Ctx *h) { cross_field(off[i], scale, h); });
+  for (int f : off) conv = conv && G->R[f].converged;
   const int st = device_status(c);
   *out = guard.release();
   if (st == TT_IGA_ERR_BAD_GEOMETRY) {

@@ -12,6 +12,7 @@
 #include <memory>
 #include <stdexcept>
 #include <string>
+#include <functional>
 #include <vector>
 
 #include "../../include/tt_iga.h"
@@ -75,6 +76,9 @@ class DBuf {
     return *this;
   }
   void release();
+  // Hand the allocation to another context (same device): it is freed on that
+  // context's stream.  The caller orders that stream after every use so far.
+  void rehome(Ctx *to);
   void *get() const { return p_; }
   size_t bytes() const { return bytes_; }
   template <typename T> T *as() const { return static_cast<T *>(p_); }
@@ -105,6 +109,13 @@ struct Ctx {
   // persistent device scratch for reductions (kScratchDoubles doubles)
   double *dscratch = nullptr;
   static constexpr int kScratchDoubles = 8192;
+
+  // Helper contexts for independent work run concurrently (own stream and
+  // scratch, the parent's status word); created on first use, see concurrent.cu.
+  bool is_sub = false;
+  std::vector<std::unique_ptr<Ctx>> subs;
+  Ctx *sub(int i);
+  void release_subs();
 
   // Live CUDA-event timing of one kernel family (0 = off), for roofline reporting.
   int prof_family = 0;
@@ -158,6 +169,23 @@ struct Ctx {
 };
 
 inline DBuf::DBuf(Ctx *c, size_t bytes) : ctx_(c), p_(c->alloc(bytes)), bytes_(bytes ? bytes : 16) {}
+inline void DBuf::rehome(Ctx *to) {
+  if (!p_ || ctx_ == to) return;
+  ctx_->in_use -= bytes_;
+  to->in_use += bytes_;
+  if (to->in_use > to->peak) to->peak = to->in_use;
+  ctx_ = to;
+}
+
+// Run f(i, ctx_i) for i < n concurrently, each on its own helper context and
+// host thread, ordered after the work already queued on c and before the work
+// queued on c afterwards.  Sequential on c itself when n <= 1 or when c uses a
+// caller-supplied allocator (whose streams the helpers must not touch).  The
+// first exception of any task is rethrown after all have finished.
+void run_concurrent(Ctx *c, int n, const std::function<void(int, Ctx *)> &f);
+
+// cudaFuncSetAttribute(MaxDynamicSharedMemorySize) once per (kernel, device), thread-safe.
+void set_smem_limit_once(const void *kernel, int bytes);
 inline void DBuf::release() {
   if (p_ && ctx_) ctx_->free(p_, bytes_);
   p_ = nullptr;

@@ -475,12 +475,8 @@ constexpr size_t kQrSmemBytes = 160 * 1024;
 
 void qr(Ctx *c, int m, int k, const double *A, long long lda, double *Q, double *R) {
   TTI_CHECK_ARG(m >= 1 && k >= 1 && k <= 256, "qr: bad sizes m=%d k=%d", m, k);
-  static bool attr = false;
-  if (!attr) {
-    TTI_CUDA(cudaFuncSetAttribute(k_qr_panel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kQrSmemBytes));
-    TTI_CUDA(cudaFuncSetAttribute(k_qr_formq, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kQrSmemBytes));
-    attr = true;
-  }
+  set_smem_limit_once((const void *)k_qr_panel, (int)kQrSmemBytes);
+  set_smem_limit_once((const void *)k_qr_formq, (int)kQrSmemBytes);
   struct Level {
     long long rows;
     int mb, nblk;
