@@ -233,9 +233,13 @@ def run_ours(args, rank, world):
     rhs = [tt.rhs_desc(wl["modes"])]
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")  # 256 MB > 129 MB L2
 
-    def step(precision, info=None):
+    def step(precision, info=None, marks=None):
         g = tt.tt_iga_geometry(ctx, gdesc)
+        if marks is not None:
+            marks[0].record(stream)
         s = tt.tt_iga_assemble(ctx, g, rhs, round_tol=wl["round_tol"])
+        if marks is not None:
+            marks[1].record(stream)
         u, st = tt.tt_iga_solve(ctx, s, tt.solve_opts(tol=TOL, precision=precision))
         if info is not None:
             info.update(st)
@@ -258,17 +262,22 @@ def run_ours(args, rank, world):
         if profile:
             tt.tt_iga_profile_enable(ctx, args.profile_family)
         l0 = tt.tt_iga_launch_count()
+        phases = []
         for _ in range(k):
             with torch.cuda.stream(stream):
                 flush.zero_()
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
+            marks = [torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)]
             e0.record(stream)
-            hs = step(precision, info)
+            hs = step(precision, info, marks)
             e1.record(stream)
             e1.synchronize()
             times.append(e0.elapsed_time(e1))
+            phases.append((e0.elapsed_time(marks[0]), marks[0].elapsed_time(marks[1]), marks[1].elapsed_time(e1)))
             release(hs)
+        info["phases_ms"] = {name: statistics.mean(ph[i] for ph in phases)
+                             for i, name in enumerate(("geometry", "assembly", "solve"))}
         launches = tt.tt_iga_launch_count() - l0
         prof = tt.tt_iga_profile_read(ctx) if profile else None
         if profile:
@@ -373,6 +382,13 @@ def run_ours(args, rank, world):
 
     if rank != 0:
         return
+    fp64_meas, fp32_meas = None, None
+    try:
+        pc = tt.tt_iga_ctx_create(stream)
+        fp64_meas, fp32_meas = tt.tt_iga_fma_peaks(pc)
+        tt.tt_iga_ctx_destroy(pc)
+    except tt.TTIgaError:
+        pass
     roof = None
     if prof is not None and prof[1] > 0:
         ms_k, n_k, flops_k = prof
@@ -383,6 +399,8 @@ def run_ours(args, rank, world):
                 "kernel": {1: "k_band_right (local matvec band stage, FP64)", 2: "k_gemm<double>",
                            3: "k_qr_panel", 6: "k_pcg_fused<double> (AMEn local PCG, one launch per solve)"}.get(
                                args.profile_family, str(args.profile_family)),
+                "peak_kind": "derived: 152 SMs x 2 FP64 FMA/clk x 2 FLOP x 2.07 GHz",
+                "peak_measured_fp64": fp64_meas, "peak_measured_fp32": fp32_meas,
                 "launches": n_k, "kernel_ms_per_step": ms_k / args.steps,
                 "share_of_step": ms_k / args.steps / ms64, "flops_per_launch": flops_k / n_k}
     line = {"metric": METRIC, "value": world * dofs / (ms64_max / 1e3), "unit": "DOFs/s", "n_gpus": world,
@@ -395,6 +413,7 @@ def run_ours(args, rank, world):
                     "d2h_bytes_per_step": d2h},
             "gpu_launches": launches, "clocks": clk, "roofline": roof, "cpu_baseline": base, "mixed": mixed,
             "twisted_n512": extra, "batched": batched, "serving": serving,
+            "phases_ms": info64.get("phases_ms"),
             "solve": {"rel_residual": info64.get("rel_residual"), "sweeps": info64.get("sweeps"),
                       "ranks": info64.get("ranks"), "op_ranks": info64.get("op_ranks"),
                       "local_matvecs": info64.get("local_matvecs"), "solve_ms": info64.get("ms_total")}}

@@ -98,6 +98,11 @@ int tt_iga_profile_enable(tt_iga_ctx *ctx, int family);
 /* Synchronise and return the summed event time (ms), the number of timed
  * launches and their summed algorithmic FLOPs. */
 int tt_iga_profile_read(tt_iga_ctx *ctx, double *ms_total, long long *launches, double *flops_total);
+/* Measured FMA throughput of the context's GPU (TFLOP/s, one FMA = 2 FLOP): a
+ * kernel of independent FMA chains over every SM, timed with CUDA events on the
+ * context stream (about 10 ms).  Either output may be NULL.  The denominators
+ * of the ALU-bound rooflines; the library has no counterpart in the paper. */
+int tt_iga_fma_peaks(tt_iga_ctx *ctx, double *fp64_tflops, double *fp32_tflops);
 
 /* --------------------------------------------------------------- geometry */
 

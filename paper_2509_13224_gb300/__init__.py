@@ -138,6 +138,7 @@ _SIGS = {
     "tt_iga_svd_small": (ctypes.c_int, [_vp, ctypes.c_int, _vp, _vp, _vp, _vp]),
     "tt_iga_svd_small_noalloc": (ctypes.c_int, [_vp, ctypes.c_int, _vp, _vp, _vp, _vp]),
     "tt_iga_maxvol": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, _vp, ctypes.c_double, ctypes.c_int, _vp, _vp]),
+    "tt_iga_fma_peaks": (ctypes.c_int, [_vp, _c_double_p, _c_double_p]),
 }
 for _name, (_res, _args) in _SIGS.items():
     _fn = getattr(_lib, _name)
@@ -260,6 +261,13 @@ def tt_iga_profile_read(ctx):
     ms, n, w = ctypes.c_double(), ctypes.c_longlong(), ctypes.c_double()
     _check(ctx, _lib.tt_iga_profile_read(ctx, ctypes.byref(ms), ctypes.byref(n), ctypes.byref(w)))
     return ms.value, n.value, w.value
+
+
+def tt_iga_fma_peaks(ctx):
+    """Measured (FP64, FP32) FMA throughput of the context's GPU in TFLOP/s."""
+    a, b = ctypes.c_double(), ctypes.c_double()
+    _check(ctx, _lib.tt_iga_fma_peaks(ctx, ctypes.byref(a), ctypes.byref(b)))
+    return a.value, b.value
 
 
 def tt_iga_solution_cores(ctx, u, out=None):

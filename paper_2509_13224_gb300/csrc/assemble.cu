@@ -138,8 +138,11 @@ void assemble_system(Ctx *c, const tt_iga_geom *g, const tt_iga_rhs_desc *rhs, i
   std::vector<TT3> F(n_rhs);
   std::vector<double> F_norm(n_rhs, 0.0);
 
+  // K = sum of the K_ab terms, rounded after every addition.  The additions form a
+  // pairwise tree whose levels run concurrently: the same number of roundings
+  // as a left-to-right sum, fewer of them one after another.
   auto build_operator = [&](Ctx *h) {
-    bool have = false;
+    std::vector<TT3> terms;
     static const int pairs[6][2] = {{0, 0}, {1, 1}, {2, 2}, {0, 1}, {0, 2}, {1, 2}};
     for (auto &pr : pairs) {
       const int i = pr[0], j = pr[1];
@@ -155,18 +158,22 @@ void assemble_system(Ctx *c, const tt_iga_geom *g, const tt_iga_rhs_desc *rhs, i
         for (int d = 0; d < 3; ++d)
           stiffness_core(h, n[d], p, g->s[d].nq, g->s[d].wts.d(), g->s[d].N.d(), g->s[d].dN.d(), R.tt.core[d].d(),
                          R.tt.r[d], R.tt.r[d + 1], d == a, d == bb, T.core[d].d());
-        if (!have) {
-          K = std::move(T);
-          have = true;
-        } else {
-          TT3 S;
-          tt_sum(h, K, 1.0, T, 1.0, S);
-          tt_round(h, S, round_tol, 0);
-          K = std::move(S);
-        }
+        terms.push_back(std::move(T));
       }
     }
-    TTI_CHECK_ARG(have, "assemble: every coefficient field vanished");
+    TTI_CHECK_ARG(!terms.empty(), "assemble: every coefficient field vanished");
+    while (terms.size() > 1) {
+      const int np = (int)terms.size() / 2;
+      std::vector<TT3> next(np);
+      run_concurrent(h, np, [&](int q, Ctx *hh) {
+        tt_sum(hh, terms[2 * q], 1.0, terms[2 * q + 1], 1.0, next[q]);
+        tt_round(hh, next[q], round_tol, 0);
+        for (int d = 0; d < 3; ++d) next[q].core[d].rehome(h);
+      });
+      if (terms.size() % 2) next.push_back(std::move(terms.back()));
+      terms = std::move(next);  // the consumed terms are freed on h, after the helpers (ordered by the join)
+    }
+    K = std::move(terms[0]);
     restrict_tt(h, K, n, p, true);
     tt_round(h, K, round_tol, 0);
     for (int d = 0; d < 3; ++d) K.core[d].rehome(c);

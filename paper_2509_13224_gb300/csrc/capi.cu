@@ -1,5 +1,6 @@
 // extern "C" entry points of the TT-IGA library (include/tt_iga.h).
 #include <algorithm>
+#include <future>
 #include <cmath>
 
 #include "amen.cuh"
@@ -139,6 +140,14 @@ int tt_iga_profile_enable(tt_iga_ctx *c, int family) {
   API_CATCH(c)
 }
 
+int tt_iga_fma_peaks(tt_iga_ctx *c, double *fp64_tflops, double *fp32_tflops) {
+  if (!c) return TT_IGA_ERR_ARG;
+  API_TRY
+  ttiga::fma_peaks(c, fp64_tflops, fp32_tflops);
+  return TT_IGA_OK;
+  API_CATCH(c)
+}
+
 int tt_iga_profile_read(tt_iga_ctx *c, double *ms_total, long long *launches, double *flops_total) {
   if (!c) return TT_IGA_ERR_ARG;
   API_TRY
@@ -185,24 +194,41 @@ int tt_iga_geometry(tt_iga_ctx *c, const tt_iga_geom_desc *g, tt_iga_geom **out)
   for (int d = 0; d < 3; ++d) build_space(c, G->s[d], g->n[d], g->p, nq);
   RhsParams none = rhs_params(nullptr);
   const int diag[3] = {0, 3, 5}, off[3] = {1, 2, 4};
-  // The three diagonal fields are independent of each other and run concurrently;
-  // the off-diagonal ones then use the largest diagonal magnitude as their zero
-  // reference.  Every field has its own seed, so the result does not depend on
-  // the order in which the fields finish.
-  auto cross_field = [&](int f, double zero_scale, Ctx *h) {
-    cross3(h, G->s, G->gp, none, f, G->desc.cross_tol, G->desc.max_rank, G->desc.seed + 101ULL * (f + 1), zero_scale,
-           G->R[f]);
+  // All six fields run concurrently.  An off-diagonal field is rank 0 when its
+  // magnitude is below 1e-13 of the largest diagonal magnitude; the diagonal
+  // fields publish theirs after their first fibre sample and the off-diagonal
+  // ones wait for them there.  Every field has its own seed, so the result
+  // does not depend on the order in which the fields run.
+  std::promise<double> diag_scale[3];
+  std::shared_future<double> diag_ref[3];
+  for (int i = 0; i < 3; ++i) diag_ref[i] = diag_scale[i].get_future().share();
+  run_concurrent(c, 6, [&](int i, Ctx *h) {
+    const int f = i < 3 ? diag[i] : off[i - 3];
+    bool published = false;
+    std::function<double(double)> ref;
+    if (i < 3)
+      ref = [&, i](double own) {
+        diag_scale[i].set_value(own);
+        published = true;
+        return 0.0;
+      };
+    else
+      ref = [&](double) {
+        double m = 0.0;
+        for (auto &r : diag_ref) m = std::max(m, r.get());
+        return m;  // 0 when every diagonal field vanished: the field's own scale decides
+      };
+    try {
+      cross3(h, G->s, G->gp, none, f, G->desc.cross_tol, G->desc.max_rank, G->desc.seed + 101ULL * (f + 1), 0.0,
+             G->R[f], &ref);
+    } catch (...) {
+      if (i < 3 && !published) diag_scale[i].set_exception(std::current_exception());
+      throw;
+    }
     for (int k = 0; k < 3; ++k) G->R[f].tt.core[k].rehome(c);
-  };
-  run_concurrent(c, 3, [&](int i, Ctx *h) { cross_field(diag[i], 0.0, h); });
-  double scale = 0.0;
+  });
   bool conv = true;
-  for (int f : diag) {
-    scale = std::max(scale, G->R[f].scale);
-    conv = conv && G->R[f].converged;
-  }
-  run_concurrent(c, 3, [&](int i, Ctx *h) { cross_field(off[i], scale, h); });
-  for (int f : off) conv = conv && G->R[f].converged;
+  for (int f = 0; f < 6; ++f) conv = conv && G->R[f].converged;
   const int st = device_status(c);
   *out = guard.release();
   if (st == TT_IGA_ERR_BAD_GEOMETRY) {

@@ -30,6 +30,7 @@ Ctx *Ctx::sub(int i) {
 
 void Ctx::release_subs() {
   for (auto &s : subs) {
+    s->release_subs();
     if (s->stream) cudaStreamSynchronize(s->stream);
     if (s->dscratch) cudaFree(s->dscratch);
     if (s->pinned) cudaFreeHost(s->pinned);

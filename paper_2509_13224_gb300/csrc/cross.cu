@@ -171,7 +171,8 @@ int skeleton(Ctx *c, const double *Y, int rows, int k, double rel, DBuf &U) {
 }  // namespace
 
 void cross3(Ctx *c, const Space *s, const GeomParams &g, const RhsParams &f, int comp, double eps, int max_rank,
-            uint64_t seed, double zero_scale, CrossResult &out) {
+            uint64_t seed, double zero_scale, CrossResult &out, const std::function<double(double)> *zero_ref) {
+  bool ref_asked = false;
   const int Q1 = s[0].Q, Q2 = s[1].Q, Q3 = s[2].Q;
   if (max_rank <= 0) max_rank = 64;
   max_rank = std::min(max_rank, 240);
@@ -196,6 +197,10 @@ void cross3(Ctx *c, const Space *s, const GeomParams &g, const RhsParams &f, int
       DBuf Y(c, (size_t)Q1 * k1 * sizeof(double));
       sm.fibers(Q1, k1, 0, {}, {}, ca, cb, Y.d());
       scale = host_maxabs(c, Y.d(), nullptr, (long long)Q1 * k1);
+      if (zero_ref && !ref_asked) {
+        zero_scale = (*zero_ref)(scale);
+        ref_asked = true;
+      }
       const double zs = zero_scale > 0 ? zero_scale : scale;
       if (scale <= 1e-13 * zs || scale == 0.0) {
         out.zero = true;
