@@ -309,10 +309,17 @@ struct Amen {
   Work<float> &work(float *) { return w32; }
 
   // Solve the local system of core k for x (in/out).  Returns the residual before the solve.
-  double local_solve(int k, const double *rhs, double *x, double tol_abs) {
+  // With check_below > 0, a residual at or below it returns at once with *checked = true
+  // and x untouched (the caller then evaluates the exact TT residual).
+  double local_solve(int k, const double *rhs, double *x, double tol_abs, double check_below = -1.0,
+                     bool *checked = nullptr) {
     const long long N = (long long)rl(k) * n(k) * rr(k);
     DBuf rbuf(c, N * sizeof(double));
     const double res0 = residual64(k, rhs, x, rbuf.d());
+    if (checked && res0 <= check_below) {
+      *checked = true;
+      return res0;
+    }
     if (res0 <= tol_abs) return res0;
     const int maxit = o.local_maxit;
     const size_t Lsz = (size_t)n(k) * (S->p + 1) * rl(k) * rr(k);
@@ -496,8 +503,20 @@ struct Amen {
     const double tol_solve = 0.1 * tol_abs / sqrt(3.0);
     const double tol_trunc = 0.3 * tol_abs / sqrt(3.0);
     int status = TT_IGA_ERR_NOT_CONVERGED;
+    // The exact residual of a finished sweep is evaluated lazily.  After the backward
+    // pass the interfaces of core 0 are orthonormal, so the local residual of core 0 in
+    // the next sweep is the norm of a projection of F - K u: when it exceeds tol ||F||
+    // the sweep cannot have converged and the exact residual is skipped; otherwise it
+    // is evaluated on the unchanged u before core 0 is touched.  The last allowed
+    // sweep is always checked at once.
+    bool check_pending = false;
+    double prev_maxloc = 0.0;
+    auto converged = [&](double res, double maxloc) {
+      return (res >= 0.0 && res <= o.tol) || (res < 0.0 && maxloc <= o.tol);
+    };
     for (int sweep = 0; sweep < o.max_sweeps; ++sweep) {
       double maxloc = 0.0;
+      bool stop_now = false;
       // stage timer for verbose >= 2 (synchronises, diagnosis only)
       auto now_ms = [&]() {
         if (o.verbose >= 2) c->sync();
@@ -510,7 +529,30 @@ struct Amen {
         const double t0 = now_ms();
         rhs_local(c, w64, PsiL[k].d(), rl(k), F.core[k].d(), f[k], n(k), f[k + 1], PsiR[k].d(), rr(k), rhs.d());
         TTI_CUDA(cudaMemcpyAsync(x.d(), u.core[k].d(), N * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
-        const double r0 = local_solve(k, rhs.d(), x.d(), tol_solve);
+        double r0;
+        if (k == 0 && check_pending) {
+          check_pending = false;
+          bool checked = false;
+          r0 = local_solve(k, rhs.d(), x.d(), tol_solve, tol_abs, &checked);
+          if (checked) {
+            const double res = exact_residual();
+            st.rel_residual = res;
+            if (o.verbose)
+              fprintf(stderr, "[tt_iga amen] after sweep %d: local %.3e of ||F||, exact residual %.3e\n", sweep,
+                      r0 / Fnorm, res);
+            if (converged(res, prev_maxloc)) {
+              status = TT_IGA_OK;
+              stop_now = true;
+              break;
+            }
+            r0 = local_solve(k, rhs.d(), x.d(), tol_solve);
+          } else if (o.verbose) {
+            fprintf(stderr, "[tt_iga amen] after sweep %d: local %.3e of ||F|| > tol, exact residual skipped\n",
+                    sweep, r0 / Fnorm);
+          }
+        } else {
+          r0 = local_solve(k, rhs.d(), x.d(), tol_solve);
+        }
         maxloc = std::max(maxloc, r0 / Fnorm);
         const double t1 = now_ms();
         t_solve += t1 - t0;
@@ -525,6 +567,7 @@ struct Amen {
           last_core_z(u.core[2].d());
         }
       }
+      if (stop_now) break;
       // backward orthogonalisation of u and z, refresh right interfaces
       const double tb0 = now_ms();
       for (int k = 2; k >= 1; --k) {
@@ -535,19 +578,22 @@ struct Amen {
       const double tb1 = now_ms();
       st.sweeps = sweep + 1;
       last_local = maxloc;
-      const double res = exact_residual();
+      st.local_residual = maxloc;
+      prev_maxloc = maxloc;
+      const bool last = sweep + 1 == o.max_sweeps;
+      const double res = last ? exact_residual() : -2.0;
       if (o.verbose >= 2)
         fprintf(stderr, "[tt_iga amen] sweep %d stages: local solves %.2f ms, truncation+enrichment %.2f ms, "
                         "left interfaces %.2f ms, backward pass %.2f ms, exact residual %.2f ms\n",
                 sweep + 1, t_solve, t_trunc, t_iface, tb1 - tb0, now_ms() - tb1);
-      st.rel_residual = res;
-      st.local_residual = maxloc;
       if (o.verbose)
-        fprintf(stderr, "[tt_iga amen] sweep %d ranks %d %d local %.3e residual %.3e matvecs %lld\n", sweep + 1,
-                u.r[1], u.r[2], maxloc, res, st.local_matvecs);
-      if ((res >= 0.0 && res <= o.tol) || (res < 0.0 && maxloc <= o.tol)) {
-        status = TT_IGA_OK;
-        break;
+        fprintf(stderr, "[tt_iga amen] sweep %d ranks %d %d local %.3e matvecs %lld\n", sweep + 1, u.r[1], u.r[2],
+                maxloc, st.local_matvecs);
+      if (last) {
+        st.rel_residual = res;
+        if (converged(res, maxloc)) status = TT_IGA_OK;
+      } else {
+        check_pending = true;
       }
     }
     st.ranks[0] = u.r[1];
