@@ -136,6 +136,7 @@ struct Amen {
   tt_iga_stats st{};
   double last_local = 0.0;
   bool last_pcg_converged = false;
+  int trunc_hint[2] = {0, 0};  // rank chosen by the last truncation of cores 0 and 1
   // scratch scalars on the device: [0] rz, [1] pq, [2] rz_new, [8..] partials
   DBuf scal;
 
@@ -414,16 +415,43 @@ struct Amen {
       gemm<double>(c, false, false, rows, b, r, 1.0, QU.d(), b, 0, SVt.d(), b, 0, 0.0, xt.d(), b, 0, 1);
       return residual64(k, rhs, xt.d(), rt.d());
     };
+    // smallest rank whose local residual meets the tolerance (binary search, the residual
+    // being non-increasing in the rank); the previous sweep's rank of this core is tried
+    // first, which settles the search in two evaluations when the rank is unchanged
     int lo = 1, hi = rmax;
-    if (res_at(hi) > tol_trunc) {
-      lo = hi;  // cannot meet the tolerance: keep everything
-    } else {
-      while (lo < hi) {
+    const int hint = trunc_hint[k];
+    bool done = false;
+    if (hint >= 1 && hint <= rmax) {
+      if (res_at(hint) <= tol_trunc) {
+        hi = hint;
+        if (hint == 1 || res_at(hint - 1) > tol_trunc) {
+          lo = hint;
+          done = true;
+        } else {
+          hi = hint - 1;
+        }
+      } else {
+        lo = hint + 1;
+        if (lo > rmax) {
+          lo = rmax;  // cannot meet the tolerance: keep everything
+          done = true;
+        }
+      }
+    }
+    if (!done) {
+      if (hint < 1 || hint > rmax) {
+        if (res_at(hi) > tol_trunc) {
+          lo = hi;  // cannot meet the tolerance: keep everything
+          done = true;
+        }
+      }
+      while (!done && lo < hi) {
         const int mid = (lo + hi) / 2;
         if (res_at(mid) <= tol_trunc) hi = mid; else lo = mid + 1;
       }
     }
     int r = lo;
+    trunc_hint[k] = r;
     if (o.max_rank > 0) r = std::min(r, o.max_rank);
     // a rank above the product of the remaining mode sizes only adds null directions
     const long long right_cap = (k == 0) ? (long long)n(1) * n(2) : (long long)n(2);

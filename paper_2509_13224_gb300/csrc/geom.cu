@@ -3,7 +3,8 @@
 // * Gauss rule: Golub-Welsch -- nodes are the eigenvalues of the symmetric
 //   tridiagonal Jacobi matrix of the Legendre recurrence (off-diagonal
 //   k / sqrt(4k^2 - 1)), weights 2 v_0^2 from the normalised eigenvectors;
-//   eigenpairs by cyclic Jacobi rotations on the dense m x m matrix (m <= 8).
+//   eigenpairs by cyclic Jacobi rotations on the dense m x m matrix (m <= 8),
+//   computed once on the host and passed to the table kernel by value.
 // * Basis: for element e the nonzero functions are e..e+p (open uniform
 //   knots, knot span e+p); values by the Cox-de Boor triangle of Section 2.1
 //   and first derivatives by its derivative formula applied to the degree
@@ -42,10 +43,13 @@ RhsParams rhs_params(const tt_iga_rhs_desc *r) {
   return p;
 }
 
-__global__ void k_basis_tables(int n, int p, int nq, double *pts, double *wts, double *N, double *dN) {
-  __shared__ double gx[8], gw[8];
-  if (threadIdx.x == 0) golub_welsch(nq, gx, gw);
-  __syncthreads();
+struct GaussRule {
+  double x[8], w[8];
+};
+
+__global__ void k_basis_tables(int n, int p, int nq, GaussRule rule, double *pts, double *wts, double *N,
+                               double *dN) {
+  const double *gx = rule.x, *gw = rule.w;
   const int ne = n - p, Q = ne * nq;
   for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < Q; q += gridDim.x * blockDim.x) {
     const int e = q / nq, l = q % nq;
@@ -65,7 +69,10 @@ __global__ void k_basis_tables(int n, int p, int nq, double *pts, double *wts, d
 void basis_tables(Ctx *c, int n, int p, int nq, double *pts, double *wts, double *N, double *dN) {
   TTI_CHECK_ARG(p >= 1 && p <= 7 && nq >= 1 && nq <= 8 && n >= p + 1, "basis tables: bad n=%d p=%d nq=%d", n, p, nq);
   const int Q = (n - p) * nq;
-  k_basis_tables<<<grid1d(Q, 128), 128, 0, c->stream>>>(n, p, nq, pts, wts, N, dN);
+  // the nq-point rule on [-1, 1] (nq <= 8) is computed once on the host and passed by value
+  GaussRule rule{};
+  golub_welsch(nq, rule.x, rule.w);
+  k_basis_tables<<<grid1d(Q, 128), 128, 0, c->stream>>>(n, p, nq, rule, pts, wts, N, dN);
   TTI_LAUNCH();
 }
 

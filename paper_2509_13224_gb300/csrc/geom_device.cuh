@@ -15,7 +15,7 @@ __device__ inline double knot_at(int i, int n, int p) {
 }
 
 // Gauss-Legendre nodes/weights on [-1, 1] by Golub-Welsch (single thread, m <= 8).
-__device__ inline void golub_welsch(int m, double *x, double *w) {
+__host__ __device__ inline void golub_welsch(int m, double *x, double *w) {
   double A[8][8], V[8][8];
   for (int i = 0; i < m; ++i)
     for (int j = 0; j < m; ++j) {
