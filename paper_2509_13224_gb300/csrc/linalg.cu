@@ -539,6 +539,17 @@ void qr(Ctx *c, int m, int k, const double *A, long long lda, double *Q, double 
 
 // ------------------------------------------------------- one-sided Jacobi SVD
 
+// One-sided Jacobi SVD of a k x k matrix (k <= 256), one CTA.  Each pair of
+// columns is handled by a group of G lanes (G = 4, 8, 16 or 32, the smallest
+// power of two >= k, 32 beyond): the three dot products reduce in log2(G)
+// shuffle levels, and all kp/2 pairs of a round run at once when the CTA is
+// large enough (for k <= 8 a single warp, synchronised with __syncwarp).  The
+// rotation angle is computed in FP32 from the FP64 dot products and cos/sin are
+// then formed in FP64 from that tangent, so every rotation is orthogonal to FP64
+// precision; an angle that is only FP32-accurate leaves a relative 1e-7 of the
+// off-diagonal entry, which later sweeps remove (convergence is tested in FP64:
+// g^2 <= tol^2 a b).  A tangent that FP32 cannot represent is computed in FP64.
+template <int G>
 __global__ void __launch_bounds__(1024) k_jacobi_svd(int k, const double *__restrict__ A, double *__restrict__ U,
                                                     double *__restrict__ S, double *__restrict__ V,
                                                     double *Wg, double *Vg, int use_smem, int *status) {
@@ -549,6 +560,11 @@ __global__ void __launch_bounds__(1024) k_jacobi_svd(int k, const double *__rest
   double *W = use_smem ? smem : Wg;           // W[c * k + i]: column c, row i
   double *Vw = use_smem ? smem + (size_t)kp * k : Vg;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+  const bool one_warp = blockDim.x == 32;
+  auto sync = [&] {
+    if (one_warp) __syncwarp();
+    else __syncthreads();
+  };
   __shared__ double red[32];
   double fro = 0.0;
   for (int e = tid; e < kp * k; e += blockDim.x) {
@@ -558,43 +574,66 @@ __global__ void __launch_bounds__(1024) k_jacobi_svd(int k, const double *__rest
     fro += v * v;
     Vw[e] = (cc == i) ? 1.0 : 0.0;
   }
-  fro = block_sum(fro, red);
+  fro = warp_sum(fro);
+  if (!one_warp) {
+    if (lane == 0) red[warp] = fro;
+    __syncthreads();
+    fro = 0.0;
+    for (int w = 0; w < nw; ++w) fro += red[w];
+  }
   // columns whose squared norm is below this are roundoff: rotating them changes nothing
   const double tiny = fro * 1e-32 + 1e-300;
-  const double tol = 4.0 * k * DBL_EPSILON;
-  __syncthreads();
+  const double tol = 4.0 * k * DBL_EPSILON, tol2 = tol * tol;
+  sync();
+  const int li = tid % G, grp = tid / G, ngrp = blockDim.x / G;
   int sweep = 0;
   for (; sweep < 60; ++sweep) {
     int rotated = 0;
     for (int rd = 0; rd < kp - 1; ++rd) {
-      for (int pi = warp; pi < kp / 2; pi += nw) {
-        int p = (rd + pi) % (kp - 1);
-        int q = (pi == 0) ? kp - 1 : (rd - pi + kp - 1) % (kp - 1);
-        if (p > q) { int t = p; p = q; q = t; }
+      // every lane runs the same number of passes (the shuffles below need the whole
+      // warp); a group without a pair in this pass contributes zeros and rotates nothing
+      for (int base = 0; base < kp / 2; base += ngrp) {
+        const int pi = base + grp;
+        const bool act = pi < kp / 2;
+        int p = 0, q = 1;
+        if (act) {
+          p = (rd + pi) % (kp - 1);
+          q = (pi == 0) ? kp - 1 : (rd - pi + kp - 1) % (kp - 1);
+          if (p > q) { int t = p; p = q; q = t; }
+        }
         double *wp = W + (size_t)p * k, *wq = W + (size_t)q * k;
         double a = 0.0, b = 0.0, g = 0.0;
-        for (int i = lane; i < k; i += 32) {
-          const double x = wp[i], y = wq[i];
-          a += x * x;
-          b += y * y;
-          g += x * y;
+        if (act)
+          for (int i = li; i < k; i += G) {
+            const double x = wp[i], y = wq[i];
+            a += x * x;
+            b += y * y;
+            g += x * y;
+          }
+#pragma unroll
+        for (int o = G / 2; o > 0; o >>= 1) {
+          a += __shfl_xor_sync(0xffffffffu, a, o);
+          b += __shfl_xor_sync(0xffffffffu, b, o);
+          g += __shfl_xor_sync(0xffffffffu, g, o);
         }
-        a = warp_sum(a);
-        b = warp_sum(b);
-        g = warp_sum(g);
-        if (g != 0.0 && a > tiny && b > tiny && fabs(g) > tol * sqrt(a) * sqrt(b)) {
-          const double zeta = (b - a) / (2.0 * g);
+        if (act && g != 0.0 && a > tiny && b > tiny && g * g > tol2 * a * b) {
+          const double num = b - a, den = 2.0 * g;
+          const float zf = (float)num / (float)den;
           double t;
-          if (fabs(zeta) > 1e100) t = 0.5 / zeta;
-          else t = copysign(1.0, zeta) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
-          const double cs = 1.0 / sqrt(1.0 + t * t), sn = cs * t;
-          for (int i = lane; i < k; i += 32) {
+          if (isfinite(zf) && fabsf(zf) < 1e15f && fabsf(zf) > 1e-15f) {
+            t = (double)(copysignf(1.f, zf) / (fabsf(zf) + sqrtf(1.f + zf * zf)));
+          } else {
+            const double zeta = num / den;
+            t = (fabs(zeta) > 1e100) ? 0.5 / zeta : copysign(1.0, zeta) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+          }
+          const double cs = rsqrt(1.0 + t * t), sn = cs * t;
+          for (int i = li; i < k; i += G) {
             const double x = wp[i], y = wq[i];
             wp[i] = cs * x - sn * y;
             wq[i] = sn * x + cs * y;
           }
           double *vp = Vw + (size_t)p * k, *vq = Vw + (size_t)q * k;
-          for (int i = lane; i < k; i += 32) {
+          for (int i = li; i < k; i += G) {
             const double x = vp[i], y = vq[i];
             vp[i] = cs * x - sn * y;
             vq[i] = sn * x + cs * y;
@@ -602,9 +641,10 @@ __global__ void __launch_bounds__(1024) k_jacobi_svd(int k, const double *__rest
           rotated = 1;
         }
       }
-      __syncthreads();
+      sync();
     }
-    if (!__syncthreads_or(rotated)) break;
+    const int any = one_warp ? __any_sync(0xffffffffu, rotated) : __syncthreads_or(rotated);
+    if (!any) break;
   }
   if (sweep == 60 && tid == 0 && status) atomicMax(status, (int)DS_BREAKDOWN);
   for (int cc = warp; cc < k; cc += nw) {
@@ -613,7 +653,7 @@ __global__ void __launch_bounds__(1024) k_jacobi_svd(int k, const double *__rest
     s = warp_sum(s);
     if (lane == 0) nrm[cc] = sqrt(s);
   }
-  __syncthreads();
+  sync();
   if (tid == 0) {
     for (int i = 0; i < k; ++i) perm[i] = i;
     for (int i = 1; i < k; ++i) {  // insertion sort, descending, stable
@@ -622,7 +662,7 @@ __global__ void __launch_bounds__(1024) k_jacobi_svd(int k, const double *__rest
       perm[j + 1] = v;
     }
   }
-  __syncthreads();
+  sync();
   for (int e = tid; e < k * k; e += blockDim.x) {
     const int i = e / k, j = e % k;
     const int src = perm[j];
@@ -631,6 +671,24 @@ __global__ void __launch_bounds__(1024) k_jacobi_svd(int k, const double *__rest
     V[e] = Vw[(size_t)src * k + i];
   }
   for (int j = tid; j < k; j += blockDim.x) S[j] = nrm[perm[j]];
+}
+
+// Lane group and CTA size for a k x k SVD: every pair of a round gets a group.
+static void svd_launch(cudaStream_t st, int k, const double *A, double *U, double *s, double *V, double *Wg,
+                       double *Vg, int use_smem, size_t bytes, int *status) {
+  const int kp = k + (k & 1), pairs = kp / 2;
+  const int G = k <= 4 ? 4 : (k <= 8 ? 8 : (k <= 16 ? 16 : 32));
+  const int threads = std::min(1024, std::max(32, (pairs * G + 31) / 32 * 32));
+  switch (G) {
+    case 4: k_jacobi_svd<4><<<1, threads, bytes, st>>>(k, A, U, s, V, Wg, Vg, use_smem, status); break;
+    case 8: k_jacobi_svd<8><<<1, threads, bytes, st>>>(k, A, U, s, V, Wg, Vg, use_smem, status); break;
+    case 16: k_jacobi_svd<16><<<1, threads, bytes, st>>>(k, A, U, s, V, Wg, Vg, use_smem, status); break;
+    default:
+      if (bytes > 48 * 1024)
+        TTI_CUDA(cudaFuncSetAttribute(k_jacobi_svd<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+      k_jacobi_svd<32><<<1, threads, bytes, st>>>(k, A, U, s, V, Wg, Vg, use_smem, status);
+      break;
+  }
 }
 
 void svd_small(Ctx *c, int k, const double *A, double *U, double *s, double *V) {
@@ -643,10 +701,8 @@ void svd_small(Ctx *c, int k, const double *A, double *U, double *s, double *V) 
     Wg = DBuf(c, (size_t)kp * k * sizeof(double));
     Vg = DBuf(c, (size_t)kp * k * sizeof(double));
     bytes = 0;
-  } else if (bytes > 48 * 1024) {
-    TTI_CUDA(cudaFuncSetAttribute(k_jacobi_svd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
   }
-  k_jacobi_svd<<<1, 1024, bytes, c->stream>>>(k, A, U, s, V, Wg.d(), Vg.d(), use_smem, c->dstatus);
+  svd_launch(c->stream, k, A, U, s, V, Wg.d(), Vg.d(), use_smem, bytes, c->dstatus);
   TTI_LAUNCH();
 }
 
@@ -681,7 +737,7 @@ int svd_small_noalloc(cudaStream_t stream, int k, const double *A, double *U, do
     }
     scratch = g_scratch_ptr[dev];
   }
-  k_jacobi_svd<<<1, 1024, 0, stream>>>(k, A, U, s, V, scratch, scratch + 256 * 256, 0, nullptr);
+  svd_launch(stream, k, A, U, s, V, scratch, scratch + 256 * 256, 0, 0, nullptr);
   g_launches.fetch_add(1, std::memory_order_relaxed);
   return cudaGetLastError() == cudaSuccess ? TT_IGA_OK : TT_IGA_ERR_CUDA;
 }
