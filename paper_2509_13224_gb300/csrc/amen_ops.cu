@@ -158,6 +158,9 @@ template <> __device__ __forceinline__ double recip_sqrt<double>(double v) { ret
 
 template <typename T, int PB>
 __global__ void k_band_cholesky(const double *__restrict__ Pm, int rl, int n, int rr, T *__restrict__ L, int *status) {
+  // rows are loaded in groups of RG, one group ahead, so the memory latency is
+  // exposed once per group instead of once per row
+  constexpr int RG = 4;
   const int npair = rl * rr, b = 2 * PB + 1;
   for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < npair; t += gridDim.x * blockDim.x) {
     const int a = t / rr, bb = t % rr;
@@ -168,8 +171,9 @@ __global__ void k_band_cholesky(const double *__restrict__ Pm, int rl, int n, in
 #pragma unroll
       for (int k = 0; k <= PB; ++k) win[q][k] = T(0);
     bool bad = false;
-    // symmetrised band entries of a row: A(i, i-PB+k) for k <= PB (loaded one row ahead)
+    // symmetrised band entries of a row: A(i, i-PB+k) for k <= PB
     auto load_row = [&](int i, T *out) {
+      if (i >= n) return;
 #pragma unroll
       for (int k = 0; k < PB; ++k) {
         const int j = i - PB + k;
@@ -178,42 +182,51 @@ __global__ void k_band_cholesky(const double *__restrict__ Pm, int rl, int n, in
       }
       out[PB] = (T)Pp[((long long)i * b + PB) * rr];
     };
-    T nxt[PB + 1];
-    load_row(0, nxt);
-    for (int i = 0; i < n; ++i) {
-      T cur[PB + 1];
+    T nxt[RG][PB + 1];
 #pragma unroll
-      for (int k = 0; k <= PB; ++k) cur[k] = nxt[k];
-      if (i + 1 < n) load_row(i + 1, nxt);
-      T row[PB + 1];
+    for (int g = 0; g < RG; ++g) load_row(g, nxt[g]);
+    for (int i0 = 0; i0 < n; i0 += RG) {
+      T cur[RG][PB + 1];
 #pragma unroll
-      for (int k = 0; k < PB; ++k) {
-        const int j = i - PB + k;
-        if (j < 0) {
-          row[k] = T(0);
-          continue;
+      for (int g = 0; g < RG; ++g)
+#pragma unroll
+        for (int k = 0; k <= PB; ++k) cur[g][k] = nxt[g][k];
+#pragma unroll
+      for (int g = 0; g < RG; ++g) load_row(i0 + RG + g, nxt[g]);
+#pragma unroll
+      for (int g = 0; g < RG; ++g) {
+        const int i = i0 + g;
+        if (i >= n) break;
+        T row[PB + 1];
+#pragma unroll
+        for (int k = 0; k < PB; ++k) {
+          const int j = i - PB + k;
+          if (j < 0) {
+            row[k] = T(0);
+            continue;
+          }
+          T sv = cur[g][k];
+#pragma unroll
+          for (int mm = 0; mm < k; ++mm) sv -= row[mm] * win[k][mm + PB - k];
+          row[k] = sv * win[k][PB];
         }
-        T sv = cur[k];
+        T sd = cur[g][PB];
 #pragma unroll
-        for (int mm = 0; mm < k; ++mm) sv -= row[mm] * win[k][mm + PB - k];
-        row[k] = sv * win[k][PB];
+        for (int mm = 0; mm < PB; ++mm) sd -= row[mm] * row[mm];
+        if (!(sd > T(1e-6) * cur[g][PB])) {
+          if (!(cur[g][PB] > T(0))) bad = true;
+          sd = (cur[g][PB] > T(0)) ? cur[g][PB] : T(1);
+        }
+        row[PB] = recip_sqrt<T>(sd);
+#pragma unroll
+        for (int k = 0; k <= PB; ++k) L[((long long)i * (PB + 1) + k) * npair + t] = row[k];
+#pragma unroll
+        for (int q = 0; q + 1 < PB; ++q)
+#pragma unroll
+          for (int k = 0; k <= PB; ++k) win[q][k] = win[q + 1][k];
+#pragma unroll
+        for (int k = 0; k <= PB; ++k) win[PB - 1][k] = row[k];
       }
-      T sd = cur[PB];
-#pragma unroll
-      for (int mm = 0; mm < PB; ++mm) sd -= row[mm] * row[mm];
-      if (!(sd > T(1e-6) * cur[PB])) {
-        if (!(cur[PB] > T(0))) bad = true;
-        sd = (cur[PB] > T(0)) ? cur[PB] : T(1);
-      }
-      row[PB] = recip_sqrt<T>(sd);
-#pragma unroll
-      for (int k = 0; k <= PB; ++k) L[((long long)i * (PB + 1) + k) * npair + t] = row[k];
-#pragma unroll
-      for (int q = 0; q + 1 < PB; ++q)
-#pragma unroll
-        for (int k = 0; k <= PB; ++k) win[q][k] = win[q + 1][k];
-#pragma unroll
-      for (int k = 0; k <= PB; ++k) win[PB - 1][k] = row[k];
     }
     if (bad) atomicMax(status, (int)DS_BREAKDOWN);
   }

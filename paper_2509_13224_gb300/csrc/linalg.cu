@@ -365,11 +365,28 @@ __global__ void k_qr_load(const double *__restrict__ A, long long lda, long long
   }
 }
 
+// Sum over the CTA, result broadcast: warps reduce by shuffles, warp 0 combines
+// the warp partials in a tree (log2 of the warp count dependent adds instead of
+// one per warp, each FP64 add costing tens of cycles here).
+__device__ __forceinline__ double cta_sum_tree(double v, double *red, double *out) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+  v = warp_sum(v);
+  if (lane == 0) red[warp] = v;
+  __syncthreads();
+  if (warp == 0) {
+    double t = (lane < nw) ? red[lane] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+    if (lane == 0) *out = t;
+  }
+  __syncthreads();
+  return *out;
+}
+
 __global__ void __launch_bounds__(256) k_qr_panel(double *__restrict__ W, int mb, int k, double *__restrict__ tau,
                                                   double *__restrict__ Rout, int use_smem) {
   extern __shared__ double qsm[];
   __shared__ double red[32];
-  __shared__ double sh[3];
+  __shared__ double sh[4];
   const long long blk = blockIdx.x;
   double *Wg = W + blk * (long long)mb * k;
   double *Wb = Wg;
@@ -384,16 +401,18 @@ __global__ void __launch_bounds__(256) k_qr_panel(double *__restrict__ W, int mb
     double *col = Wb + (long long)j * mb;
     double s = 0.0;
     for (int i = j + 1 + tid; i < mb; i += blockDim.x) s += col[i] * col[i];
-    s = block_sum(s, red);
+    s = cta_sum_tree(s, red, &sh[3]);
     if (tid == 0) {
       const double x0 = (j < mb) ? col[j] : 0.0;
       if (s == 0.0) {
         sh[0] = 0.0; sh[1] = x0; sh[2] = 0.0;
       } else {
-        const double beta = -copysign(sqrt(x0 * x0 + s), x0);
-        sh[0] = (beta - x0) / beta;
-        sh[1] = beta;
-        sh[2] = 1.0 / (x0 - beta);
+        // beta = -sign(x0) sqrt(h), h = x0^2 + s; with y = 1/sqrt(h): |beta| = h y,
+        // tau = (beta - x0) / beta = 1 + |x0| y, and 1/(x0 - beta) = sign(x0) / (|x0| + h y)
+        const double h = x0 * x0 + s, y = rsqrt(h), ab = h * y;
+        sh[0] = 1.0 + fabs(x0) * y;
+        sh[1] = -copysign(ab, x0);
+        sh[2] = copysign(1.0, x0) / (fabs(x0) + ab);
       }
       tb[j] = sh[0];
     }
@@ -406,9 +425,14 @@ __global__ void __launch_bounds__(256) k_qr_panel(double *__restrict__ W, int mb
     if (tj != 0.0) {
       for (int cc = j + 1 + warp; cc < k; cc += nw) {
         double *ccol = Wb + (long long)cc * mb;
-        double w = (lane == 0) ? ccol[j] : 0.0;
-        for (int i = j + 1 + lane; i < mb; i += 32) w += col[i] * ccol[i];
-        w = warp_sum(w) * tj;
+        double w = (lane == 0) ? ccol[j] : 0.0, w2 = 0.0;
+        int i = j + 1 + lane;
+        for (; i + 32 < mb; i += 64) {
+          w += col[i] * ccol[i];
+          w2 += col[i + 32] * ccol[i + 32];
+        }
+        if (i < mb) w += col[i] * ccol[i];
+        w = warp_sum(w + w2) * tj;
         if (lane == 0) ccol[j] -= w;
         for (int i = j + 1 + lane; i < mb; i += 32) ccol[i] -= w * col[i];
       }
