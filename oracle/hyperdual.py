@@ -76,6 +76,12 @@ def cos(x):
     return np.cos(x)
 
 
+def log(x):
+    if isinstance(x, HD):
+        return x.apply(np.log(x.a), 1.0 / x.a, -1.0 / (x.a * x.a))
+    return np.log(x)
+
+
 def laplacian(u, X):
     """Sum over k of d^2 u / d x_k^2 at points X[..., 3] for a function u(x, y, z)."""
     total = np.zeros(X.shape[:-1])

@@ -9,7 +9,10 @@ approximates: element-loop quadrature of
 with the same per-direction Gauss rule as the TT path (p+1 points per element
 unless stated), homogeneous Dirichlet data on all six faces imposed by
 dropping the first and last basis function of every direction (the open knot
-vector makes the basis interpolatory at the ends), a Jacobi-preconditioned
+vector makes the basis interpolatory at the ends) -- or, for the
+non-homogeneous Dirichlet problem of Section 4.3 (constant data on some faces,
+natural conditions on the others), a lift g carrying the data on the dropped
+functions and the right-hand side F - K g -- a Jacobi-preconditioned
 conjugate-gradient solve of the restricted system, and the relative L2 error
 of Eq. (L2norm) read as sqrt(int (u_h - u)^2) / sqrt(int u^2) with p+3 Gauss
 points per element.
@@ -167,6 +170,70 @@ def restrict(Kst, F):
             sl[3 + d] = o
             Ki[tuple(sl)] = 0.0
     return Ki, F[1:-1, 1:-1, 1:-1].copy()
+
+
+def bc_ranges(n, dirichlet):
+    """Kept functions per direction: a Dirichlet face drops the basis function that is
+    interpolatory on it (index 0 on xi_d = 0, n_d - 1 on xi_d = 1).  Face f = 2 d + side."""
+    lo = [1 if dirichlet[2 * d] else 0 for d in range(3)]
+    hi = [1 if dirichlet[2 * d + 1] else 0 for d in range(3)]
+    return lo, hi
+
+
+def restrict_bc(Kst, F, lo, hi):
+    """Rows/columns lo_d .. n_d - 1 - hi_d of the stencil operator and the load vector."""
+    n = Kst.shape[:3]
+    sl = tuple(slice(lo[d], n[d] - hi[d]) for d in range(3))
+    Ki = Kst[sl].copy()
+    p = tuple((q - 1) // 2 for q in Kst.shape[3:])
+    m = Ki.shape[:3]
+    for d in range(3):
+        for o in range(Kst.shape[3 + d]):
+            shift = o - p[d]
+            idx = np.arange(m[d])
+            bad = (idx + shift < 0) | (idx + shift >= m[d])
+            sel = [slice(None)] * 6
+            sel[d] = bad
+            sel[3 + d] = o
+            Ki[tuple(sel)] = 0.0
+    return Ki, F[sl].copy()
+
+
+def lift_vector(n, dirichlet, value):
+    """Coefficients g of the Dirichlet data: the constant face value on the interpolatory
+    boundary function of every Dirichlet face, zero elsewhere.  Nonzero data is accepted on
+    the faces of one direction only, and the faces of the other two directions must then be
+    natural, so that no coefficient belongs to two faces with different data."""
+    g = np.zeros(n)
+    dirs = [d for d in range(3) if any(dirichlet[2 * d + s] and value[2 * d + s] != 0.0 for s in range(2))]
+    assert len(dirs) <= 1, "nonzero Dirichlet data on more than one direction"
+    for d in dirs:
+        assert not any(dirichlet[2 * e + s] for e in range(3) if e != d for s in range(2)), \
+            "nonzero Dirichlet data with Dirichlet faces in another direction"
+        for s in range(2):
+            if dirichlet[2 * d + s]:
+                sel = [slice(None)] * 3
+                sel[d] = 0 if s == 0 else n[d] - 1
+                g[tuple(sel)] = value[2 * d + s]
+    return g
+
+
+def solve_bc(spaces, geom, source, dirichlet, value, tol=1e-14):
+    """Dirichlet faces with constant data, natural (zero-flux) conditions on the others:
+    u = g + u_I with K_II u_I = F_I - (K g)_I; returns the full coefficient array."""
+    assert any(dirichlet), "pure natural conditions leave K singular"
+    Kst, F = assemble(spaces, geom, source)
+    n = F.shape
+    p = tuple(s.p for s in spaces)
+    g = lift_vector(n, dirichlet, value)
+    lo, hi = bc_ranges(n, dirichlet)
+    rhs = F - stencil_matvec(Kst, g, p)
+    Ki, Fi = restrict_bc(Kst, rhs, lo, hi)
+    ui, it, relres = pcg(Ki, Fi, p, tol=tol)
+    u = g.copy()
+    u[tuple(slice(lo[d], n[d] - hi[d]) for d in range(3))] += ui
+    return u, {"iterations": it, "relres": relres, "Kst": Kst, "F": F, "lo": lo, "hi": hi, "lift": g,
+               "Ki": Ki, "Fi": Fi}
 
 
 def pcg(Kst, F, p, tol=1e-14, maxiter=100000, x0=None):

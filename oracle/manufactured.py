@@ -64,3 +64,20 @@ class ConstantSource:
 
     def f(self, X):
         return np.full(X.shape[:-1], self.value)
+
+
+class RingLog:
+    """Exact solution of -Laplace(u) = 0 on the quarter cylinder (no twist, no swell) with
+    u = u_in on rho = r_in, u = u_out on rho = r_out and zero flux on the other faces
+    (Section 4.3, the ring problem): u = u_in + (u_out - u_in) ln(rho / r_in) / ln(r_out / r_in)."""
+
+    def __init__(self, r_in=1.0, r_out=2.0, u_in=1.0, u_out=2.0):
+        self.r_in, self.r_out = float(r_in), float(r_out)
+        self.u_in, self.u_out = float(u_in), float(u_out)
+
+    def u(self, X):
+        rho = np.sqrt(X[..., 0] ** 2 + X[..., 1] ** 2)
+        return self.u_in + (self.u_out - self.u_in) * np.log(rho / self.r_in) / np.log(self.r_out / self.r_in)
+
+    def f(self, X):
+        return np.zeros(X.shape[:-1])
