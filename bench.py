@@ -329,6 +329,37 @@ def run_ours(args, rank, world):
             extra[name] = {"value": world * wx["n"] ** 3 / (ms / 1e3), "ms_per_step": ms,
                            "rel_residual": st["rel_residual"], "ranks": st["ranks"], "sweeps": st["sweeps"]}
 
+    # side measurement: the ring problem of Section 4.3 (Dirichlet data 1 and 2 on the radial faces,
+    # natural conditions elsewhere, f = 0) on the quarter cylinder at the bench size, with its L2 error
+    # against the log solution
+    ring = None
+    if not args.no_extra and args.workload == WORKLOAD:
+        bc = tt.bc_desc([1, 1, 0, 0, 0, 0], [1.0, 2.0, 0, 0, 0, 0])
+        rrhs = [tt.rhs_desc(ring_log=True)]
+        ring = {"workload": "ring_quarter_cylinder_p3_n128", "dofs": dofs, "bc": "u=1 on rho=1, u=2 on rho=2, natural"}
+        ts = []
+        for rep in range(3):
+            with torch.cuda.stream(stream):
+                flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            g = tt.tt_iga_geometry(ctx, gdesc)
+            s = tt.tt_iga_assemble_bc(ctx, g, rrhs, bc, round_tol=wl["round_tol"])
+            u, st = tt.tt_iga_solve(ctx, s, tt.solve_opts(tol=TOL, precision=tt.FP64))
+            e1.record(stream)
+            e1.synchronize()
+            if rep > 0:
+                ts.append(e0.elapsed_time(e1))
+            if rep == 2:
+                ring["l2_error"] = tt.tt_iga_l2_error(ctx, g, u, rrhs[0])
+            tt.tt_iga_solution_destroy(u)
+            tt.tt_iga_system_destroy(s)
+            tt.tt_iga_geom_destroy(g)
+        ms = max_over_ranks(statistics.mean(ts), world)
+        ring.update({"value": world * dofs / (ms / 1e3), "unit": "DOFs/s", "ms_per_step": ms,
+                     "rel_residual": st["rel_residual"], "ranks": st["ranks"], "sweeps": st["sweeps"]})
+
     # end to end through the C ABI: host descriptors in, compressed solution cores read back to pinned host memory
     e2e_times = []
     hbuf = None
@@ -412,7 +443,7 @@ def run_ours(args, rank, world):
             "e2e": {"value": world * dofs / e2e_s, "unit": "DOFs/s", "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h},
             "gpu_launches": launches, "clocks": clk, "roofline": roof, "cpu_baseline": base, "mixed": mixed,
-            "twisted_n512": extra, "batched": batched, "serving": serving,
+            "twisted_n512": extra, "ring_dirichlet": ring, "batched": batched, "serving": serving,
             "phases_ms": info64.get("phases_ms"),
             "solve": {"rel_residual": info64.get("rel_residual"), "sweeps": info64.get("sweeps"),
                       "ranks": info64.get("ranks"), "op_ranks": info64.get("op_ranks"),

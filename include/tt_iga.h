@@ -144,14 +144,20 @@ int tt_iga_geom_ranks(const tt_iga_geom *g, int ranks[6][2], double max_rel_err[
 
 /* ------------------------------------------------------------ right-hand side */
 
-enum { TT_IGA_RHS_MANUFACTURED = 0, TT_IGA_RHS_CONSTANT = 1 };
+enum { TT_IGA_RHS_MANUFACTURED = 0, TT_IGA_RHS_CONSTANT = 1, TT_IGA_RHS_RING_LOG = 2 };
 #define TT_IGA_MAX_MODES 8
 
 /* Source term.  MANUFACTURED: f = -Laplace(u) of the bubble solution of the
  * geometry (annulus: (rho^2 - r_in^2)(r_out^2 - rho^2) x' y' zeta (1 - zeta) in
  * the coordinates with twist and swell undone; box: sin(pi x/lx) sin(pi y/ly)
  * sin(pi z/lz)) times 1 + sum_k a[k] sin(b[k] . x + c[k]); the Laplacian is
- * taken exactly on the device by hyper-dual arithmetic.  CONSTANT: f = value. */
+ * taken exactly on the device by hyper-dual arithmetic.  CONSTANT: f = value.
+ * RING_LOG: f = value (0 for the ring problem of Section 4.3); with Dirichlet
+ * data u_in on the radial face xi_1 = 0 and u_out on xi_1 = 1 of the annulus
+ * without twist and swell, natural conditions elsewhere, and value 0, the exact
+ * solution is u = u_in + (u_out - u_in) ln(rho / r_in) / ln(r_out / r_in), which
+ * tt_iga_l2_error compares against (u_in, u_out taken from the solution's
+ * boundary data). */
 typedef struct {
   int kind;
   int n_modes; /* 0 .. TT_IGA_MAX_MODES */
@@ -172,6 +178,29 @@ typedef struct {
  * per direction are n_d - 2.  rhs points to n_rhs descriptors (n_rhs >= 1). */
 int tt_iga_assemble(tt_iga_ctx *ctx, const tt_iga_geom *g, const tt_iga_rhs_desc *rhs, int n_rhs,
                     double round_tol, tt_iga_system **out);
+
+/* Boundary conditions (Section 4.3).  Face f = 2 d + side of parametric
+ * direction d = 0, 1, 2 (side 0: xi_d = 0, side 1: xi_d = 1; for the annulus
+ * d = 0 is the radial direction).  dirichlet[f] != 0: u = value[f] on the face
+ * (constant data), imposed by dropping the basis function that is
+ * interpolatory there and moving the data to the right-hand side,
+ * F <- F - K g with g the lift carrying the data on the dropped functions;
+ * dirichlet[f] == 0: natural condition (zero normal flux).  Nonzero values are
+ * accepted on the faces of one direction only, and the faces of the other two
+ * directions must then be natural; at least one face must be Dirichlet
+ * (otherwise K is singular).  Violations return TT_IGA_ERR_ARG. */
+typedef struct {
+  int dirichlet[6];
+  double value[6];
+} tt_iga_bc_desc;
+
+/* tt_iga_assemble with boundary conditions bc (tt_iga_assemble is the case of
+ * six homogeneous Dirichlet faces).  The unknowns of direction d are the basis
+ * functions lo_d .. n_d - 1 - hi_d, lo_d / hi_d = 1 when face 2d / 2d+1 is
+ * Dirichlet, so the mode sizes are n_d - lo_d - hi_d; the solution, its
+ * evaluation and its L2 error include the lift. */
+int tt_iga_assemble_bc(tt_iga_ctx *ctx, const tt_iga_geom *g, const tt_iga_rhs_desc *rhs, int n_rhs,
+                       double round_tol, const tt_iga_bc_desc *bc, tt_iga_system **out);
 void tt_iga_system_destroy(tt_iga_system *s);
 /* Operator TT ranks (R1, R2), load ranks of right-hand side k, and mode sizes. */
 int tt_iga_system_info(const tt_iga_system *s, int op_ranks[2], int n_rhs_max, int (*rhs_ranks)[2],
@@ -225,7 +254,8 @@ int tt_iga_residual(tt_iga_ctx *ctx, const tt_iga_system *s, const tt_iga_soluti
 
 /* Copy the solution's TT cores to host memory: out receives core 1
  * [1][m1][r1], core 2 [r1][m2][r2] and core 3 [r2][m3][1] back to back (FP64);
- * modes[3] (m_d = n_d - 2) and ranks[4] are filled.  ERR_TOO_LARGE if cap (in
+ * modes[3] (m_d = n_d - 2 with six Dirichlet faces, n_d - lo_d - hi_d in
+ * general, see tt_iga_assemble_bc) and ranks[4] are filled.  ERR_TOO_LARGE if cap (in
  * doubles) is too small; pass out = NULL to query the sizes only. */
 int tt_iga_solution_cores(tt_iga_ctx *ctx, const tt_iga_solution *u, double *out, size_t cap, int modes[3],
                           int ranks[4]);
@@ -236,8 +266,10 @@ int tt_iga_solution_cores(tt_iga_ctx *ctx, const tt_iga_solution *u, double *out
  * xi and u_out are device pointers (FP64). */
 int tt_iga_eval(tt_iga_ctx *ctx, const tt_iga_solution *u, int m, const double *xi, double *u_out);
 /* Relative L2 error sqrt(int (u_h - u)^2) / sqrt(int u^2) over the mapped
- * domain (Eq. L2norm, with p+3 Gauss points per element) against the
- * manufactured solution of rhs (kind MANUFACTURED). */
+ * domain (Eq. L2norm, with p+3 Gauss points per element) against the exact
+ * solution of rhs: the manufactured solution (kind MANUFACTURED), or the log
+ * solution of the ring problem (kind RING_LOG: annulus without twist and swell,
+ * Dirichlet data on the radial faces only, taken from u's boundary data). */
 int tt_iga_l2_error(tt_iga_ctx *ctx, const tt_iga_geom *g, const tt_iga_solution *u,
                     const tt_iga_rhs_desc *rhs, double *rel_l2);
 

@@ -20,7 +20,7 @@ _lib = ctypes.CDLL(LIB_PATH)
 OK, ERR_ARG, ERR_OOM, ERR_CUDA, ERR_NOT_CONVERGED, ERR_TIMEOUT, ERR_TOO_LARGE, ERR_BAD_GEOMETRY, ERR_STATE = (
     0, -1, -2, -3, -4, -5, -6, -7, -8)
 GEOM_BOX, GEOM_ANNULUS = 0, 1
-RHS_MANUFACTURED, RHS_CONSTANT = 0, 1
+RHS_MANUFACTURED, RHS_CONSTANT, RHS_RING_LOG = 0, 1, 2
 FP64, MIXED_FP32, MIXED_TF32 = 0, 1, 2
 MAX_MODES = 8
 
@@ -45,6 +45,10 @@ class GeomDesc(ctypes.Structure):
                 ("lx", ctypes.c_double), ("ly", ctypes.c_double), ("lz", ctypes.c_double),
                 ("p", ctypes.c_int), ("n", ctypes.c_int * 3), ("nq", ctypes.c_int),
                 ("cross_tol", ctypes.c_double), ("max_rank", ctypes.c_int), ("seed", ctypes.c_uint64)]
+
+
+class BcDesc(ctypes.Structure):
+    _fields_ = [("dirichlet", ctypes.c_int * 6), ("value", ctypes.c_double * 6)]
 
 
 class RhsDesc(ctypes.Structure):
@@ -101,6 +105,8 @@ _SIGS = {
     "tt_iga_geometry": (ctypes.c_int, [_vp, ctypes.POINTER(GeomDesc), ctypes.POINTER(_vp)]),
     "tt_iga_geom_destroy": (None, [_vp]),
     "tt_iga_geom_ranks": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_int * 2 * 6), ctypes.POINTER(ctypes.c_double * 6)]),
+    "tt_iga_assemble_bc": (ctypes.c_int, [_vp, _vp, ctypes.POINTER(RhsDesc), ctypes.c_int, ctypes.c_double,
+                                          ctypes.POINTER(BcDesc), ctypes.POINTER(_vp)]),
     "tt_iga_assemble": (ctypes.c_int, [_vp, _vp, ctypes.POINTER(RhsDesc), ctypes.c_int, ctypes.c_double,
                                        ctypes.POINTER(_vp)]),
     "tt_iga_system_destroy": (None, [_vp]),
@@ -188,9 +194,14 @@ def geom_desc(geometry, p, n, cross_tol=1e-10, max_rank=0, seed=0, nq=0):
     return d
 
 
-def rhs_desc(modes=(), constant=None):
-    """RhsDesc: manufactured source with modulation modes [(a, (b1,b2,b3), c)], or a constant f."""
+def rhs_desc(modes=(), constant=None, ring_log=False):
+    """RhsDesc: manufactured source with modulation modes [(a, (b1,b2,b3), c)], a constant f, or
+    (ring_log) f = 0 whose exact solution is the log profile of the ring problem."""
     r = RhsDesc()
+    if ring_log:
+        r.kind = RHS_RING_LOG
+        r.value = 0.0
+        return r
     if constant is not None:
         r.kind = RHS_CONSTANT
         r.value = float(constant)
@@ -318,6 +329,22 @@ def tt_iga_assemble(ctx, g, rhs_list, round_tol=1e-12):
     arr = (RhsDesc * len(rhs_list))(*rhs_list)
     h = ctypes.c_void_p()
     _check(ctx, _lib.tt_iga_assemble(ctx, g, arr, len(rhs_list), round_tol, ctypes.byref(h)))
+    return h
+
+
+def bc_desc(dirichlet, values=(0.0,) * 6):
+    """BcDesc: dirichlet[f] (bool) and constant value[f] for face f = 2 d + side."""
+    b = BcDesc()
+    for f in range(6):
+        b.dirichlet[f] = 1 if dirichlet[f] else 0
+        b.value[f] = float(values[f])
+    return b
+
+
+def tt_iga_assemble_bc(ctx, g, rhs_list, bc, round_tol=1e-12):
+    arr = (RhsDesc * len(rhs_list))(*rhs_list)
+    h = ctypes.c_void_p()
+    _check(ctx, _lib.tt_iga_assemble_bc(ctx, g, arr, len(rhs_list), round_tol, ctypes.byref(bc), ctypes.byref(h)))
     return h
 
 

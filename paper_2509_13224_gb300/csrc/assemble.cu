@@ -10,6 +10,7 @@
 #include <algorithm>
 #include <cmath>
 
+#include "amen_ops.cuh"
 #include "handles.cuh"
 #include "linalg.cuh"
 #include "tt.cuh"
@@ -83,8 +84,9 @@ void load_core(Ctx *c, int n, int p, int nq, const double *wts, const double *N,
 
 // Drop basis functions 0 and n-1 (homogeneous Dirichlet, Section 4.3):
 // band core [r0][n][b][r1] -> [r0][n-2][b][r1], zeroing couplings to the dropped functions.
-__global__ void k_restrict_band(const double *src, double *dst, int r0, int n, int p, int r1) {
-  const int b = 2 * p + 1, nr = n - 2;
+// Keep functions lo .. lo + nr - 1 of a band core (couplings to dropped functions zeroed).
+__global__ void k_restrict_band(const double *src, double *dst, int r0, int n, int p, int r1, int lo, int nr) {
+  const int b = 2 * p + 1;
   const long long tot = (long long)r0 * nr * b * r1;
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < tot; e += (long long)gridDim.x * blockDim.x) {
     const int beta = (int)(e % r1);
@@ -94,47 +96,90 @@ __global__ void k_restrict_band(const double *src, double *dst, int r0, int n, i
     const int ir = (int)(t % nr);
     const int alpha = (int)(t / nr);
     const int jr = ir + o - p;
-    dst[e] = (jr >= 0 && jr < nr) ? src[(((long long)alpha * n + ir + 1) * b + o) * r1 + beta] : 0.0;
+    dst[e] = (jr >= 0 && jr < nr) ? src[(((long long)alpha * n + ir + lo) * b + o) * r1 + beta] : 0.0;
   }
 }
 
-__global__ void k_restrict_vec(const double *src, double *dst, int r0, int n, int r1) {
-  const int nr = n - 2;
+__global__ void k_restrict_vec(const double *src, double *dst, int r0, int n, int r1, int lo, int nr) {
   const long long tot = (long long)r0 * nr * r1;
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < tot; e += (long long)gridDim.x * blockDim.x) {
     const int beta = (int)(e % r1);
     const long long t = e / r1;
     const int ir = (int)(t % nr), alpha = (int)(t / nr);
-    dst[e] = src[((long long)alpha * n + ir + 1) * r1 + beta];
+    dst[e] = src[((long long)alpha * n + ir + lo) * r1 + beta];
   }
 }
 
-static void restrict_tt(Ctx *c, TT3 &x, const int n[3], int p, bool band) {
+static void restrict_tt(Ctx *c, TT3 &x, const BoundaryLayout &bl, int p, bool band) {
   for (int k = 0; k < 3; ++k) {
     const int r0 = x.r[k], r1 = x.r[k + 1];
-    const int nr = n[k] - 2;
+    const int n = bl.nfull[k], nr = n - bl.lo[k] - bl.hi[k];
     const int bw = band ? 2 * p + 1 : 1;
     DBuf out(c, (size_t)r0 * nr * bw * r1 * sizeof(double));
     const long long tot = (long long)r0 * nr * bw * r1;
     if (band)
-      k_restrict_band<<<grid1d(tot, 256), 256, 0, c->stream>>>(x.core[k].d(), out.d(), r0, n[k], p, r1);
+      k_restrict_band<<<grid1d(tot, 256), 256, 0, c->stream>>>(x.core[k].d(), out.d(), r0, n, p, r1, bl.lo[k], nr);
     else
-      k_restrict_vec<<<grid1d(tot, 256), 256, 0, c->stream>>>(x.core[k].d(), out.d(), r0, n[k], r1);
+      k_restrict_vec<<<grid1d(tot, 256), 256, 0, c->stream>>>(x.core[k].d(), out.d(), r0, n, r1, bl.lo[k], nr);
     TTI_LAUNCH();
     x.core[k] = std::move(out);
     x.m[k] = nr * bw;
   }
 }
 
+static TT3 clone_tt(Ctx *c, const TT3 &x) {
+  TT3 y;
+  for (int k = 0; k < 3; ++k) y.m[k] = x.m[k];
+  for (int k = 0; k < 4; ++k) y.r[k] = x.r[k];
+  y.alloc(c);
+  for (int k = 0; k < 3; ++k)
+    TTI_CUDA(cudaMemcpyAsync(y.core[k].get(), x.core[k].get(), x.core_elems(k) * sizeof(double),
+                             cudaMemcpyDeviceToDevice, c->stream));
+  return y;
+}
+
+BoundaryLayout boundary_layout(const tt_iga_bc_desc *bc, const int nfull[3]) {
+  BoundaryLayout bl;
+  for (int d = 0; d < 3; ++d) bl.nfull[d] = nfull[d];
+  if (!bc) return bl;
+  bool any = false;
+  int dir = -1;
+  for (int d = 0; d < 3; ++d) {
+    bl.lo[d] = bc->dirichlet[2 * d] ? 1 : 0;
+    bl.hi[d] = bc->dirichlet[2 * d + 1] ? 1 : 0;
+    any = any || bl.lo[d] || bl.hi[d];
+    for (int side = 0; side < 2; ++side) {
+      TTI_CHECK_ARG(std::isfinite(bc->value[2 * d + side]), "bc: value of face %d is not finite", 2 * d + side);
+      if (bc->dirichlet[2 * d + side] && bc->value[2 * d + side] != 0.0) {
+        TTI_CHECK_ARG(dir < 0 || dir == d, "bc: nonzero Dirichlet data on more than one direction");
+        dir = d;
+      }
+    }
+  }
+  TTI_CHECK_ARG(any, "bc: no Dirichlet face (the operator would be singular)");
+  if (dir >= 0) {
+    for (int e = 0; e < 3; ++e)
+      TTI_CHECK_ARG(e == dir || (!bl.lo[e] && !bl.hi[e]),
+                    "bc: nonzero data on direction %d needs natural faces in direction %d", dir, e);
+    bl.lift_dir = dir;
+    bl.lift_lo = bc->dirichlet[2 * dir] ? bc->value[2 * dir] : 0.0;
+    bl.lift_hi = bc->dirichlet[2 * dir + 1] ? bc->value[2 * dir + 1] : 0.0;
+  }
+  for (int d = 0; d < 3; ++d)
+    TTI_CHECK_ARG(nfull[d] - bl.lo[d] - bl.hi[d] >= 1, "bc: no unknowns left in direction %d", d);
+  return bl;
+}
+
 // The operator (sum of the K_ab terms, rounded after every addition) and each
 // load vector are independent and are built concurrently on helper contexts.
 void assemble_system(Ctx *c, const tt_iga_geom *g, const tt_iga_rhs_desc *rhs, int n_rhs, double round_tol,
-                     tt_iga_system *out) {
+                     const BoundaryLayout &bl, tt_iga_system *out) {
   const int p = g->desc.p;
   const int b = 2 * p + 1;
   int n[3];
   for (int d = 0; d < 3; ++d) n[d] = g->s[d].n;
-  TT3 K;
+  const bool lift = bl.lift_dir >= 0;
+  TT3 K, Kfull;  // Kfull: the operator before restriction, kept for F - K g
   std::vector<TT3> F(n_rhs);
   std::vector<double> F_norm(n_rhs, 0.0);
 
@@ -174,7 +219,11 @@ void assemble_system(Ctx *c, const tt_iga_geom *g, const tt_iga_rhs_desc *rhs, i
       terms = std::move(next);  // the consumed terms are freed on h, after the helpers (ordered by the join)
     }
     K = std::move(terms[0]);
-    restrict_tt(h, K, n, p, true);
+    if (lift) {
+      Kfull = clone_tt(h, K);
+      for (int d = 0; d < 3; ++d) Kfull.core[d].rehome(c);
+    }
+    restrict_tt(h, K, bl, p, true);
     tt_round(h, K, round_tol, 0);
     for (int d = 0; d < 3; ++d) K.core[d].rehome(c);
   };
@@ -196,8 +245,10 @@ void assemble_system(Ctx *c, const tt_iga_geom *g, const tt_iga_rhs_desc *rhs, i
         load_core(h, n[d], p, g->s[d].nq, g->s[d].wts.d(), g->s[d].N.d(), fj.tt.core[d].d(), fj.tt.r[d],
                   fj.tt.r[d + 1], Fk.core[d].d());
     }
-    restrict_tt(h, Fk, n, p, false);
-    F_norm[k] = tt_round(h, Fk, round_tol, 0);
+    if (!lift) {
+      restrict_tt(h, Fk, bl, p, false);
+      F_norm[k] = tt_round(h, Fk, round_tol, 0);
+    }
     for (int d = 0; d < 3; ++d) Fk.core[d].rehome(c);
   };
 
@@ -206,10 +257,44 @@ void assemble_system(Ctx *c, const tt_iga_geom *g, const tt_iga_rhs_desc *rhs, i
     else build_load(task - 1, h);
   });
 
+  if (lift) {
+    // g = (lift_lo e_0 + lift_hi e_{n-1}) in direction lift_dir, ones in the others (rank 1);
+    // K g by band TT-matrix times TT vector, then F_k <- F_k - K g, restricted and rounded
+    TT3 G;
+    for (int d = 0; d < 3; ++d) G.m[d] = n[d];
+    G.r[1] = G.r[2] = 1;
+    G.alloc(c);
+    for (int d = 0; d < 3; ++d) {
+      std::vector<double> v(n[d], d == bl.lift_dir ? 0.0 : 1.0);
+      if (d == bl.lift_dir) {
+        v[0] = bl.lift_lo;
+        v[n[d] - 1] = bl.lift_hi;
+      }
+      c->h2d(G.core[d].get(), v.data(), v.size() * sizeof(double));
+    }
+    TT3 Kg;
+    for (int d = 0; d < 3; ++d) Kg.m[d] = n[d];
+    for (int k = 0; k < 4; ++k) Kg.r[k] = Kfull.r[k];
+    Kg.alloc(c);
+    for (int d = 0; d < 3; ++d) {
+      BandCore A{Kfull.core[d].d(), nullptr, Kfull.r[d], n[d], b, p, Kfull.r[d + 1]};
+      tt_matvec_core(c, A, G.core[d].d(), 1, 1, Kg.core[d].d());
+    }
+    c->sync();  // the host vectors above are released at scope end
+    for (int k = 0; k < n_rhs; ++k) {
+      TT3 S;
+      tt_sum(c, F[k], 1.0, Kg, -1.0, S);
+      restrict_tt(c, S, bl, p, false);
+      F_norm[k] = tt_round(c, S, round_tol, 0);
+      F[k] = std::move(S);
+    }
+  }
+
   out->ctx = c;
   out->p = p;
   out->b = b;
-  for (int d = 0; d < 3; ++d) out->n[d] = n[d] - 2;
+  out->bl = bl;
+  for (int d = 0; d < 3; ++d) out->n[d] = n[d] - bl.lo[d] - bl.hi[d];
   out->K = std::move(K);
   out->F.clear();
   out->F_norm.clear();

@@ -261,16 +261,26 @@ int tt_iga_geom_ranks(const tt_iga_geom *g, int ranks[6][2], double max_rel_err[
 
 int tt_iga_assemble(tt_iga_ctx *c, const tt_iga_geom *g, const tt_iga_rhs_desc *rhs, int n_rhs, double round_tol,
                     tt_iga_system **out) {
+  return tt_iga_assemble_bc(c, g, rhs, n_rhs, round_tol, nullptr, out);
+}
+
+int tt_iga_assemble_bc(tt_iga_ctx *c, const tt_iga_geom *g, const tt_iga_rhs_desc *rhs, int n_rhs,
+                       double round_tol, const tt_iga_bc_desc *bc, tt_iga_system **out) {
   if (!c || !g || !out || (n_rhs > 0 && !rhs) || n_rhs < 1) return TT_IGA_ERR_ARG;
   *out = nullptr;
   API_TRY
   if (g->ctx != c) fail(TT_IGA_ERR_STATE, "assemble: geometry belongs to another context");
-  for (int k = 0; k < n_rhs; ++k)
+  for (int k = 0; k < n_rhs; ++k) {
     TTI_CHECK_ARG(rhs[k].n_modes >= 0 && rhs[k].n_modes <= TT_IGA_MAX_MODES, "assemble: n_modes out of range");
+    TTI_CHECK_ARG(rhs[k].kind >= TT_IGA_RHS_MANUFACTURED && rhs[k].kind <= TT_IGA_RHS_RING_LOG,
+                  "assemble: unknown right-hand side kind %d", rhs[k].kind);
+  }
   if (round_tol <= 0) round_tol = 1e-12;
+  const int nfull[3] = {g->s[0].n, g->s[1].n, g->s[2].n};
+  const BoundaryLayout bl = boundary_layout(bc, nfull);
   auto *S = new tt_iga_system();
   std::unique_ptr<tt_iga_system> guard(S);
-  assemble_system(c, g, rhs, n_rhs, round_tol, S);
+  assemble_system(c, g, rhs, n_rhs, round_tol, bl, S);
   const int st = device_status(c);
   *out = guard.release();
   if (st != TT_IGA_OK) {
@@ -317,6 +327,7 @@ int tt_iga_solve(tt_iga_ctx *c, const tt_iga_system *s, const tt_iga_solve_opts 
                 "solve: precision %d not available (FP64 and MIXED_FP32 are built)", o.precision);
   TTI_CHECK_ARG(o.rhs_index >= 0 && o.rhs_index < (int)s->F.size(), "solve: rhs_index %d out of range", o.rhs_index);
   auto *U = new tt_iga_solution();
+  U->bl = s->bl;
   std::unique_ptr<tt_iga_solution> guard(U);
   int status = amen_solve(c, s, o, U, st);
   const int ds = device_status(c);
@@ -386,7 +397,12 @@ int tt_iga_l2_error(tt_iga_ctx *c, const tt_iga_geom *g, const tt_iga_solution *
                     double *rel) {
   if (!c || !g || !u || !rhs || !rel) return TT_IGA_ERR_ARG;
   API_TRY
-  TTI_CHECK_ARG(rhs->kind == TT_IGA_RHS_MANUFACTURED, "l2_error: needs a manufactured right-hand side");
+  TTI_CHECK_ARG(rhs->kind == TT_IGA_RHS_MANUFACTURED || rhs->kind == TT_IGA_RHS_RING_LOG,
+                "l2_error: needs a right-hand side with an exact solution (MANUFACTURED or RING_LOG)");
+  if (rhs->kind == TT_IGA_RHS_RING_LOG)
+    TTI_CHECK_ARG(g->desc.kind == TT_IGA_GEOM_ANNULUS && g->desc.twist == 0.0 && g->desc.swell == 0.0 &&
+                      u->bl.lift_dir == 0,
+                  "l2_error: the ring solution needs the annulus without twist and swell and radial Dirichlet data");
   *rel = l2_error(c, g, u, rhs);
   return TT_IGA_OK;
   API_CATCH(c)

@@ -1,6 +1,7 @@
-// Evaluation of the TT solution u_h(xi) = sum_a u_a N_a(xi) and the relative
-// L2 error of Eq. (L2norm), read as sqrt(int (u_h - u)^2) / sqrt(int u^2) over
-// the mapped domain with p+3 Gauss points per element and direction.
+// Evaluation of the TT solution u_h(xi) = sum_a u_a N_a(xi) (plus the lift of
+// the Dirichlet data, Section 4.3) and the relative L2 error of Eq. (L2norm),
+// read as sqrt(int (u_h - u)^2) / sqrt(int u^2) over the mapped domain with p+3
+// Gauss points per element and direction.
 #include <algorithm>
 
 #include "eval.cuh"
@@ -9,12 +10,33 @@
 
 namespace ttiga {
 
-// u_h at parametric points: the p+1 nonzero functions per direction, interior
-// functions 1..n-2 map to restricted TT index a-1.
+// Where the unknowns sit among the basis functions and the lift of the Dirichlet data.
+struct EvalLayout {
+  int nfull[3], lo[3], m[3];
+  int lift_dir;
+  double lift_lo, lift_hi;
+};
+
+static EvalLayout eval_layout(const tt_iga_solution *u) {
+  EvalLayout L;
+  for (int d = 0; d < 3; ++d) {
+    L.nfull[d] = u->bl.nfull[d];
+    L.lo[d] = u->bl.lo[d];
+    L.m[d] = u->n[d];
+  }
+  L.lift_dir = u->bl.lift_dir;
+  L.lift_lo = u->bl.lift_lo;
+  L.lift_hi = u->bl.lift_hi;
+  return L;
+}
+
+// u_h at parametric points: the p+1 nonzero functions per direction; function a
+// of direction d is restricted TT index a - lo_d when it is an unknown; the lift
+// lift_lo N_0 + lift_hi N_{n-1} of the lift direction is added.
 __global__ void k_eval_points(const double *__restrict__ U1, const double *__restrict__ U2,
-                              const double *__restrict__ U3, int n1, int n2, int n3, int p, int r1, int r2, int m,
+                              const double *__restrict__ U3, EvalLayout L, int p, int r1, int r2, int m,
                               const double *__restrict__ xi, double *__restrict__ out) {
-  const int nf[3] = {n1, n2, n3};
+  const int *nf = L.nfull;
   for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < m; t += gridDim.x * blockDim.x) {
     double Nv[3][9], Dv[9];
     int e[3];
@@ -27,12 +49,12 @@ __global__ void k_eval_points(const double *__restrict__ U1, const double *__res
       e[d] = el;
       local_basis(x, el + p, nf[d], p, Nv[d], Dv);
     }
-    const int m1 = n1 - 2, m2 = n2 - 2, m3 = n3 - 2;
+    const int m1 = L.m[0], m2 = L.m[1], m3 = L.m[2];
     double v = 0.0;
     for (int a = 0; a < r1; ++a) {
       double v1 = 0.0;
       for (int k = 0; k <= p; ++k) {
-        const int g = e[0] + k - 1;
+        const int g = e[0] + k - L.lo[0];
         if (g >= 0 && g < m1) v1 += Nv[0][k] * U1[(long long)g * r1 + a];
       }
       if (v1 == 0.0) continue;
@@ -40,13 +62,18 @@ __global__ void k_eval_points(const double *__restrict__ U1, const double *__res
       for (int b = 0; b < r2; ++b) {
         double v2 = 0.0, v3 = 0.0;
         for (int k = 0; k <= p; ++k) {
-          const int g2 = e[1] + k - 1, g3 = e[2] + k - 1;
+          const int g2 = e[1] + k - L.lo[1], g3 = e[2] + k - L.lo[2];
           if (g2 >= 0 && g2 < m2) v2 += Nv[1][k] * U2[((long long)a * m2 + g2) * r2 + b];
           if (g3 >= 0 && g3 < m3) v3 += Nv[2][k] * U3[(long long)b * m3 + g3];
         }
         s += v2 * v3;
       }
       v += v1 * s;
+    }
+    if (L.lift_dir >= 0) {
+      const int d = L.lift_dir, ne = nf[d] - p;
+      if (e[d] == 0) v += L.lift_lo * Nv[d][0];
+      if (e[d] == ne - 1) v += L.lift_hi * Nv[d][p];
     }
     out[t] = v;
   }
@@ -55,16 +82,14 @@ __global__ void k_eval_points(const double *__restrict__ U1, const double *__res
 void eval_points(Ctx *c, const tt_iga_solution *u, int m, const double *xi, double *out) {
   if (m <= 0) return;
   k_eval_points<<<grid1d(m, 128), 128, 0, c->stream>>>(u->u.core[0].d(), u->u.core[1].d(), u->u.core[2].d(),
-                                                       u->n[0] + 2, u->n[1] + 2, u->n[2] + 2, u->p, u->u.r[1],
-                                                       u->u.r[2], m, xi, out);
+                                                       eval_layout(u), u->p, u->u.r[1], u->u.r[2], m, xi, out);
   TTI_LAUNCH();
 }
 
-// T[q][a][b] = sum_k N[q][k] U[a][e(q)+k-1][b] over interior functions (restricted core U[ra][n-2][rb]).
-__global__ void k_core_table(const double *__restrict__ N, int Q, int nq, int n, int p, const double *__restrict__ U,
-                             int ra, int rb, double *__restrict__ T) {
+// T[q][a][b] = sum_k N[q][k] U[a][e(q)+k-lo][b] over the unknown functions (restricted core U[ra][m][rb]).
+__global__ void k_core_table(const double *__restrict__ N, int Q, int nq, int lo, int m, int p,
+                             const double *__restrict__ U, int ra, int rb, double *__restrict__ T) {
   const long long tot = (long long)Q * ra * rb;
-  const int m = n - 2;
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < tot; e += (long long)gridDim.x * blockDim.x) {
     const int b = (int)(e % rb);
     const long long t = e / rb;
@@ -73,10 +98,22 @@ __global__ void k_core_table(const double *__restrict__ N, int Q, int nq, int n,
     const int el = q / nq;
     double s = 0.0;
     for (int k = 0; k <= p; ++k) {
-      const int g = el + k - 1;
+      const int g = el + k - lo;
       if (g >= 0 && g < m) s += N[(long long)q * (p + 1) + k] * U[((long long)a * m + g) * rb + b];
     }
     T[e] = s;
+  }
+}
+
+// Lift at the points of the lift direction: lift_lo N_0 (first element) + lift_hi N_{n-1} (last element).
+__global__ void k_lift_table(const double *__restrict__ N, int Q, int nq, int ne, int p, double lift_lo,
+                             double lift_hi, double *__restrict__ out) {
+  for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < Q; q += gridDim.x * blockDim.x) {
+    const int el = q / nq;
+    double v = 0.0;
+    if (el == 0) v += lift_lo * N[(long long)q * (p + 1)];
+    if (el == ne - 1) v += lift_hi * N[(long long)q * (p + 1) + p];
+    out[q] = v;
   }
 }
 
@@ -84,7 +121,8 @@ __global__ void k_l2_accumulate(GeomParams g, RhsParams f, const double *__restr
                                 const double *__restrict__ x3, const double *__restrict__ w1,
                                 const double *__restrict__ w2, const double *__restrict__ w3, int Q1, int Q2, int Q3,
                                 const double *__restrict__ T1, const double *__restrict__ T2,
-                                const double *__restrict__ T3, int r1, int r2, double *part) {
+                                const double *__restrict__ T3, int r1, int r2, int lift_dir,
+                                const double *__restrict__ liftq, double u_in, double u_out, double *part) {
   __shared__ double red[2][32];
   double num = 0.0, den = 0.0;
   const long long tot = (long long)Q1 * Q2 * Q3;
@@ -99,12 +137,16 @@ __global__ void k_l2_accumulate(GeomParams g, RhsParams f, const double *__restr
       for (int b = 0; b < r2; ++b) s += T2[((long long)q2 * r1 + a) * r2 + b] * T3[(long long)q3 * r2 + b];
       uh += t1 * s;
     }
+    if (lift_dir >= 0) uh += liftq[lift_dir == 0 ? q1 : (lift_dir == 1 ? q2 : q3)];
     double X[3], J[3][3];
     map_point(g, x1[q1], x2[q2], x3[q3], X, J);
     const double det = J[0][0] * (J[1][1] * J[2][2] - J[1][2] * J[2][1]) -
                        J[0][1] * (J[1][0] * J[2][2] - J[1][2] * J[2][0]) +
                        J[0][2] * (J[1][0] * J[2][1] - J[1][1] * J[2][0]);
-    const double ue = manufactured_value(g, f, X[0], X[1], X[2]);
+    // RING_LOG: the log solution of the ring problem (annulus without twist and swell)
+    const double ue = (f.kind == TT_IGA_RHS_RING_LOG)
+                          ? u_in + (u_out - u_in) * log(sqrt(X[0] * X[0] + X[1] * X[1]) / g.r_in) / log(g.r_out / g.r_in)
+                          : manufactured_value(g, f, X[0], X[1], X[2]);
     const double w = w1[q1] * w2[q2] * w3[q3] * det;
     num += w * (uh - ue) * (uh - ue);
     den += w * ue * ue;
@@ -131,12 +173,20 @@ double l2_error(Ctx *c, const tt_iga_geom *g, const tt_iga_solution *u, const tt
   Space fine[3];
   DBuf T[3];
   for (int d = 0; d < 3; ++d) {
-    build_space(c, fine[d], u->n[d] + 2, p, std::min(p + 3, 8));
+    build_space(c, fine[d], u->bl.nfull[d], p, std::min(p + 3, 8));
     const int ra = u->u.r[d], rb = u->u.r[d + 1];
     T[d] = DBuf(c, (size_t)fine[d].Q * ra * rb * sizeof(double));
     const long long tot = (long long)fine[d].Q * ra * rb;
-    k_core_table<<<grid1d(tot, 256), 256, 0, c->stream>>>(fine[d].N.d(), fine[d].Q, fine[d].nq, u->n[d] + 2, p,
-                                                          u->u.core[d].d(), ra, rb, T[d].d());
+    k_core_table<<<grid1d(tot, 256), 256, 0, c->stream>>>(fine[d].N.d(), fine[d].Q, fine[d].nq, u->bl.lo[d], u->n[d],
+                                                          p, u->u.core[d].d(), ra, rb, T[d].d());
+    TTI_LAUNCH();
+  }
+  const int ld = u->bl.lift_dir;
+  DBuf liftq(c, ld >= 0 ? (size_t)fine[ld].Q * sizeof(double) : 16);
+  if (ld >= 0) {
+    k_lift_table<<<grid1d(fine[ld].Q, 128), 128, 0, c->stream>>>(fine[ld].N.d(), fine[ld].Q, fine[ld].nq,
+                                                                 fine[ld].ne, p, u->bl.lift_lo, u->bl.lift_hi,
+                                                                 liftq.d());
     TTI_LAUNCH();
   }
   RhsParams rp = rhs_params(rhs);
@@ -144,7 +194,8 @@ double l2_error(Ctx *c, const tt_iga_geom *g, const tt_iga_solution *u, const tt
   DBuf part(c, 2 * nb * sizeof(double));
   k_l2_accumulate<<<nb, 256, 0, c->stream>>>(g->gp, rp, fine[0].pts.d(), fine[1].pts.d(), fine[2].pts.d(),
                                              fine[0].wts.d(), fine[1].wts.d(), fine[2].wts.d(), fine[0].Q, fine[1].Q,
-                                             fine[2].Q, T[0].d(), T[1].d(), T[2].d(), u->u.r[1], u->u.r[2], part.d());
+                                             fine[2].Q, T[0].d(), T[1].d(), T[2].d(), u->u.r[1], u->u.r[2], ld,
+                                             liftq.d(), u->bl.lift_lo, u->bl.lift_hi, part.d());
   TTI_LAUNCH();
   std::vector<double> h(2 * nb);
   c->d2h(h.data(), part.d(), h.size() * sizeof(double));

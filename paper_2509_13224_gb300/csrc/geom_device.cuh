@@ -166,7 +166,7 @@ __device__ inline double manufactured_value(const GeomParams &g, const RhsParams
 
 __device__ inline double source_term(const GeomParams &g, const RhsParams &f, double x, double y, double z) {
   if (!f.has) return 0.0;
-  if (f.kind == TT_IGA_RHS_CONSTANT) return f.value;
+  if (f.kind == TT_IGA_RHS_CONSTANT || f.kind == TT_IGA_RHS_RING_LOG) return f.value;
   double lap = 0.0;
   const double X[3] = {x, y, z};
   for (int k = 0; k < 3; ++k) {

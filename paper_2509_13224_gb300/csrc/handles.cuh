@@ -14,12 +14,24 @@ struct tt_iga_geom {
   double ms_cross = 0.0;
 };
 
-// Restricted TT system: band-stored operator with mode sizes (n_d - 2)(2p+1)
-// and one TT load vector per right-hand side with mode sizes n_d - 2.
+namespace ttiga {
+// Which basis functions are unknowns and the lift of the Dirichlet data:
+// direction d keeps functions lo[d] .. nfull[d] - 1 - hi[d]; the lift is
+// lift_lo N_0(xi_dir) + lift_hi N_{n-1}(xi_dir) (dir = -1: no lift).
+struct BoundaryLayout {
+  int lo[3] = {1, 1, 1}, hi[3] = {1, 1, 1}, nfull[3] = {0, 0, 0};
+  int lift_dir = -1;
+  double lift_lo = 0.0, lift_hi = 0.0;
+};
+}  // namespace ttiga
+
+// Restricted TT system: band-stored operator with mode sizes n_d(2p+1) and one
+// TT load vector per right-hand side with mode sizes n_d (the unknowns).
 struct tt_iga_system {
   ttiga::Ctx *ctx = nullptr;
-  int n[3] = {0, 0, 0};   // restricted sizes n_d - 2
+  int n[3] = {0, 0, 0};   // restricted sizes nfull_d - lo_d - hi_d
   int p = 0, b = 0;       // degree and band width 2p + 1
+  ttiga::BoundaryLayout bl;
   ttiga::TT3 K;
   std::vector<ttiga::TT3> F;
   std::vector<double> F_norm;
@@ -29,6 +41,7 @@ struct tt_iga_solution {
   ttiga::Ctx *ctx = nullptr;
   int n[3] = {0, 0, 0};   // restricted sizes
   int p = 0;
+  ttiga::BoundaryLayout bl;
   ttiga::TT3 u;
 };
 
@@ -45,8 +58,11 @@ void stiffness_core(Ctx *c, int n, int p, int nq, const double *wts, const doubl
                     const double *G, int r0, int r1, int test_deriv, int trial_deriv, double *M);
 void load_core(Ctx *c, int n, int p, int nq, const double *wts, const double *N, const double *G, int r0, int r1,
                double *F);
+// Boundary layout of bc (nullptr: six homogeneous Dirichlet faces); fails with
+// TT_IGA_ERR_ARG on the cases tt_iga_assemble_bc rejects.
+BoundaryLayout boundary_layout(const tt_iga_bc_desc *bc, const int nfull[3]);
 void assemble_system(Ctx *c, const tt_iga_geom *g, const tt_iga_rhs_desc *rhs, int n_rhs, double round_tol,
-                     tt_iga_system *out);
+                     const BoundaryLayout &bl, tt_iga_system *out);
 // Dense restricted operator entries for (row, col) multi-index pairs (device arrays).
 void operator_entries(Ctx *c, const tt_iga_system *s, int m, const int *rows, const int *cols, double *out);
 
