@@ -116,3 +116,55 @@ def coefficient_tensor(J):
     Jinv = np.linalg.inv(J)
     R = np.einsum("...ab,...cb->...ac", Jinv, Jinv) * detJ[..., None, None]
     return detJ, R
+
+
+class NURBSPatch:
+    """Single-patch trivariate NURBS volume (Section 2.2, the NURBS map of Eq. for x(xi)):
+
+        X(xi) = sum_a w_a P_a N_a(xi) / sum_a w_a N_a(xi),  N_a = N_a1(xi1) N_a2(xi2) N_a3(xi3),
+
+    degrees deg[d], open knot vectors knots[d] on [0, 1], control points ctrl[c1, c2, c3, 3] and
+    positive weights w[c1, c2, c3].  The Jacobian follows from the quotient rule with the
+    B-spline derivatives of spline.bspline_basis."""
+
+    def __init__(self, degrees, knots, ctrl, weights):
+        self.deg = [int(q) for q in degrees]
+        self.knots = [np.asarray(k, dtype=np.float64) for k in knots]
+        self.ctrl = np.asarray(ctrl, dtype=np.float64)
+        self.w = np.asarray(weights, dtype=np.float64)
+        for d in range(3):
+            assert len(self.knots[d]) == self.ctrl.shape[d] + self.deg[d] + 1
+
+    def map(self, xi1, xi2, xi3):
+        from .spline import bspline_basis
+        (N1, D1), (N2, D2), (N3, D3) = (bspline_basis(self.knots[d], self.deg[d], x)
+                                        for d, x in enumerate((xi1, xi2, xi3)))
+        wP = self.w[..., None] * self.ctrl
+        W = np.einsum("ia,jb,kc,abc->ijk", N1, N2, N3, self.w, optimize=True)
+        A = np.einsum("ia,jb,kc,abcd->ijkd", N1, N2, N3, wP, optimize=True)
+        dW = [np.einsum("ia,jb,kc,abc->ijk", *B, self.w, optimize=True)
+              for B in ((D1, N2, N3), (N1, D2, N3), (N1, N2, D3))]
+        dA = [np.einsum("ia,jb,kc,abcd->ijkd", *B, wP, optimize=True)
+              for B in ((D1, N2, N3), (N1, D2, N3), (N1, N2, D3))]
+        X = A / W[..., None]
+        J = np.empty(X.shape + (3,))
+        for b in range(3):
+            J[..., :, b] = (dA[b] - X * dW[b][..., None]) / W[..., None]
+        return X, J
+
+
+def quarter_cylinder_patch(r_in=1.0, r_out=2.0, height=1.0):
+    """The quarter cylinder of Annulus (no twist, no swell) as a NURBS patch: radial degree 1,
+    angular rational quadratic quarter circle (control (1,0), (1,1), (0,1), weights 1, sqrt(2)/2, 1),
+    axial degree 1."""
+    arc = np.array([[1.0, 0.0], [1.0, 1.0], [0.0, 1.0]])
+    warc = np.array([1.0, np.sqrt(0.5), 1.0])
+    ctrl = np.zeros((2, 3, 2, 3))
+    w = np.zeros((2, 3, 2))
+    for i, r in enumerate((r_in, r_out)):
+        for j in range(3):
+            for k, z in enumerate((0.0, height)):
+                ctrl[i, j, k] = [r * arc[j, 0], r * arc[j, 1], z]
+                w[i, j, k] = warc[j]
+    knots = [[0, 0, 1, 1], [0, 0, 0, 1, 1, 1], [0, 0, 1, 1]]
+    return NURBSPatch((1, 2, 1), knots, ctrl, w)
