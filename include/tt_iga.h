@@ -106,7 +106,7 @@ int tt_iga_fma_peaks(tt_iga_ctx *ctx, double *fp64_tflops, double *fp32_tflops);
 
 /* --------------------------------------------------------------- geometry */
 
-enum { TT_IGA_GEOM_BOX = 0, TT_IGA_GEOM_ANNULUS = 1 };
+enum { TT_IGA_GEOM_BOX = 0, TT_IGA_GEOM_ANNULUS = 1, TT_IGA_GEOM_NURBS = 2 };
 
 /* Geometry and discretisation (Section 3.3, Section 2).
  *  ANNULUS: quarter annulus of radii r_in < r_out and height `height`: radial
@@ -136,6 +136,34 @@ typedef struct {
  * sampled det J <= 0; ERR_NOT_CONVERGED if the cross did not validate within
  * max_rank (the handle is still returned). */
 int tt_iga_geometry(tt_iga_ctx *ctx, const tt_iga_geom_desc *g, tt_iga_geom **out);
+
+#define TT_IGA_NURBS_MAX_DEGREE 4
+#define TT_IGA_NURBS_MAX_CP 64
+
+/* A single-patch trivariate NURBS volume (Section 2.2):
+ *   x(xi) = sum_a w_a P_a N_a(xi) / sum_a w_a N_a(xi),  N_a = N_a1(xi_1) N_a2(xi_2) N_a3(xi_3),
+ * with degree deg[d] (1 .. TT_IGA_NURBS_MAX_DEGREE) and ncp[d] control points
+ * (deg[d] + 1 .. TT_IGA_NURBS_MAX_CP) per direction, open knot vectors knots[d]
+ * of ncp[d] + deg[d] + 1 nondecreasing values starting with deg[d] + 1 zeros and
+ * ending with deg[d] + 1 ones, control points ctrl[(i3 ncp[1] + i2) ncp[0] + i1][3]
+ * and positive weights weights[(i3 ncp[1] + i2) ncp[0] + i1] (xi_1 fastest).
+ * Host pointers, read during tt_iga_geometry_nurbs only.  The solution space is
+ * the one of tt_iga_geom_desc (degree p, n[d] functions on open uniform knots),
+ * independent of the patch's own knots: the patch is the exact geometry. */
+typedef struct {
+  int deg[3];
+  int ncp[3];
+  const double *knots[3];
+  const double *ctrl;
+  const double *weights;
+} tt_iga_nurbs_patch;
+
+/* tt_iga_geometry for a NURBS patch: g supplies the discretisation (p, n, nq,
+ * cross_tol, max_rank, seed) and g->kind must be TT_IGA_GEOM_NURBS.  Systems on
+ * this geometry take CONSTANT right-hand sides (the manufactured solutions are
+ * defined for the annulus and the box).  ERR_ARG on a malformed patch. */
+int tt_iga_geometry_nurbs(tt_iga_ctx *ctx, const tt_iga_geom_desc *g, const tt_iga_nurbs_patch *patch,
+                          tt_iga_geom **out);
 void tt_iga_geom_destroy(tt_iga_geom *g);
 /* TT ranks (r1, r2) of field f = 0..5 in the order R11, R12, R13, R22, R23, R33
  * (rank 0 marks a field that is zero to the cross tolerance), plus the

@@ -19,7 +19,7 @@ _lib = ctypes.CDLL(LIB_PATH)
 
 OK, ERR_ARG, ERR_OOM, ERR_CUDA, ERR_NOT_CONVERGED, ERR_TIMEOUT, ERR_TOO_LARGE, ERR_BAD_GEOMETRY, ERR_STATE = (
     0, -1, -2, -3, -4, -5, -6, -7, -8)
-GEOM_BOX, GEOM_ANNULUS = 0, 1
+GEOM_BOX, GEOM_ANNULUS, GEOM_NURBS = 0, 1, 2
 RHS_MANUFACTURED, RHS_CONSTANT, RHS_RING_LOG = 0, 1, 2
 FP64, MIXED_FP32, MIXED_TF32 = 0, 1, 2
 MAX_MODES = 8
@@ -49,6 +49,11 @@ class GeomDesc(ctypes.Structure):
 
 class BcDesc(ctypes.Structure):
     _fields_ = [("dirichlet", ctypes.c_int * 6), ("value", ctypes.c_double * 6)]
+
+
+class NurbsPatch(ctypes.Structure):
+    _fields_ = [("deg", ctypes.c_int * 3), ("ncp", ctypes.c_int * 3), ("knots", _c_double_p * 3),
+                ("ctrl", _c_double_p), ("weights", _c_double_p)]
 
 
 class RhsDesc(ctypes.Structure):
@@ -105,6 +110,8 @@ _SIGS = {
     "tt_iga_geometry": (ctypes.c_int, [_vp, ctypes.POINTER(GeomDesc), ctypes.POINTER(_vp)]),
     "tt_iga_geom_destroy": (None, [_vp]),
     "tt_iga_geom_ranks": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_int * 2 * 6), ctypes.POINTER(ctypes.c_double * 6)]),
+    "tt_iga_geometry_nurbs": (ctypes.c_int, [_vp, ctypes.POINTER(GeomDesc), ctypes.POINTER(NurbsPatch),
+                                             ctypes.POINTER(_vp)]),
     "tt_iga_assemble_bc": (ctypes.c_int, [_vp, _vp, ctypes.POINTER(RhsDesc), ctypes.c_int, ctypes.c_double,
                                           ctypes.POINTER(BcDesc), ctypes.POINTER(_vp)]),
     "tt_iga_assemble": (ctypes.c_int, [_vp, _vp, ctypes.POINTER(RhsDesc), ctypes.c_int, ctypes.c_double,
@@ -181,6 +188,8 @@ def geom_desc(geometry, p, n, cross_tol=1e-10, max_rank=0, seed=0, nq=0):
     elif geometry["kind"] == "box":
         d.kind = GEOM_BOX
         d.lx, d.ly, d.lz = geometry["lx"], geometry["ly"], geometry["lz"]
+    elif geometry["kind"] == "nurbs":
+        d.kind = GEOM_NURBS  # the patch itself goes to tt_iga_geometry_nurbs
     else:
         raise ValueError("unknown geometry kind")
     d.p = int(p)
@@ -298,6 +307,33 @@ def tt_iga_solution_cores(ctx, u, out=None):
         cores.append(out[off:off + sizes[k]].reshape(r[k], m[k], r[k + 1]))
         off += sizes[k]
     return cores
+
+
+def tt_iga_geometry_nurbs(ctx, desc, degrees, knots, ctrl, weights, allow_not_converged=False):
+    """Geometry on a NURBS patch: degrees (3), knots (3 arrays), ctrl [c1, c2, c3, 3] and
+    weights [c1, c2, c3] with the xi_1 index first (numpy layout); desc.kind must be GEOM_NURBS."""
+    import numpy as np
+    ctrl = np.asarray(ctrl, dtype=np.float64)
+    w = np.asarray(weights, dtype=np.float64)
+    c_fast = np.ascontiguousarray(ctrl.transpose(2, 1, 0, 3))  # xi_1 fastest, as the C ABI wants
+    w_fast = np.ascontiguousarray(w.transpose(2, 1, 0))
+    kn = [np.ascontiguousarray(k, dtype=np.float64) for k in knots]
+    patch = NurbsPatch()
+    for d in range(3):
+        patch.deg[d] = int(degrees[d])
+        patch.ncp[d] = int(ctrl.shape[d])
+        patch.knots[d] = kn[d].ctypes.data_as(_c_double_p)
+    patch.ctrl = c_fast.ctypes.data_as(_c_double_p)
+    patch.weights = w_fast.ctypes.data_as(_c_double_p)
+    h = ctypes.c_void_p()
+    allow = (ERR_NOT_CONVERGED,) if allow_not_converged else ()
+    code = _lib.tt_iga_geometry_nurbs(ctx, ctypes.byref(desc), ctypes.byref(patch), ctypes.byref(h))
+    if code != OK and h.value and code not in allow:
+        msg = tt_iga_last_error(ctx)
+        _lib.tt_iga_geom_destroy(h)
+        raise TTIgaError(code, msg)
+    _check(ctx, code, allow)
+    return h
 
 
 def tt_iga_geometry(ctx, desc, allow_not_converged=False):

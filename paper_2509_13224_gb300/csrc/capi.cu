@@ -168,29 +168,20 @@ int tt_iga_profile_read(tt_iga_ctx *c, double *ms_total, long long *launches, do
 
 // ------------------------------------------------------------------ geometry
 
-int tt_iga_geometry(tt_iga_ctx *c, const tt_iga_geom_desc *g, tt_iga_geom **out) {
-  if (!c || !g || !out) return TT_IGA_ERR_ARG;
-  *out = nullptr;
-  API_TRY
-  TTI_CHECK_ARG(g->kind == TT_IGA_GEOM_BOX || g->kind == TT_IGA_GEOM_ANNULUS, "geometry: unknown kind %d", g->kind);
+namespace {
+
+void check_discretisation(const tt_iga_geom_desc *g) {
   TTI_CHECK_ARG(g->p >= 1 && g->p <= 7, "geometry: degree p=%d outside 1..7", g->p);
   for (int d = 0; d < 3; ++d)
     TTI_CHECK_ARG(g->n[d] >= g->p + 2, "geometry: n[%d]=%d needs >= p+2", d, g->n[d]);
-  if (g->kind == TT_IGA_GEOM_ANNULUS)
-    TTI_CHECK_ARG(g->r_in > 0 && g->r_out > g->r_in && g->height > 0 && fabs(g->swell) < 1.0,
-                  "geometry: bad annulus parameters");
-  else
-    TTI_CHECK_ARG(g->lx > 0 && g->ly > 0 && g->lz > 0, "geometry: bad box lengths");
   const int nq = g->nq > 0 ? g->nq : g->p + 1;
   TTI_CHECK_ARG(nq <= 8, "geometry: nq=%d above 8", nq);
-  auto *G = new tt_iga_geom();
-  std::unique_ptr<tt_iga_geom> guard(G);
-  G->ctx = c;
-  G->desc = *g;
-  G->desc.nq = nq;
-  if (G->desc.cross_tol <= 0) G->desc.cross_tol = 1e-10;
-  if (G->desc.max_rank <= 0) G->desc.max_rank = 64;
-  G->gp = geom_params(G->desc);
+}
+
+// Tables of the three directions and the TT-cross of the six fields of R (shared by
+// the analytic maps and the NURBS patch); G->desc and G->gp are set by the caller.
+int build_geometry(tt_iga_ctx *c, tt_iga_geom *G, const tt_iga_geom_desc *g) {
+  const int nq = G->desc.nq;
   for (int d = 0; d < 3; ++d) build_space(c, G->s[d], g->n[d], g->p, nq);
   RhsParams none = rhs_params(nullptr);
   const int diag[3] = {0, 3, 5}, off[3] = {1, 2, 4};
@@ -230,7 +221,6 @@ int tt_iga_geometry(tt_iga_ctx *c, const tt_iga_geom_desc *g, tt_iga_geom **out)
   bool conv = true;
   for (int f = 0; f < 6; ++f) conv = conv && G->R[f].converged;
   const int st = device_status(c);
-  *out = guard.release();
   if (st == TT_IGA_ERR_BAD_GEOMETRY) {
     c->last_error = "geometry: det J <= 0 at a sampled quadrature point";
     return st;
@@ -240,6 +230,87 @@ int tt_iga_geometry(tt_iga_ctx *c, const tt_iga_geom_desc *g, tt_iga_geom **out)
     return TT_IGA_ERR_NOT_CONVERGED;
   }
   return TT_IGA_OK;
+}
+
+tt_iga_geom *new_geometry(tt_iga_ctx *c, const tt_iga_geom_desc *g) {
+  auto *G = new tt_iga_geom();
+  G->ctx = c;
+  G->desc = *g;
+  G->desc.nq = g->nq > 0 ? g->nq : g->p + 1;
+  if (G->desc.cross_tol <= 0) G->desc.cross_tol = 1e-10;
+  if (G->desc.max_rank <= 0) G->desc.max_rank = 64;
+  G->gp = geom_params(G->desc);
+  return G;
+}
+
+}  // namespace
+
+int tt_iga_geometry(tt_iga_ctx *c, const tt_iga_geom_desc *g, tt_iga_geom **out) {
+  if (!c || !g || !out) return TT_IGA_ERR_ARG;
+  *out = nullptr;
+  API_TRY
+  TTI_CHECK_ARG(g->kind == TT_IGA_GEOM_BOX || g->kind == TT_IGA_GEOM_ANNULUS,
+                "geometry: unknown kind %d (NURBS patches go through tt_iga_geometry_nurbs)", g->kind);
+  check_discretisation(g);
+  if (g->kind == TT_IGA_GEOM_ANNULUS)
+    TTI_CHECK_ARG(g->r_in > 0 && g->r_out > g->r_in && g->height > 0 && fabs(g->swell) < 1.0,
+                  "geometry: bad annulus parameters");
+  else
+    TTI_CHECK_ARG(g->lx > 0 && g->ly > 0 && g->lz > 0, "geometry: bad box lengths");
+  std::unique_ptr<tt_iga_geom> guard(new_geometry(c, g));
+  const int st = build_geometry(c, guard.get(), g);
+  *out = guard.release();
+  return st;
+  API_CATCH(c)
+}
+
+int tt_iga_geometry_nurbs(tt_iga_ctx *c, const tt_iga_geom_desc *g, const tt_iga_nurbs_patch *patch,
+                          tt_iga_geom **out) {
+  if (!c || !g || !patch || !out) return TT_IGA_ERR_ARG;
+  *out = nullptr;
+  API_TRY
+  TTI_CHECK_ARG(g->kind == TT_IGA_GEOM_NURBS, "geometry_nurbs: desc kind must be TT_IGA_GEOM_NURBS");
+  check_discretisation(g);
+  TTI_CHECK_ARG(patch->ctrl && patch->weights, "geometry_nurbs: null control points or weights");
+  std::vector<double> packed;
+  long long ncp = 1;
+  for (int d = 0; d < 3; ++d) {
+    const int q = patch->deg[d], m = patch->ncp[d];
+    TTI_CHECK_ARG(q >= 1 && q <= TT_IGA_NURBS_MAX_DEGREE, "geometry_nurbs: degree %d of direction %d", q, d);
+    TTI_CHECK_ARG(m >= q + 1 && m <= TT_IGA_NURBS_MAX_CP, "geometry_nurbs: %d control points in direction %d", m, d);
+    TTI_CHECK_ARG(patch->knots[d], "geometry_nurbs: null knot vector %d", d);
+    const double *t = patch->knots[d];
+    const int len = m + q + 1;
+    for (int k = 0; k < len; ++k) {
+      TTI_CHECK_ARG(std::isfinite(t[k]) && (k == 0 || t[k] >= t[k - 1]), "geometry_nurbs: knots %d not nondecreasing",
+                    d);
+      if (k <= q) TTI_CHECK_ARG(t[k] == 0.0, "geometry_nurbs: knots %d must start with %d zeros", d, q + 1);
+      if (k >= len - q - 1) TTI_CHECK_ARG(t[k] == 1.0, "geometry_nurbs: knots %d must end with %d ones", d, q + 1);
+      packed.push_back(t[k]);
+    }
+    ncp *= m;
+  }
+  for (long long i = 0; i < ncp; ++i) {
+    TTI_CHECK_ARG(patch->weights[i] > 0.0 && std::isfinite(patch->weights[i]), "geometry_nurbs: weight %lld", i);
+    packed.push_back(patch->weights[i]);
+  }
+  for (long long i = 0; i < 3 * ncp; ++i) {
+    TTI_CHECK_ARG(std::isfinite(patch->ctrl[i]), "geometry_nurbs: control point value %lld", i);
+    packed.push_back(patch->ctrl[i]);
+  }
+  std::unique_ptr<tt_iga_geom> guard(new_geometry(c, g));
+  tt_iga_geom *G = guard.get();
+  G->nurbs = DBuf(c, packed.size() * sizeof(double));
+  c->h2d(G->nurbs.get(), packed.data(), packed.size() * sizeof(double));
+  for (int d = 0; d < 3; ++d) {
+    G->gp.nd[d] = patch->deg[d];
+    G->gp.nc[d] = patch->ncp[d];
+  }
+  G->gp.nurbs = G->nurbs.d();
+  c->sync();  // the packed host copy is released at scope end
+  const int st = build_geometry(c, G, g);
+  *out = guard.release();
+  return st;
   API_CATCH(c)
 }
 
@@ -274,6 +345,8 @@ int tt_iga_assemble_bc(tt_iga_ctx *c, const tt_iga_geom *g, const tt_iga_rhs_des
     TTI_CHECK_ARG(rhs[k].n_modes >= 0 && rhs[k].n_modes <= TT_IGA_MAX_MODES, "assemble: n_modes out of range");
     TTI_CHECK_ARG(rhs[k].kind >= TT_IGA_RHS_MANUFACTURED && rhs[k].kind <= TT_IGA_RHS_RING_LOG,
                   "assemble: unknown right-hand side kind %d", rhs[k].kind);
+    TTI_CHECK_ARG(g->desc.kind != TT_IGA_GEOM_NURBS || rhs[k].kind == TT_IGA_RHS_CONSTANT,
+                  "assemble: a NURBS patch takes CONSTANT right-hand sides only");
   }
   if (round_tol <= 0) round_tol = 1e-12;
   const int nfull[3] = {g->s[0].n, g->s[1].n, g->s[2].n};
@@ -399,6 +472,7 @@ int tt_iga_l2_error(tt_iga_ctx *c, const tt_iga_geom *g, const tt_iga_solution *
   API_TRY
   TTI_CHECK_ARG(rhs->kind == TT_IGA_RHS_MANUFACTURED || rhs->kind == TT_IGA_RHS_RING_LOG,
                 "l2_error: needs a right-hand side with an exact solution (MANUFACTURED or RING_LOG)");
+  TTI_CHECK_ARG(g->desc.kind != TT_IGA_GEOM_NURBS, "l2_error: no exact solution is defined on a NURBS patch");
   if (rhs->kind == TT_IGA_RHS_RING_LOG)
     TTI_CHECK_ARG(g->desc.kind == TT_IGA_GEOM_ANNULUS && g->desc.twist == 0.0 && g->desc.swell == 0.0 &&
                       u->bl.lift_dir == 0,

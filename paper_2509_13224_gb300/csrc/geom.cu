@@ -20,7 +20,7 @@
 namespace ttiga {
 
 GeomParams geom_params(const tt_iga_geom_desc &g) {
-  GeomParams p;
+  GeomParams p{};
   p.kind = g.kind;
   p.r_in = g.r_in; p.r_out = g.r_out; p.height = g.height; p.twist = g.twist; p.swell = g.swell;
   p.lx = g.lx; p.ly = g.ly; p.lz = g.lz;

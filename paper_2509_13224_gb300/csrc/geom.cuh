@@ -15,6 +15,11 @@ struct GeomParams {
   int kind;
   double r_in, r_out, height, twist, swell;
   double lx, ly, lz;
+  // NURBS patch (kind TT_IGA_GEOM_NURBS): degrees, control points per direction and
+  // the packed device data: knots of directions 0, 1, 2, weights, control points
+  // (x, y, z interleaved), control-point index i1 fastest.
+  int nd[3], nc[3];
+  const double *nurbs;
 };
 
 struct RhsParams {

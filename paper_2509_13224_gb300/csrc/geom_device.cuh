@@ -178,7 +178,104 @@ __device__ inline double source_term(const GeomParams &g, const RhsParams &f, do
 }
 
 // Physical point and Jacobian J[a][b] = dx_a/dxi_b of the map at parametric xi.
+// Nonzero B-spline functions N_{s-q..s} of degree q on a general knot vector t
+// (span s: t[s] <= x < t[s+1], the last non-empty span for x = 1) and their first
+// derivatives, by the Cox-de Boor triangle of Section 2.1: the row of degree q-1
+// gives the derivatives, dN_i = q N_{i,q-1} / (t_{i+q} - t_i) - q N_{i+1,q-1} / (t_{i+q+1} - t_{i+1}).
+__device__ inline int nurbs_span(const double *t, int q, int nc, double x) {
+  if (x >= t[nc]) return nc - 1;
+  int lo = q, hi = nc;  // t[lo] <= x < t[hi]
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) / 2;
+    if (x < t[mid]) hi = mid; else lo = mid;
+  }
+  return lo;
+}
+
+__device__ inline void nurbs_basis_ders(const double *t, int q, int s, double x, double N[TT_IGA_NURBS_MAX_DEGREE + 1],
+                                        double D[TT_IGA_NURBS_MAX_DEGREE + 1]) {
+  double left[TT_IGA_NURBS_MAX_DEGREE + 1], right[TT_IGA_NURBS_MAX_DEGREE + 1];
+  double P[TT_IGA_NURBS_MAX_DEGREE + 1];  // degree j values on span s
+  P[0] = 1.0;
+  double Pm[TT_IGA_NURBS_MAX_DEGREE + 1];  // degree q-1 values
+  for (int j = 1; j <= q; ++j) {
+    if (j == q)
+      for (int r = 0; r < q; ++r) Pm[r] = P[r];
+    left[j] = x - t[s + 1 - j];
+    right[j] = t[s + j] - x;
+    double saved = 0.0;
+    for (int r = 0; r < j; ++r) {
+      const double den = right[r + 1] + left[j - r];
+      const double tmp = den != 0.0 ? P[r] / den : 0.0;
+      P[r] = saved + right[r + 1] * tmp;
+      saved = left[j - r] * tmp;
+    }
+    P[j] = saved;
+  }
+  for (int r = 0; r <= q; ++r) N[r] = P[r];
+  // derivative of function i = s - q + r from the degree q-1 functions i and i+1 (r-1 and r in Pm)
+  for (int r = 0; r <= q; ++r) {
+    const int i = s - q + r;
+    double d = 0.0;
+    if (r >= 1) {
+      const double den = t[i + q] - t[i];
+      if (den != 0.0) d += q * Pm[r - 1] / den;
+    }
+    if (r <= q - 1) {
+      const double den = t[i + q + 1] - t[i + 1];
+      if (den != 0.0) d -= q * Pm[r] / den;
+    }
+    D[r] = d;
+  }
+}
+
+// x(xi) of a NURBS patch and its Jacobian: X = A / W, dX/dxi_d = (dA_d - X dW_d) / W with
+// W = sum w N, A = sum w P N over the (q1+1)(q2+1)(q3+1) control points supporting xi.
+__device__ inline void nurbs_map(const GeomParams &g, double x1, double x2, double x3, double X[3], double J[3][3]) {
+  const double *t[3];
+  t[0] = g.nurbs;
+  t[1] = t[0] + g.nc[0] + g.nd[0] + 1;
+  t[2] = t[1] + g.nc[1] + g.nd[1] + 1;
+  const double *w = t[2] + g.nc[2] + g.nd[2] + 1;
+  const double *P = w + g.nc[0] * g.nc[1] * g.nc[2];
+  const double xs[3] = {fmin(fmax(x1, 0.0), 1.0), fmin(fmax(x2, 0.0), 1.0), fmin(fmax(x3, 0.0), 1.0)};
+  double N[3][TT_IGA_NURBS_MAX_DEGREE + 1], D[3][TT_IGA_NURBS_MAX_DEGREE + 1];
+  int s[3];
+  for (int d = 0; d < 3; ++d) {
+    s[d] = nurbs_span(t[d], g.nd[d], g.nc[d], xs[d]);
+    nurbs_basis_ders(t[d], g.nd[d], s[d], xs[d], N[d], D[d]);
+  }
+  double W = 0.0, dW[3] = {0.0, 0.0, 0.0}, A[3] = {0.0, 0.0, 0.0}, dA[3][3] = {};
+  for (int c = 0; c <= g.nd[2]; ++c) {
+    const int i3 = s[2] - g.nd[2] + c;
+    for (int b = 0; b <= g.nd[1]; ++b) {
+      const int i2 = s[1] - g.nd[1] + b;
+      for (int a = 0; a <= g.nd[0]; ++a) {
+        const int i1 = s[0] - g.nd[0] + a;
+        const long long idx = ((long long)i3 * g.nc[1] + i2) * g.nc[0] + i1;
+        const double wi = w[idx];
+        const double v = N[0][a] * N[1][b] * N[2][c];
+        const double dv[3] = {D[0][a] * N[1][b] * N[2][c], N[0][a] * D[1][b] * N[2][c], N[0][a] * N[1][b] * D[2][c]};
+        W += wi * v;
+        for (int e = 0; e < 3; ++e) {
+          const double pw = wi * P[3 * idx + e];
+          A[e] += pw * v;
+          for (int d = 0; d < 3; ++d) dA[e][d] += pw * dv[d];
+        }
+        for (int d = 0; d < 3; ++d) dW[d] += wi * dv[d];
+      }
+    }
+  }
+  for (int e = 0; e < 3; ++e) X[e] = A[e] / W;
+  for (int e = 0; e < 3; ++e)
+    for (int d = 0; d < 3; ++d) J[e][d] = (dA[e][d] - X[e] * dW[d]) / W;
+}
+
 __device__ inline void map_point(const GeomParams &g, double x1, double x2, double x3, double X[3], double J[3][3]) {
+  if (g.kind == TT_IGA_GEOM_NURBS) {
+    nurbs_map(g, x1, x2, x3, X, J);
+    return;
+  }
   if (g.kind == TT_IGA_GEOM_BOX) {
     X[0] = g.lx * x1; X[1] = g.ly * x2; X[2] = g.lz * x3;
     for (int a = 0; a < 3; ++a)

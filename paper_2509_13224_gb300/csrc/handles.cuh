@@ -12,6 +12,7 @@ struct tt_iga_geom {
   ttiga::Space s[3];
   ttiga::CrossResult R[6];
   double ms_cross = 0.0;
+  ttiga::DBuf nurbs;  // packed NURBS patch (kind TT_IGA_GEOM_NURBS), see GeomParams
 };
 
 namespace ttiga {

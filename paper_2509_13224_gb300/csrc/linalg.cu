@@ -697,6 +697,8 @@ __global__ void __launch_bounds__(1024) k_jacobi_svd(int k, const double *__rest
   for (int j = tid; j < k; j += blockDim.x) S[j] = nrm[perm[j]];
 }
 
+constexpr size_t kSvdSmemMax = 200 * 1024;  // W and V panels in shared memory up to this size
+
 // Lane group and CTA size for a k x k SVD: every pair of a round gets a group.
 static void svd_launch(cudaStream_t st, int k, const double *A, double *U, double *s, double *V, double *Wg,
                        double *Vg, int use_smem, size_t bytes, int *status) {
@@ -708,8 +710,11 @@ static void svd_launch(cudaStream_t st, int k, const double *A, double *U, doubl
     case 8: k_jacobi_svd<8><<<1, threads, bytes, st>>>(k, A, U, s, V, Wg, Vg, use_smem, status); break;
     case 16: k_jacobi_svd<16><<<1, threads, bytes, st>>>(k, A, U, s, V, Wg, Vg, use_smem, status); break;
     default:
-      if (bytes > 48 * 1024)
-        TTI_CUDA(cudaFuncSetAttribute(k_jacobi_svd<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+      // the limit is raised once to the largest size any call uses: a per-call value could
+      // be lowered by a concurrent call on another thread between its setting and this launch;
+      // raised whenever shared memory is used, since the kernel's static arrays count against
+      // the default 48 KB too
+      if (bytes > 0) set_smem_limit_once((const void *)k_jacobi_svd<32>, (int)kSvdSmemMax);
       k_jacobi_svd<32><<<1, threads, bytes, st>>>(k, A, U, s, V, Wg, Vg, use_smem, status);
       break;
   }
@@ -719,7 +724,7 @@ void svd_small(Ctx *c, int k, const double *A, double *U, double *s, double *V) 
   TTI_CHECK_ARG(k >= 1 && k <= 256, "svd_small: k=%d out of range", k);
   const int kp = k + (k & 1);
   size_t bytes = 2 * (size_t)kp * k * sizeof(double);
-  int use_smem = bytes <= 200 * 1024;
+  int use_smem = bytes <= kSvdSmemMax;
   DBuf Wg, Vg;
   if (!use_smem) {
     Wg = DBuf(c, (size_t)kp * k * sizeof(double));
@@ -727,7 +732,13 @@ void svd_small(Ctx *c, int k, const double *A, double *U, double *s, double *V) 
     bytes = 0;
   }
   svd_launch(c->stream, k, A, U, s, V, Wg.d(), Vg.d(), use_smem, bytes, c->dstatus);
-  TTI_LAUNCH();
+  const cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    const int kp2 = k + (k & 1), G = k <= 4 ? 4 : (k <= 8 ? 8 : (k <= 16 ? 16 : 32));
+    fail(TT_IGA_ERR_CUDA, "svd_small launch (k=%d, lanes per pair %d, threads %d, shared bytes %zu): %s", k, G,
+         std::min(1024, std::max(32, (kp2 / 2 * G + 31) / 32 * 32)), bytes, cudaGetErrorString(e));
+  }
+  g_launches.fetch_add(1, std::memory_order_relaxed);
 }
 
 // ------------------------------------------- allocation-free SVD entry point

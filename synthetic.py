@@ -78,3 +78,28 @@ def poisson_arrivals(rate_hz, count, seed):
 def random_points(m, seed):
     """m parametric points in [0, 1]^3."""
     return rng(seed).uniform(0.0, 1.0, size=(m, 3))
+
+
+def curved_patch(seed=2, counts=(4, 4, 3), jitter=0.05):
+    """A curved single-patch NURBS volume for the NURBS-input tests: degree 2 in every
+    direction, control points on a cylindrical grid (r in [1, 2], theta in [0, pi/2],
+    z in [0, 1]) moved by Gaussian noise of size jitter, weights in [0.7, 1.3], one interior
+    knot at 0.5 in the first two directions.  Returns (degrees, knots, ctrl[c1, c2, c3, 3],
+    weights[c1, c2, c3])."""
+    g = rng(seed)
+    c1, c2, c3 = counts
+    r = np.linspace(1.0, 2.0, c1)[:, None, None]
+    t = np.linspace(0.0, 0.5 * math.pi, c2)[None, :, None]
+    z = np.linspace(0.0, 1.0, c3)[None, None, :]
+    ctrl = np.zeros((c1, c2, c3, 3))
+    ctrl[..., 0] = r * np.cos(t) + 0 * z
+    ctrl[..., 1] = r * np.sin(t) + 0 * z
+    ctrl[..., 2] = 0 * r + 0 * t + z
+    ctrl = ctrl + jitter * g.standard_normal(ctrl.shape)
+    w = g.uniform(0.7, 1.3, (c1, c2, c3))
+
+    def knots(c, inner):
+        return [0.0, 0.0, 0.0] + inner + [1.0, 1.0, 1.0] if c == 3 + len(inner) else None
+
+    kn = [knots(c1, [0.5]), knots(c2, [0.5]), knots(c3, [])]
+    return (2, 2, 2), kn, ctrl, w

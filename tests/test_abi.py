@@ -47,7 +47,7 @@ def test_struct_layouts_match_header(lib_path, tmp_path):
     import paper_2509_13224_gb300 as tt
     structs = {"tt_iga_geom_desc": tt.GeomDesc, "tt_iga_rhs_desc": tt.RhsDesc, "tt_iga_solve_opts": tt.SolveOpts,
                "tt_iga_stats": tt.Stats, "tt_iga_ctx_opts": tt.CtxOpts, "tt_iga_batch_item": tt.BatchItem,
-               "tt_iga_bc_desc": tt.BcDesc,
+               "tt_iga_bc_desc": tt.BcDesc, "tt_iga_nurbs_patch": tt.NurbsPatch,
                "tt_iga_batch_result": tt.BatchResult}
     lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "tt_iga.h"', "int main(void) {"]
     for cname, py in structs.items():

@@ -31,18 +31,8 @@ def test_trilinear_patch_equals_the_box():
 
 
 def _curved_patch(seed=2):
-    rng = np.random.default_rng(seed)
-    base = quarter_cylinder_patch(1.0, 2.0, 1.0)
-    # degree 2 in every direction with perturbed interior control points and weights
-    c = [4, 4, 3]
-    ctrl = np.zeros(c + [3])
-    w = np.zeros(c)
-    g = [np.linspace(0, 1, ci) for ci in c]
-    X, _ = base.map(g[0], g[1], g[2])
-    ctrl[:] = X + 0.05 * rng.standard_normal(X.shape)
-    w[:] = rng.uniform(0.7, 1.3, c)
-    knots = [[0, 0, 0, 0.5, 1, 1, 1], [0, 0, 0, 0.5, 1, 1, 1], [0, 0, 0, 1, 1, 1]]
-    return NURBSPatch((2, 2, 2), knots, ctrl, w)
+    import synthetic
+    return NURBSPatch(*synthetic.curved_patch(seed))
 
 
 def test_jacobian_matches_finite_differences():
