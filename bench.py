@@ -360,6 +360,49 @@ def run_ours(args, rank, world):
         ring.update({"value": world * dofs / (ms / 1e3), "unit": "DOFs/s", "ms_per_step": ms,
                      "rel_residual": st["rel_residual"], "ranks": st["ranks"], "sweeps": st["sweeps"]})
 
+    # side measurement of the NURBS input path: (1) the bench problem with the quarter cylinder given as a
+    # NURBS control net (the map evaluated from the net on the device), (2) a curved patch (degree 2,
+    # perturbed cylindrical net, random weights) at n = 32, constant source, homogeneous Dirichlet data
+    nurbs = None
+    if not args.no_extra and args.workload == WORKLOAD:
+        cases = [("quarter_cylinder_as_nurbs_p3_n128", synthetic.quarter_cylinder_net(1.0, 2.0, 1.0), n,
+                  wl["cross_tol"], [tt.rhs_desc(constant=1.0)]),
+                 ("curved_nurbs_patch_p3_n32", synthetic.curved_patch(seed=2), 32, 1e-8, [tt.rhs_desc(constant=1.0)])]
+        nurbs = {}
+        for name, net, nn, ctol, rr in cases:
+            ndesc = tt.geom_desc({"kind": "nurbs"}, p, nn, cross_tol=ctol, seed=rank)
+            rec = {"dofs": nn ** 3}
+            ts, tg = [], []
+            for rep in range(3):
+                with torch.cuda.stream(stream):
+                    flush.zero_()
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                eg = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                g = tt.tt_iga_geometry_nurbs(ctx, ndesc, *net, allow_not_converged=True)
+                eg.record(stream)
+                s = tt.tt_iga_assemble(ctx, g, rr, round_tol=max(ctol, wl["round_tol"]))
+                u, st = tt.tt_iga_solve(ctx, s, tt.solve_opts(tol=TOL, precision=tt.FP64), allow_not_converged=True)
+                e1.record(stream)
+                e1.synchronize()
+                if rep > 0:
+                    ts.append(e0.elapsed_time(e1))
+                    tg.append(e0.elapsed_time(eg))
+                if rep == 2:
+                    gr, gerr = tt.tt_iga_geom_ranks(g)
+                    rec.update({"geometry_ranks": gr, "cross_max_rel_err": max(gerr),
+                                "op_ranks": tt.tt_iga_system_info(s)["op_ranks"]})
+                tt.tt_iga_solution_destroy(u)
+                tt.tt_iga_system_destroy(s)
+                tt.tt_iga_geom_destroy(g)
+            ms = max_over_ranks(statistics.mean(ts), world)
+            rec.update({"value": world * nn ** 3 / (ms / 1e3), "unit": "DOFs/s", "ms_per_step": ms,
+                        "geometry_ms": statistics.mean(tg),
+                        "rel_residual": st["rel_residual"], "converged": bool(st["converged"]), "ranks": st["ranks"],
+                        "sweeps": st["sweeps"]})
+            nurbs[name] = rec
+
     # end to end through the C ABI: host descriptors in, compressed solution cores read back to pinned host memory
     e2e_times = []
     hbuf = None
@@ -443,7 +486,7 @@ def run_ours(args, rank, world):
             "e2e": {"value": world * dofs / e2e_s, "unit": "DOFs/s", "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h},
             "gpu_launches": launches, "clocks": clk, "roofline": roof, "cpu_baseline": base, "mixed": mixed,
-            "twisted_n512": extra, "ring_dirichlet": ring, "batched": batched, "serving": serving,
+            "twisted_n512": extra, "ring_dirichlet": ring, "nurbs_patch": nurbs, "batched": batched, "serving": serving,
             "phases_ms": info64.get("phases_ms"),
             "solve": {"rel_residual": info64.get("rel_residual"), "sweeps": info64.get("sweeps"),
                       "ranks": info64.get("ranks"), "op_ranks": info64.get("op_ranks"),

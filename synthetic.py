@@ -103,3 +103,20 @@ def curved_patch(seed=2, counts=(4, 4, 3), jitter=0.05):
 
     kn = [knots(c1, [0.5]), knots(c2, [0.5]), knots(c3, [])]
     return (2, 2, 2), kn, ctrl, w
+
+
+def quarter_cylinder_net(r_in=1.0, r_out=2.0, height=1.0):
+    """The quarter cylinder as a NURBS control net (degrees (1, 2, 1)): radial control values
+    r_in, r_out, the quarter circle (1,0), (1,1), (0,1) with weights 1, sqrt(2)/2, 1, axial 0 and
+    height.  Returns (degrees, knots, ctrl[2, 3, 2, 3], weights[2, 3, 2])."""
+    arc = [(1.0, 0.0), (1.0, 1.0), (0.0, 1.0)]
+    warc = [1.0, math.sqrt(0.5), 1.0]
+    ctrl = np.zeros((2, 3, 2, 3))
+    w = np.zeros((2, 3, 2))
+    for i, r in enumerate((r_in, r_out)):
+        for j in range(3):
+            for k, z in enumerate((0.0, height)):
+                ctrl[i, j, k] = [r * arc[j][0], r * arc[j][1], z]
+                w[i, j, k] = warc[j]
+    knots = [[0.0, 0.0, 1.0, 1.0], [0.0, 0.0, 0.0, 1.0, 1.0, 1.0], [0.0, 0.0, 1.0, 1.0]]
+    return (1, 2, 1), knots, ctrl, w
