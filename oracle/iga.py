@@ -218,11 +218,41 @@ def lift_vector(n, dirichlet, value):
     return g
 
 
-def solve_bc(spaces, geom, source, dirichlet, value, tol=1e-14):
-    """Dirichlet faces with constant data, natural (zero-flux) conditions on the others:
-    u = g + u_I with K_II u_I = F_I - (K g)_I; returns the full coefficient array."""
+def neumann_load(spaces, geom, face, flux):
+    """Load of a constant normal flux du/dn = flux on face = 2 d + side (outward normal):
+    F_a = int_face flux N_a dGamma, dGamma = |dx/dxi_e x dx/dxi_f| dxi_e dxi_f over the two
+    tangential directions e < f, with the per-direction Gauss rules of the spaces.  Only the
+    functions that are nonzero on the face (index 0 on side 0, n_d - 1 on side 1) receive load."""
+    d, side = divmod(face, 2)
+    e, f = [k for k in range(3) if k != d]
+    n = tuple(sp.n for sp in spaces)
+    xs = [sp.flat_points() for sp in spaces]
+    ws = [sp.flat_weights() for sp in spaces]
+    xs[d] = np.array([float(side)])
+    X, J = geom.map(*xs)
+    area = np.linalg.norm(np.cross(J[..., :, e], J[..., :, f]), axis=-1)  # [Q1|1, Q2|1, Q3|1]
+    area = np.squeeze(area, axis=d)
+    Ne, _ = bspline_basis(spaces[e].knots, spaces[e].p, xs[e])
+    Nf, _ = bspline_basis(spaces[f].knots, spaces[f].p, xs[f])
+    G = np.einsum("qa,rb,qr,q,r->ab", Ne, Nf, flux * area, ws[e], ws[f], optimize=True)
+    F = np.zeros(n)
+    sel = [slice(None)] * 3
+    sel[d] = 0 if side == 0 else n[d] - 1
+    F[tuple(sel)] = G
+    return F
+
+
+def solve_bc(spaces, geom, source, dirichlet, value, tol=1e-14, flux=None):
+    """Dirichlet faces with constant data, natural conditions on the others (zero flux, or the
+    constant normal flux flux[face] on a natural face): u = g + u_I with
+    K_II u_I = F_I + (F_Gamma)_I - (K g)_I; returns the full coefficient array."""
     assert any(dirichlet), "pure natural conditions leave K singular"
     Kst, F = assemble(spaces, geom, source)
+    if flux is not None:
+        for face in range(6):
+            if flux[face] != 0.0:
+                assert not dirichlet[face], "flux data on a Dirichlet face"
+                F = F + neumann_load(spaces, geom, face, flux[face])
     n = F.shape
     p = tuple(s.p for s in spaces)
     g = lift_vector(n, dirichlet, value)

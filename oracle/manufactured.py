@@ -14,6 +14,8 @@ With r_in = 1, r_out = 2, H = 1, no twist and no modes it is
 sin(pi x/Lx) sin(pi y/Ly) sin(pi z/Lz) times the same modulation.
 f = -Laplace(u) in physical coordinates, by hyper-dual differentiation.
 """
+import math
+
 import numpy as np
 
 from . import hyperdual as hd
@@ -78,6 +80,36 @@ class RingLog:
     def u(self, X):
         rho = np.sqrt(X[..., 0] ** 2 + X[..., 1] ** 2)
         return self.u_in + (self.u_out - self.u_in) * np.log(rho / self.r_in) / np.log(self.r_out / self.r_in)
+
+    def f(self, X):
+        return np.zeros(X.shape[:-1])
+
+
+
+class RingMixed:
+    """Exact radial solution u = A + B ln(rho / r_in) of -Laplace(u) = 0 on the quarter cylinder
+    (no twist, no swell) with zero flux on the angular and axial faces and, on each radial face,
+    either a value (Dirichlet) or an outward normal flux du/dn (Section 4.3 with Neumann data).
+    The outward normal is -rho on rho = r_in and +rho on rho = r_out, so du/dn = -B / r_in there
+    and +B / r_out here; a value fixes A + B ln(rho / r_in).  inner / outer are pairs
+    ("value", a) or ("flux", q); at least one must be a value."""
+
+    def __init__(self, r_in=1.0, r_out=2.0, inner=("value", 1.0), outer=("flux", 1.0)):
+        self.r_in, self.r_out = float(r_in), float(r_out)
+        L = math.log(self.r_out / self.r_in)
+        (ki, vi), (ko, vo) = inner, outer
+        assert "value" in (ki, ko), "flux data on both radial faces leaves A undetermined"
+        if ki == "value" and ko == "value":
+            self.A, self.B = vi, (vo - vi) / L
+        elif ki == "value":
+            self.A, self.B = vi, vo * self.r_out
+        else:
+            self.B = -vi * self.r_in
+            self.A = vo - self.B * L
+
+    def u(self, X):
+        rho = np.sqrt(X[..., 0] ** 2 + X[..., 1] ** 2)
+        return self.A + self.B * np.log(rho / self.r_in)
 
     def f(self, X):
         return np.zeros(X.shape[:-1])
