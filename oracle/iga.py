@@ -12,7 +12,8 @@ dropping the first and last basis function of every direction (the open knot
 vector makes the basis interpolatory at the ends) -- or, for the
 non-homogeneous Dirichlet problem of Section 4.3 (constant data on some faces,
 natural conditions on the others), a lift g carrying the data on the dropped
-functions and the right-hand side F - K g -- a Jacobi-preconditioned
+functions and the right-hand side F - K g, plus, for a constant normal flux on
+a natural face, the face load int flux N_a dGamma -- a Jacobi-preconditioned
 conjugate-gradient solve of the restricted system, and the relative L2 error
 of Eq. (L2norm) read as sqrt(int (u_h - u)^2) / sqrt(int u^2) with p+3 Gauss
 points per element.
@@ -25,7 +26,10 @@ g = i1 + n1 (i2 + n2 i3) (i1 fastest).
 
 Pins: tests/test_oracle_iga.py (Kronecker structure on the identity map with
 textbook 1D matrices, symmetry, K 1 = 0, SPD after restriction, volume, dense
-LU on tiny meshes, energy identity, L2 convergence rate h^(p+1)).
+LU on tiny meshes, energy identity, L2 convergence rate h^(p+1));
+tests/test_oracle_bc.py (Dirichlet data); tests/test_oracle_neumann.py (face
+loads against basis-integral and surface-area closed forms, exact linear
+solutions with flux data, the mixed ring problem's convergence).
 """
 import numpy as np
 
