@@ -180,12 +180,15 @@ enum { TT_IGA_RHS_MANUFACTURED = 0, TT_IGA_RHS_CONSTANT = 1, TT_IGA_RHS_RING_LOG
  * the coordinates with twist and swell undone; box: sin(pi x/lx) sin(pi y/ly)
  * sin(pi z/lz)) times 1 + sum_k a[k] sin(b[k] . x + c[k]); the Laplacian is
  * taken exactly on the device by hyper-dual arithmetic.  CONSTANT: f = value.
- * RING_LOG: f = value (0 for the ring problem of Section 4.3); with Dirichlet
- * data u_in on the radial face xi_1 = 0 and u_out on xi_1 = 1 of the annulus
- * without twist and swell, natural conditions elsewhere, and value 0, the exact
- * solution is u = u_in + (u_out - u_in) ln(rho / r_in) / ln(r_out / r_in), which
- * tt_iga_l2_error compares against (u_in, u_out taken from the solution's
- * boundary data). */
+ * RING_LOG: f = value (0 for the ring problem of Section 4.3); on the annulus
+ * without twist and swell, with value 0, zero flux on the four faces of
+ * directions 1 and 2, and on each radial face (xi_1 = 0: rho = r_in, xi_1 = 1:
+ * rho = r_out) either Dirichlet data or a flux, at least one of them Dirichlet,
+ * the exact solution is u = A + B ln(rho / r_in): Dirichlet data u_in, u_out on
+ * both gives A = u_in, B = (u_out - u_in) / ln(r_out / r_in); a flux q on the
+ * outer face gives B = q r_out, on the inner face B = -q r_in (outward normal
+ * -rho), and the Dirichlet face fixes A.  tt_iga_l2_error compares against it,
+ * with the data taken from the solution's boundary conditions. */
 typedef struct {
   int kind;
   int n_modes; /* 0 .. TT_IGA_MAX_MODES */
@@ -213,13 +216,21 @@ int tt_iga_assemble(tt_iga_ctx *ctx, const tt_iga_geom *g, const tt_iga_rhs_desc
  * (constant data), imposed by dropping the basis function that is
  * interpolatory there and moving the data to the right-hand side,
  * F <- F - K g with g the lift carrying the data on the dropped functions;
- * dirichlet[f] == 0: natural condition (zero normal flux).  Nonzero values are
- * accepted on the faces of one direction only, and the faces of the other two
- * directions must then be natural; at least one face must be Dirichlet
- * (otherwise K is singular).  Violations return TT_IGA_ERR_ARG. */
+ * dirichlet[f] == 0: natural condition with the constant outward normal flux
+ * du/dn = flux[f] (0: zero flux), which adds the face's part of the surface
+ * load vector f_s (Section 3.3; the boundary term of the weak form of Section
+ * 3.2), int_face flux[f] N_a dGamma, to every right-hand side; the area density
+ * |dx/dxi_e x dx/dxi_f| of the face (e, f its tangential directions) is a
+ * TT-cross of its own, contracted with the same per-direction Gauss rules as
+ * the volume load.  Nonzero values are accepted on the faces of one direction
+ * only, and the faces of the other two directions must then be natural; at
+ * least one face must be Dirichlet (otherwise K is singular); a nonzero flux
+ * is accepted on natural faces only; values and fluxes must be finite.
+ * Violations return TT_IGA_ERR_ARG. */
 typedef struct {
   int dirichlet[6];
   double value[6];
+  double flux[6];
 } tt_iga_bc_desc;
 
 /* tt_iga_assemble with boundary conditions bc (tt_iga_assemble is the case of
@@ -297,7 +308,7 @@ int tt_iga_eval(tt_iga_ctx *ctx, const tt_iga_solution *u, int m, const double *
  * domain (Eq. L2norm, with p+3 Gauss points per element) against the exact
  * solution of rhs: the manufactured solution (kind MANUFACTURED), or the log
  * solution of the ring problem (kind RING_LOG: annulus without twist and swell,
- * Dirichlet data on the radial faces only, taken from u's boundary data). */
+ * data on the radial faces only, taken from u's boundary conditions). */
 int tt_iga_l2_error(tt_iga_ctx *ctx, const tt_iga_geom *g, const tt_iga_solution *u,
                     const tt_iga_rhs_desc *rhs, double *rel_l2);
 

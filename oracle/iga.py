@@ -223,7 +223,8 @@ def lift_vector(n, dirichlet, value):
 
 
 def neumann_load(spaces, geom, face, flux):
-    """Load of a constant normal flux du/dn = flux on face = 2 d + side (outward normal):
+    """Surface load vector f_s (Section 3.3) of a constant normal flux du/dn = flux on
+    face = 2 d + side (outward normal):
     F_a = int_face flux N_a dGamma, dGamma = |dx/dxi_e x dx/dxi_f| dxi_e dxi_f over the two
     tangential directions e < f, with the per-direction Gauss rules of the spaces.  Only the
     functions that are nonzero on the face (index 0 on side 0, n_d - 1 on side 1) receive load."""

@@ -48,7 +48,7 @@ class GeomDesc(ctypes.Structure):
 
 
 class BcDesc(ctypes.Structure):
-    _fields_ = [("dirichlet", ctypes.c_int * 6), ("value", ctypes.c_double * 6)]
+    _fields_ = [("dirichlet", ctypes.c_int * 6), ("value", ctypes.c_double * 6), ("flux", ctypes.c_double * 6)]
 
 
 class NurbsPatch(ctypes.Structure):
@@ -368,12 +368,14 @@ def tt_iga_assemble(ctx, g, rhs_list, round_tol=1e-12):
     return h
 
 
-def bc_desc(dirichlet, values=(0.0,) * 6):
-    """BcDesc: dirichlet[f] (bool) and constant value[f] for face f = 2 d + side."""
+def bc_desc(dirichlet, values=(0.0,) * 6, flux=(0.0,) * 6):
+    """BcDesc: dirichlet[f] (bool), constant value[f] (Dirichlet faces) and constant outward
+    normal flux[f] (natural faces) for face f = 2 d + side."""
     b = BcDesc()
     for f in range(6):
         b.dirichlet[f] = 1 if dirichlet[f] else 0
         b.value[f] = float(values[f])
+        b.flux[f] = float(flux[f])
     return b
 
 

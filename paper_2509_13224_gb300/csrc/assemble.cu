@@ -82,6 +82,19 @@ void load_core(Ctx *c, int n, int p, int nq, const double *wts, const double *N,
   TTI_LAUNCH();
 }
 
+// Normal-direction core of a face load: the area density's core G[r0][Q][r1] does not vary
+// along the mode (the field is evaluated on the face), so its first slice, scaled by the flux
+// q, sits on basis function idx (0 or n - 1, the only one nonzero on the face); the others are 0.
+__global__ void k_face_core(const double *G, int r0, int Q, int r1, int n, int idx, double q, double *F) {
+  const long long tot = (long long)r0 * n * r1;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < tot; e += (long long)gridDim.x * blockDim.x) {
+    const int beta = (int)(e % r1);
+    const long long t = e / r1;
+    const int i = (int)(t % n), alpha = (int)(t / n);
+    F[e] = (i == idx) ? q * G[(long long)alpha * Q * r1 + beta] : 0.0;
+  }
+}
+
 // Drop basis functions 0 and n-1 (homogeneous Dirichlet, Section 4.3):
 // band core [r0][n][b][r1] -> [r0][n-2][b][r1], zeroing couplings to the dropped functions.
 // Keep functions lo .. lo + nr - 1 of a band core (couplings to dropped functions zeroed).
@@ -149,7 +162,11 @@ BoundaryLayout boundary_layout(const tt_iga_bc_desc *bc, const int nfull[3]) {
     bl.hi[d] = bc->dirichlet[2 * d + 1] ? 1 : 0;
     any = any || bl.lo[d] || bl.hi[d];
     for (int side = 0; side < 2; ++side) {
-      TTI_CHECK_ARG(std::isfinite(bc->value[2 * d + side]), "bc: value of face %d is not finite", 2 * d + side);
+      const int f = 2 * d + side;
+      TTI_CHECK_ARG(std::isfinite(bc->value[f]), "bc: value of face %d is not finite", f);
+      TTI_CHECK_ARG(std::isfinite(bc->flux[f]), "bc: flux of face %d is not finite", f);
+      TTI_CHECK_ARG(bc->flux[f] == 0.0 || !bc->dirichlet[f], "bc: flux on the Dirichlet face %d", f);
+      bl.flux[f] = bc->flux[f];
       if (bc->dirichlet[2 * d + side] && bc->value[2 * d + side] != 0.0) {
         TTI_CHECK_ARG(dir < 0 || dir == d, "bc: nonzero Dirichlet data on more than one direction");
         dir = d;
@@ -179,7 +196,9 @@ void assemble_system(Ctx *c, const tt_iga_geom *g, const tt_iga_rhs_desc *rhs, i
   int n[3];
   for (int d = 0; d < 3; ++d) n[d] = g->s[d].n;
   const bool lift = bl.lift_dir >= 0;
+  const bool flux = bl.has_flux();
   TT3 K, Kfull;  // Kfull: the operator before restriction, kept for F - K g
+  TT3 Fn;        // sum of the face loads of the flux data
   std::vector<TT3> F(n_rhs);
   std::vector<double> F_norm(n_rhs, 0.0);
 
@@ -245,18 +264,71 @@ void assemble_system(Ctx *c, const tt_iga_geom *g, const tt_iga_rhs_desc *rhs, i
         load_core(h, n[d], p, g->s[d].nq, g->s[d].wts.d(), g->s[d].N.d(), fj.tt.core[d].d(), fj.tt.r[d],
                   fj.tt.r[d + 1], Fk.core[d].d());
     }
-    if (!lift) {
+    if (!lift && !flux) {
       restrict_tt(h, Fk, bl, p, false);
       F_norm[k] = tt_round(h, Fk, round_tol, 0);
     }
     for (int d = 0; d < 3; ++d) Fk.core[d].rehome(c);
   };
 
-  run_concurrent(c, 1 + n_rhs, [&](int task, Ctx *h) {
+  // Surface load vector of the flux data (f_s of Section 3.3, the boundary term of the weak
+  // form of Section 3.2), F_a = q int_face N_a dGamma: the area density of each face with a
+  // flux by TT-cross, contracted with the tangential quadrature, summed over the faces.
+  auto build_faces = [&](Ctx *h) {
+    std::vector<TT3> terms;
+    RhsParams none = rhs_params(nullptr);
+    for (int f = 0; f < 6; ++f) {
+      const double q = bl.flux[f];
+      if (q == 0.0) continue;
+      const int d = f >> 1;
+      CrossResult a;
+      cross3(h, g->s, g->gp, none, kFaceComp0 + f, g->desc.cross_tol, g->desc.max_rank,
+             g->desc.seed + 104729ULL * (f + 1), 0.0, a);
+      TTI_CHECK_ARG(!a.zero, "bc: face %d has zero area", f);
+      if (!a.converged) fail(TT_IGA_ERR_NOT_CONVERGED, "bc: TT-cross of the area of face %d did not validate", f);
+      TT3 T;
+      for (int k = 0; k < 3; ++k) T.m[k] = n[k];
+      for (int k = 0; k < 4; ++k) T.r[k] = a.tt.r[k];
+      T.alloc(h);
+      for (int k = 0; k < 3; ++k) {
+        if (k == d) {
+          const long long tot = (long long)T.r[k] * n[k] * T.r[k + 1];
+          k_face_core<<<grid1d(tot, 256), 256, 0, h->stream>>>(a.tt.core[k].d(), T.r[k], g->s[k].Q, T.r[k + 1], n[k],
+                                                                (f & 1) ? n[k] - 1 : 0, q, T.core[k].d());
+          TTI_LAUNCH();
+        } else {
+          load_core(h, n[k], p, g->s[k].nq, g->s[k].wts.d(), g->s[k].N.d(), a.tt.core[k].d(), T.r[k], T.r[k + 1],
+                    T.core[k].d());
+        }
+      }
+      if (!terms.empty()) {
+        TT3 S;
+        tt_sum(h, terms.back(), 1.0, T, 1.0, S);
+        tt_round(h, S, round_tol, 0);
+        terms.back() = std::move(S);
+      } else {
+        terms.push_back(std::move(T));
+      }
+    }
+    Fn = std::move(terms.back());
+    for (int k = 0; k < 3; ++k) Fn.core[k].rehome(c);
+  };
+
+  run_concurrent(c, 1 + n_rhs + (flux ? 1 : 0), [&](int task, Ctx *h) {
     if (task == 0) build_operator(h);
-    else build_load(task - 1, h);
+    else if (task <= n_rhs) build_load(task - 1, h);
+    else build_faces(h);
   });
 
+  if (flux && !lift) {
+    for (int k = 0; k < n_rhs; ++k) {
+      TT3 S;
+      tt_sum(c, F[k], 1.0, Fn, 1.0, S);
+      restrict_tt(c, S, bl, p, false);
+      F_norm[k] = tt_round(c, S, round_tol, 0);
+      F[k] = std::move(S);
+    }
+  }
   if (lift) {
     // g = (lift_lo e_0 + lift_hi e_{n-1}) in direction lift_dir, ones in the others (rank 1);
     // K g by band TT-matrix times TT vector, then F_k <- F_k - K g, restricted and rounded
@@ -282,6 +354,11 @@ void assemble_system(Ctx *c, const tt_iga_geom *g, const tt_iga_rhs_desc *rhs, i
     }
     c->sync();  // the host vectors above are released at scope end
     for (int k = 0; k < n_rhs; ++k) {
+      if (flux) {
+        TT3 T;
+        tt_sum(c, F[k], 1.0, Fn, 1.0, T);
+        F[k] = std::move(T);
+      }
       TT3 S;
       tt_sum(c, F[k], 1.0, Kg, -1.0, S);
       restrict_tt(c, S, bl, p, false);

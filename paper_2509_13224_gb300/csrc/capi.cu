@@ -473,10 +473,15 @@ int tt_iga_l2_error(tt_iga_ctx *c, const tt_iga_geom *g, const tt_iga_solution *
   TTI_CHECK_ARG(rhs->kind == TT_IGA_RHS_MANUFACTURED || rhs->kind == TT_IGA_RHS_RING_LOG,
                 "l2_error: needs a right-hand side with an exact solution (MANUFACTURED or RING_LOG)");
   TTI_CHECK_ARG(g->desc.kind != TT_IGA_GEOM_NURBS, "l2_error: no exact solution is defined on a NURBS patch");
-  if (rhs->kind == TT_IGA_RHS_RING_LOG)
-    TTI_CHECK_ARG(g->desc.kind == TT_IGA_GEOM_ANNULUS && g->desc.twist == 0.0 && g->desc.swell == 0.0 &&
-                      u->bl.lift_dir == 0,
-                  "l2_error: the ring solution needs the annulus without twist and swell and radial Dirichlet data");
+  if (rhs->kind == TT_IGA_RHS_RING_LOG) {
+    const BoundaryLayout &bl = u->bl;
+    bool radial_only = bl.lift_dir <= 0 && (bl.lo[0] || bl.hi[0]);
+    for (int d = 1; d < 3; ++d)
+      radial_only = radial_only && !bl.lo[d] && !bl.hi[d] && bl.flux[2 * d] == 0.0 && bl.flux[2 * d + 1] == 0.0;
+    TTI_CHECK_ARG(g->desc.kind == TT_IGA_GEOM_ANNULUS && g->desc.twist == 0.0 && g->desc.swell == 0.0 && radial_only,
+                  "l2_error: the ring solution needs the annulus without twist and swell, data on the radial faces "
+                  "only and at least one radial Dirichlet face");
+  }
   *rel = l2_error(c, g, u, rhs);
   return TT_IGA_OK;
   API_CATCH(c)

@@ -72,10 +72,8 @@ __global__ void k_fibers(GeomParams g, RhsParams f, int comp, const double *x1, 
     } else {
       i1 = rowA[row]; i2 = rowB[row]; i3 = col;
     }
-    double o[8];
     int bad = 0;
-    point_outputs(g, f, x1[i1], x2[i2], x3[i3], o, &bad);
-    Y[e] = o[comp];
+    Y[e] = field_value(g, f, comp, x1[i1], x2[i2], x3[i3], &bad);
     if (bad) atomicMax(status, (int)DS_BAD_GEOMETRY);
   }
 }
@@ -83,10 +81,8 @@ __global__ void k_fibers(GeomParams g, RhsParams f, int comp, const double *x1, 
 __global__ void k_field_points(GeomParams g, RhsParams f, int comp, const double *x1, const double *x2,
                                const double *x3, int m, const int *idx, double *out, int *status) {
   for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < m; t += gridDim.x * blockDim.x) {
-    double o[8];
     int bad = 0;
-    point_outputs(g, f, x1[idx[3 * t]], x2[idx[3 * t + 1]], x3[idx[3 * t + 2]], o, &bad);
-    out[t] = o[comp];
+    out[t] = field_value(g, f, comp, x1[idx[3 * t]], x2[idx[3 * t + 1]], x3[idx[3 * t + 2]], &bad);
     if (bad) atomicMax(status, (int)DS_BAD_GEOMETRY);
   }
 }

@@ -14,7 +14,8 @@ struct CrossResult {
   long long evaluations = 0;
 };
 
-// Cross of output component comp (0..7 of the point evaluator) on the grid of
+// Cross of output component comp (0..7 of the point evaluator, 8..13 the face
+// area densities, see field_value) on the grid of
 // spaces s[3].  eps: relative accuracy; zero_scale: fields with max |f| below
 // 1e-13 * zero_scale are rank 0 (pass 0 to use the field's own scale).
 // zero_ref (optional) replaces zero_scale: it is called once, with max |f| over

@@ -122,7 +122,7 @@ __global__ void k_l2_accumulate(GeomParams g, RhsParams f, const double *__restr
                                 const double *__restrict__ w2, const double *__restrict__ w3, int Q1, int Q2, int Q3,
                                 const double *__restrict__ T1, const double *__restrict__ T2,
                                 const double *__restrict__ T3, int r1, int r2, int lift_dir,
-                                const double *__restrict__ liftq, double u_in, double u_out, double *part) {
+                                const double *__restrict__ liftq, double ring_a, double ring_b, double *part) {
   __shared__ double red[2][32];
   double num = 0.0, den = 0.0;
   const long long tot = (long long)Q1 * Q2 * Q3;
@@ -143,9 +143,9 @@ __global__ void k_l2_accumulate(GeomParams g, RhsParams f, const double *__restr
     const double det = J[0][0] * (J[1][1] * J[2][2] - J[1][2] * J[2][1]) -
                        J[0][1] * (J[1][0] * J[2][2] - J[1][2] * J[2][0]) +
                        J[0][2] * (J[1][0] * J[2][1] - J[1][1] * J[2][0]);
-    // RING_LOG: the log solution of the ring problem (annulus without twist and swell)
+    // RING_LOG: the radial solution A + B ln(rho / r_in) of the ring problem (annulus without twist and swell)
     const double ue = (f.kind == TT_IGA_RHS_RING_LOG)
-                          ? u_in + (u_out - u_in) * log(sqrt(X[0] * X[0] + X[1] * X[1]) / g.r_in) / log(g.r_out / g.r_in)
+                          ? ring_a + ring_b * log(sqrt(X[0] * X[0] + X[1] * X[1]) / g.r_in)
                           : manufactured_value(g, f, X[0], X[1], X[2]);
     const double w = w1[q1] * w2[q2] * w3[q3] * det;
     num += w * (uh - ue) * (uh - ue);
@@ -168,8 +168,28 @@ __global__ void k_l2_accumulate(GeomParams g, RhsParams f, const double *__restr
   }
 }
 
+// Coefficients of the ring problem's exact solution u = A + B ln(rho / r_in) from the radial faces'
+// data: a value fixes A + B ln(rho / r_in) there, an outward flux q fixes du/dn = B / r_out
+// (outer face) or -B / r_in (inner face, outward normal -rho).
+static void ring_solution(const tt_iga_geom *g, const BoundaryLayout &bl, double *A, double *B) {
+  const double L = log(g->desc.r_out / g->desc.r_in);
+  const double v_in = bl.lift_dir == 0 ? bl.lift_lo : 0.0, v_out = bl.lift_dir == 0 ? bl.lift_hi : 0.0;
+  if (bl.lo[0] && bl.hi[0]) {
+    *A = v_in;
+    *B = (v_out - v_in) / L;
+  } else if (bl.lo[0]) {
+    *A = v_in;
+    *B = bl.flux[1] * g->desc.r_out;
+  } else {
+    *B = -bl.flux[0] * g->desc.r_in;
+    *A = v_out - *B * L;
+  }
+}
+
 double l2_error(Ctx *c, const tt_iga_geom *g, const tt_iga_solution *u, const tt_iga_rhs_desc *rhs) {
   const int p = u->p;
+  double ring_a = 0.0, ring_b = 0.0;
+  if (rhs->kind == TT_IGA_RHS_RING_LOG) ring_solution(g, u->bl, &ring_a, &ring_b);
   Space fine[3];
   DBuf T[3];
   for (int d = 0; d < 3; ++d) {
@@ -195,7 +215,7 @@ double l2_error(Ctx *c, const tt_iga_geom *g, const tt_iga_solution *u, const tt
   k_l2_accumulate<<<nb, 256, 0, c->stream>>>(g->gp, rp, fine[0].pts.d(), fine[1].pts.d(), fine[2].pts.d(),
                                              fine[0].wts.d(), fine[1].wts.d(), fine[2].wts.d(), fine[0].Q, fine[1].Q,
                                              fine[2].Q, T[0].d(), T[1].d(), T[2].d(), u->u.r[1], u->u.r[2], ld,
-                                             liftq.d(), u->bl.lift_lo, u->bl.lift_hi, part.d());
+                                             liftq.d(), ring_a, ring_b, part.d());
   TTI_LAUNCH();
   std::vector<double> h(2 * nb);
   c->d2h(h.data(), part.d(), h.size() * sizeof(double));

@@ -37,6 +37,10 @@ RhsParams rhs_params(const tt_iga_rhs_desc *r);
 void build_space(Ctx *c, Space &s, int n, int p, int nq);
 void basis_tables(Ctx *c, int n, int p, int nq, double *pts, double *wts, double *N, double *dN);
 
+// First cross component beyond the 8 point outputs: component kFaceComp0 + f is the
+// area density of face f = 2 d + side (field_value in geom_device.cuh).
+constexpr int kFaceComp0 = 8;
+
 // Evaluate the 8 point outputs (R11 R12 R13 R22 R23 R33 detJ f*detJ) at m grid
 // points idx[m][3] (device); out[m][8] (device).
 void geom_points(Ctx *c, const GeomParams &g, const RhsParams &f, const double *x1, const double *x2,

@@ -347,5 +347,33 @@ __device__ inline void point_outputs(const GeomParams &g, const RhsParams &f, do
   o[7] = f.has ? source_term(g, f, X[0], X[1], X[2]) * det : 0.0;
 }
 
+// Cross components beyond the eight point outputs: kFaceComp0 + 2 d + side is the area
+// density |dx/dxi_e x dx/dxi_f| of the face xi_d = side (e < f its tangential directions),
+// the surface measure of a face integral.  It is evaluated with xi_d replaced by side, so as
+// a field on the volume grid it does not vary along direction d.
+
+__device__ inline double face_area_density(const GeomParams &g, int face, double x1, double x2, double x3, int *bad) {
+  const int d = face >> 1;
+  const double side = (double)(face & 1);
+  double X[3], J[3][3];
+  map_point(g, d == 0 ? side : x1, d == 1 ? side : x2, d == 2 ? side : x3, X, J);
+  const int e = d == 0 ? 1 : 0, h = d == 2 ? 1 : 2;
+  const double c0 = J[1][e] * J[2][h] - J[2][e] * J[1][h];
+  const double c1 = J[2][e] * J[0][h] - J[0][e] * J[2][h];
+  const double c2 = J[0][e] * J[1][h] - J[1][e] * J[0][h];
+  const double a = sqrt(c0 * c0 + c1 * c1 + c2 * c2);
+  if (!(a > 0.0)) *bad = 1;
+  return a;
+}
+
+// One cross component at a point (0..7: point_outputs, 8..13: face area densities).
+__device__ inline double field_value(const GeomParams &g, const RhsParams &f, int comp, double x1, double x2,
+                                     double x3, int *bad) {
+  if (comp >= kFaceComp0) return face_area_density(g, comp - kFaceComp0, x1, x2, x3, bad);
+  double o[8];
+  point_outputs(g, f, x1, x2, x3, o, bad);
+  return o[comp];
+}
+
 
 }  // namespace ttiga

@@ -23,6 +23,12 @@ struct BoundaryLayout {
   int lo[3] = {1, 1, 1}, hi[3] = {1, 1, 1}, nfull[3] = {0, 0, 0};
   int lift_dir = -1;
   double lift_lo = 0.0, lift_hi = 0.0;
+  double flux[6] = {0, 0, 0, 0, 0, 0};  // outward normal flux of the natural faces
+  bool has_flux() const {
+    for (double q : flux)
+      if (q != 0.0) return true;
+    return false;
+  }
 };
 }  // namespace ttiga
 

@@ -1,5 +1,5 @@
-"""Pins of the oracle's Neumann (flux) data on natural faces (Section 4.3 with a prescribed normal
-flux): the face load against closed forms of B-spline integrals and surface areas, exactness of
+"""Pins of the oracle's Neumann (flux) data on natural faces (the surface load vector f_s of
+Section 3.3): the face load against closed forms of B-spline integrals and surface areas, exactness of
 linear solutions on the box (both signs of the outward normal), and convergence of the mixed
 ring problem to its log solution."""
 import math
