@@ -291,6 +291,35 @@ int tt_iga_solution_ranks(const tt_iga_solution *u, int ranks[2]);
 int tt_iga_residual(tt_iga_ctx *ctx, const tt_iga_system *s, const tt_iga_solution *u, int k,
                     double *rel_residual);
 
+/* Several right-hand sides as one block-TT solve (AMEn of Section 4.1.2 on the
+ * block system).  tt_iga_system_stack builds the block system of all n_rhs
+ * right-hand sides of s: the right-hand-side index k is merged into TT mode
+ * `mode` (0, 1 or 2; index i_d + m_d k, so that mode's size becomes n_rhs m_d),
+ * the operator is I (x) K (that core of K repeated on the diagonal blocks of
+ * the merged mode, no coupling across blocks) and its single load holds
+ * F_k / ||F_k|| in block k (TT ranks added,
+ * then rounded to relative accuracy eps; 0: 1e-14).  scales (host, n_rhs
+ * doubles, may be NULL) receives ||F_k||.  A solution of the block system
+ * (tt_iga_solve with rhs_index 0) is sliced by tt_iga_solution_unstack: block
+ * k times scale, the solution of right-hand side k of s (its TT ranks are the
+ * block solution's).  tt_iga_eval and tt_iga_l2_error reject block solutions. */
+int tt_iga_system_stack(tt_iga_ctx *ctx, const tt_iga_system *s, int mode, double eps, tt_iga_system **out,
+                        double *scales);
+int tt_iga_solution_unstack(tt_iga_ctx *ctx, const tt_iga_solution *ub, int k, double scale,
+                            tt_iga_solution **out);
+/* Every right-hand side of s by one block-TT solve: stack, solve the block
+ * system to relative residual opts->tol / sqrt(n_rhs) (the block residual is
+ * the root mean square of the per-right-hand-side relative residuals, so each
+ * of them meets opts->tol), unstack.  out (host array of n_rhs handles)
+ * receives the solutions, also on ERR_NOT_CONVERGED; rel_res (host, n_rhs, may
+ * be NULL) the exact per-right-hand-side relative residuals (-1 where the TT
+ * rank of F_k - K u_k would exceed 256); st the block solve's statistics.
+ * mode: the TT mode that carries the right-hand-side index (0, 1, 2; -1: 1,
+ * the middle mode, whose two neighbouring ranks then span the unions of the
+ * solutions' outer-mode subspaces).  opts->rhs_index is ignored. */
+int tt_iga_solve_block(tt_iga_ctx *ctx, const tt_iga_system *s, const tt_iga_solve_opts *opts, int mode,
+                       tt_iga_solution **out, tt_iga_stats *st, double *rel_res);
+
 /* Copy the solution's TT cores to host memory: out receives core 1
  * [1][m1][r1], core 2 [r1][m2][r2] and core 3 [r2][m3][1] back to back (FP64);
  * modes[3] (m_d = n_d - 2 with six Dirichlet faces, n_d - lo_d - hi_d in
@@ -314,22 +343,31 @@ int tt_iga_l2_error(tt_iga_ctx *ctx, const tt_iga_geom *g, const tt_iga_solution
 
 /* ------------------------------------------------------------ batching */
 
+/* How an instance's right-hand sides are solved: BLOCK, one block-TT solve of
+ * all of them (tt_iga_solve_block, right-hand-side index in the middle TT
+ * mode; each meets opts.tol); EACH, one AMEn solve per right-hand side. */
+enum { TT_IGA_RHS_BLOCK = 0, TT_IGA_RHS_EACH = 1 };
+
 /* One instance of a batch: geometry and discretisation, its right-hand sides
- * (host array of n_rhs descriptors, 1..8), the assembly rounding tolerance and
- * the solve options (rhs_index is ignored: every right-hand side is solved). */
+ * (host array of n_rhs descriptors, 1..8), the assembly rounding tolerance,
+ * the solve options (rhs_index is ignored: every right-hand side is solved)
+ * and rhs_solve (TT_IGA_RHS_BLOCK or TT_IGA_RHS_EACH; a single right-hand
+ * side is always solved by tt_iga_solve). */
 typedef struct {
   tt_iga_geom_desc geom;
   int n_rhs;
   const tt_iga_rhs_desc *rhs;
   double round_tol;
   tt_iga_solve_opts opts;
+  int rhs_solve;
 } tt_iga_batch_item;
 
 typedef struct {
   int status;                /* tt_iga_status of this instance */
-  int ranks[2];              /* solution ranks of its last right-hand side */
-  int sweeps;                /* AMEn sweeps summed over its right-hand sides */
-  double rel_residual_max;   /* worst exact relative residual over its right-hand sides */
+  int ranks[2];              /* solution ranks of its last right-hand side (BLOCK: of all) */
+  int sweeps;                /* AMEn sweeps summed over its solves */
+  double rel_residual_max;   /* worst exact relative residual over its right-hand sides
+                                (-1 where one was skipped for its TT rank) */
   long long dofs;            /* n1 n2 n3 times the number of right-hand sides */
   double ms_geometry, ms_assemble, ms_solve;  /* host wall clock per phase */
   double t_start_ms, t_end_ms;                /* start / end relative to the batch start */

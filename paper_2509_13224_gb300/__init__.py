@@ -22,6 +22,7 @@ OK, ERR_ARG, ERR_OOM, ERR_CUDA, ERR_NOT_CONVERGED, ERR_TIMEOUT, ERR_TOO_LARGE, E
 GEOM_BOX, GEOM_ANNULUS, GEOM_NURBS = 0, 1, 2
 RHS_MANUFACTURED, RHS_CONSTANT, RHS_RING_LOG = 0, 1, 2
 FP64, MIXED_FP32, MIXED_TF32 = 0, 1, 2
+RHS_BLOCK, RHS_EACH = 0, 1
 MAX_MODES = 8
 
 _c_double_p = ctypes.POINTER(ctypes.c_double)
@@ -70,7 +71,7 @@ class SolveOpts(ctypes.Structure):
 
 class BatchItem(ctypes.Structure):
     _fields_ = [("geom", GeomDesc), ("n_rhs", ctypes.c_int), ("rhs", ctypes.POINTER(RhsDesc)),
-                ("round_tol", ctypes.c_double), ("opts", SolveOpts)]
+                ("round_tol", ctypes.c_double), ("opts", SolveOpts), ("rhs_solve", ctypes.c_int)]
 
 
 class BatchResult(ctypes.Structure):
@@ -120,6 +121,11 @@ _SIGS = {
     "tt_iga_system_info": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_int * 2), ctypes.c_int, _vp,
                                           ctypes.POINTER(ctypes.c_int * 3)]),
     "tt_iga_solve": (ctypes.c_int, [_vp, _vp, ctypes.POINTER(SolveOpts), ctypes.POINTER(_vp), ctypes.POINTER(Stats)]),
+    "tt_iga_system_stack": (ctypes.c_int, [_vp, _vp, ctypes.c_int, ctypes.c_double, ctypes.POINTER(_vp),
+                                           _c_double_p]),
+    "tt_iga_solution_unstack": (ctypes.c_int, [_vp, _vp, ctypes.c_int, ctypes.c_double, ctypes.POINTER(_vp)]),
+    "tt_iga_solve_block": (ctypes.c_int, [_vp, _vp, ctypes.POINTER(SolveOpts), ctypes.c_int, ctypes.POINTER(_vp),
+                                          ctypes.POINTER(Stats), _c_double_p]),
     "tt_iga_solution_destroy": (None, [_vp]),
     "tt_iga_solution_ranks": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_int * 2)]),
     "tt_iga_residual": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int, _c_double_p]),
@@ -418,6 +424,39 @@ def tt_iga_solution_destroy(u):
     _lib.tt_iga_solution_destroy(u)
 
 
+def tt_iga_system_stack(ctx, s, mode=1, eps=0.0):
+    """Block system of all right-hand sides of s merged into TT mode `mode`; returns (handle, [||F_k||])."""
+    nrhs = tt_iga_system_info(s)["n_rhs"]
+    h = ctypes.c_void_p()
+    sc = (ctypes.c_double * nrhs)()
+    _check(ctx, _lib.tt_iga_system_stack(ctx, s, mode, eps, ctypes.byref(h), sc))
+    return h, list(sc)
+
+
+def tt_iga_solution_unstack(ctx, ub, k, scale):
+    h = ctypes.c_void_p()
+    _check(ctx, _lib.tt_iga_solution_unstack(ctx, ub, k, scale, ctypes.byref(h)))
+    return h
+
+
+def tt_iga_solve_block(ctx, s, opts, mode=-1, allow_not_converged=False):
+    """One block-TT solve of every right-hand side of s; returns ([solutions], stats, [rel. residuals])."""
+    nrhs = tt_iga_system_info(s)["n_rhs"]
+    hs = (_vp * nrhs)()
+    st = Stats()
+    rr = (ctypes.c_double * nrhs)()
+    allow = (ERR_NOT_CONVERGED,) if allow_not_converged else ()
+    code = _lib.tt_iga_solve_block(ctx, s, ctypes.byref(opts), mode, hs, ctypes.byref(st), rr)
+    sols = [ctypes.c_void_p(h) for h in hs]
+    if code != OK and code not in allow:
+        msg = tt_iga_last_error(ctx)
+        for h in sols:
+            if h.value:
+                _lib.tt_iga_solution_destroy(h)
+        raise TTIgaError(code, msg)
+    return sols, st.as_dict(), list(rr)
+
+
 def tt_iga_solution_ranks(u):
     r = (ctypes.c_int * 2)()
     _check(None, _lib.tt_iga_solution_ranks(u, ctypes.byref(r)))
@@ -491,8 +530,10 @@ def tt_iga_vector_entries(ctx, s, u, k, idx):
     return out
 
 
-def batch_items(instances, tol=1e-8, precision=FP64, cross_tol=1e-10, round_tol=1e-12, max_rank=0):
-    """BatchItem array from instance dicts (synthetic.random_instance); keeps the rhs arrays alive."""
+def batch_items(instances, tol=1e-8, precision=FP64, cross_tol=1e-10, round_tol=1e-12, max_rank=0,
+                rhs_solve=None):
+    """BatchItem array from instance dicts (synthetic.random_instance); keeps the rhs arrays alive.
+    rhs_solve: RHS_BLOCK (default) or RHS_EACH."""
     arr = (BatchItem * len(instances))()
     keep = []
     for k, inst in enumerate(instances):
@@ -504,6 +545,7 @@ def batch_items(instances, tol=1e-8, precision=FP64, cross_tol=1e-10, round_tol=
         arr[k].rhs = ctypes.cast(rh, ctypes.POINTER(RhsDesc))
         arr[k].round_tol = round_tol
         arr[k].opts = solve_opts(tol=tol, precision=precision)
+        arr[k].rhs_solve = RHS_BLOCK if rhs_solve is None else int(rhs_solve)
     return arr, keep
 
 

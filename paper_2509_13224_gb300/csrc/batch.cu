@@ -3,6 +3,8 @@
 // non-blocking stream and host thread, so the small kernels of different
 // instances overlap on the device.  Instances are started largest first
 // (by n1 n2 n3 times the number of right-hand sides) to shorten the tail.
+// The right-hand sides of an instance are solved as one block-TT solve
+// (tt_iga_solve_block) or one by one, as the item asks.
 // Each instance's arithmetic is independent of the others: no cross-instance
 // reductions or atomics, so a result is the same alone and in a batch.
 #include <algorithm>
@@ -19,7 +21,9 @@ int tt_iga_batch_solve(int device, int count, const tt_iga_batch_item *items, in
                        double *wall_ms) {
   if (count < 0 || (count > 0 && (!items || !results)) || lanes < 1 || lanes > 64) return TT_IGA_ERR_ARG;
   for (int i = 0; i < count; ++i)
-    if (items[i].n_rhs < 1 || items[i].n_rhs > 8 || !items[i].rhs) return TT_IGA_ERR_ARG;
+    if (items[i].n_rhs < 1 || items[i].n_rhs > 8 || !items[i].rhs ||
+        (items[i].rhs_solve != TT_IGA_RHS_BLOCK && items[i].rhs_solve != TT_IGA_RHS_EACH))
+      return TT_IGA_ERR_ARG;
   std::vector<int> order(count);
   for (int i = 0; i < count; ++i) order[i] = i;
   auto cost = [&](int i) {
@@ -59,7 +63,20 @@ int tt_iga_batch_solve(int device, int count, const tt_iga_batch_item *items, in
       if (st == TT_IGA_OK) st = tt_iga_assemble(ctx, g, it.rhs, it.n_rhs, it.round_tol, &s);
       auto tc = std::chrono::steady_clock::now();
       double worst = 0.0;
-      for (int k = 0; k < it.n_rhs && st == TT_IGA_OK; ++k) {
+      if (st == TT_IGA_OK && it.n_rhs > 1 && it.rhs_solve == TT_IGA_RHS_BLOCK) {
+        tt_iga_solution *us[8] = {};
+        double rr[8];
+        tt_iga_stats stats{};
+        st = tt_iga_solve_block(ctx, s, &it.opts, -1, us, &stats, rr);
+        for (int k = 0; k < it.n_rhs; ++k) {
+          worst = (worst < 0.0 || rr[k] < 0.0) ? -1.0 : std::max(worst, rr[k]);
+          tt_iga_solution_destroy(us[k]);
+        }
+        res.ranks[0] = stats.ranks[0];
+        res.ranks[1] = stats.ranks[1];
+        res.sweeps = stats.sweeps;
+      }
+      for (int k = 0; k < it.n_rhs && st == TT_IGA_OK && !(it.n_rhs > 1 && it.rhs_solve == TT_IGA_RHS_BLOCK); ++k) {
         tt_iga_solve_opts so = it.opts;
         so.rhs_index = k;
         tt_iga_solution *u = nullptr;

@@ -5,6 +5,7 @@
 
 #include "amen.cuh"
 #include "amen_ops.cuh"
+#include "block.cuh"
 #include "eval.cuh"
 #include "handles.cuh"
 #include "linalg.cuh"
@@ -381,12 +382,8 @@ int tt_iga_system_info(const tt_iga_system *s, int op_ranks[2], int n_rhs_max, i
 
 // --------------------------------------------------------------------- solve
 
-int tt_iga_solve(tt_iga_ctx *c, const tt_iga_system *s, const tt_iga_solve_opts *opts, tt_iga_solution **out,
-                 tt_iga_stats *st) {
-  if (!c || !s || !out) return TT_IGA_ERR_ARG;
-  *out = nullptr;
-  API_TRY
-  if (s->ctx != c) fail(TT_IGA_ERR_STATE, "solve: system belongs to another context");
+// Solve options with the defaults of tt_iga_solve_opts filled in.
+static tt_iga_solve_opts solve_defaults(const tt_iga_solve_opts *opts) {
   tt_iga_solve_opts o{};
   if (opts) o = *opts;
   if (o.tol <= 0) o.tol = 1e-8;
@@ -398,9 +395,21 @@ int tt_iga_solve(tt_iga_ctx *c, const tt_iga_system *s, const tt_iga_solve_opts 
   if (o.local_maxit <= 0) o.local_maxit = 500;
   TTI_CHECK_ARG(o.precision == TT_IGA_FP64 || o.precision == TT_IGA_MIXED_FP32,
                 "solve: precision %d not available (FP64 and MIXED_FP32 are built)", o.precision);
+  return o;
+}
+
+int tt_iga_solve(tt_iga_ctx *c, const tt_iga_system *s, const tt_iga_solve_opts *opts, tt_iga_solution **out,
+                 tt_iga_stats *st) {
+  if (!c || !s || !out) return TT_IGA_ERR_ARG;
+  *out = nullptr;
+  API_TRY
+  if (s->ctx != c) fail(TT_IGA_ERR_STATE, "solve: system belongs to another context");
+  const tt_iga_solve_opts o = solve_defaults(opts);
   TTI_CHECK_ARG(o.rhs_index >= 0 && o.rhs_index < (int)s->F.size(), "solve: rhs_index %d out of range", o.rhs_index);
   auto *U = new tt_iga_solution();
   U->bl = s->bl;
+  U->stacked = s->stacked;
+  U->stack_mode = s->stack_mode;
   std::unique_ptr<tt_iga_solution> guard(U);
   int status = amen_solve(c, s, o, U, st);
   const int ds = device_status(c);
@@ -415,6 +424,75 @@ int tt_iga_solve(tt_iga_ctx *c, const tt_iga_system *s, const tt_iga_solve_opts 
 }
 
 void tt_iga_solution_destroy(tt_iga_solution *u) { delete u; }
+
+int tt_iga_system_stack(tt_iga_ctx *c, const tt_iga_system *s, int mode, double eps, tt_iga_system **out,
+                        double *scales) {
+  if (!c || !s || !out) return TT_IGA_ERR_ARG;
+  *out = nullptr;
+  API_TRY
+  if (s->ctx != c) fail(TT_IGA_ERR_STATE, "stack: system belongs to another context");
+  auto *B = new tt_iga_system();
+  std::unique_ptr<tt_iga_system> guard(B);
+  std::vector<double> sc;
+  stack_system(c, s, mode, eps > 0 ? eps : 1e-14, B, sc);
+  if (scales) std::copy(sc.begin(), sc.end(), scales);
+  *out = guard.release();
+  return TT_IGA_OK;
+  API_CATCH(c)
+}
+
+int tt_iga_solution_unstack(tt_iga_ctx *c, const tt_iga_solution *ub, int k, double scale, tt_iga_solution **out) {
+  if (!c || !ub || !out) return TT_IGA_ERR_ARG;
+  *out = nullptr;
+  API_TRY
+  TTI_CHECK_ARG(std::isfinite(scale), "unstack: scale is not finite");
+  auto *U = new tt_iga_solution();
+  std::unique_ptr<tt_iga_solution> guard(U);
+  unstack_solution(c, ub, k, scale, U);
+  *out = guard.release();
+  return TT_IGA_OK;
+  API_CATCH(c)
+}
+
+int tt_iga_solve_block(tt_iga_ctx *c, const tt_iga_system *s, const tt_iga_solve_opts *opts, int mode,
+                       tt_iga_solution **out, tt_iga_stats *st, double *rel_res) {
+  if (!c || !s || !out) return TT_IGA_ERR_ARG;
+  const int nb = (int)s->F.size();
+  for (int k = 0; k < nb; ++k) out[k] = nullptr;
+  API_TRY
+  if (s->ctx != c) fail(TT_IGA_ERR_STATE, "solve_block: system belongs to another context");
+  tt_iga_solve_opts o = solve_defaults(opts);
+  o.rhs_index = 0;
+  o.tol /= sqrt((double)nb);  // block residual = rms of the per-right-hand-side relative residuals
+  tt_iga_system B;
+  std::vector<double> scale;
+  if (mode < 0) mode = kDefaultStackMode;
+  stack_system(c, s, mode, 1e-3 * o.tol, &B, scale);
+  tt_iga_solution ub;
+  ub.bl = s->bl;
+  ub.stacked = nb;
+  ub.stack_mode = mode;
+  int status = amen_solve(c, &B, o, &ub, st);
+  const int ds = device_status(c);
+  std::vector<std::unique_ptr<tt_iga_solution>> sols(nb);
+  for (int k = 0; k < nb; ++k) {
+    sols[k].reset(new tt_iga_solution());
+    unstack_solution(c, &ub, k, scale[k], sols[k].get());
+    if (rel_res) {
+      rel_res[k] = -1.0;
+      if (s->K.r[1] * ub.u.r[1] + s->F[k].r[1] <= 256 && s->K.r[2] * ub.u.r[2] + s->F[k].r[2] <= 256)
+        rel_res[k] = exact_residual(c, s, sols[k].get(), k);
+    }
+  }
+  for (int k = 0; k < nb; ++k) out[k] = sols[k].release();
+  if (ds != TT_IGA_OK && status == TT_IGA_OK) {
+    c->last_error = "solve_block: device-side breakdown flag raised";
+    return ds;
+  }
+  if (status != TT_IGA_OK) c->last_error = "solve_block: AMEn did not reach the tolerance within max_sweeps";
+  return status;
+  API_CATCH(c)
+}
 
 int tt_iga_solution_ranks(const tt_iga_solution *u, int ranks[2]) {
   if (!u || !ranks) return TT_IGA_ERR_ARG;
@@ -460,6 +538,7 @@ int tt_iga_solution_cores(tt_iga_ctx *c, const tt_iga_solution *u, double *out, 
 int tt_iga_eval(tt_iga_ctx *c, const tt_iga_solution *u, int m, const double *xi, double *u_out) {
   if (!c || !u || m < 0 || (m > 0 && (!xi || !u_out))) return TT_IGA_ERR_ARG;
   API_TRY
+  TTI_CHECK_ARG(u->stacked == 1, "eval: block solution (slice it with tt_iga_solution_unstack first)");
   eval_points(c, u, m, xi, u_out);
   c->sync();
   return TT_IGA_OK;
@@ -470,6 +549,7 @@ int tt_iga_l2_error(tt_iga_ctx *c, const tt_iga_geom *g, const tt_iga_solution *
                     double *rel) {
   if (!c || !g || !u || !rhs || !rel) return TT_IGA_ERR_ARG;
   API_TRY
+  TTI_CHECK_ARG(u->stacked == 1, "l2_error: block solution (slice it with tt_iga_solution_unstack first)");
   TTI_CHECK_ARG(rhs->kind == TT_IGA_RHS_MANUFACTURED || rhs->kind == TT_IGA_RHS_RING_LOG,
                 "l2_error: needs a right-hand side with an exact solution (MANUFACTURED or RING_LOG)");
   TTI_CHECK_ARG(g->desc.kind != TT_IGA_GEOM_NURBS, "l2_error: no exact solution is defined on a NURBS patch");

@@ -42,6 +42,8 @@ struct tt_iga_system {
   ttiga::TT3 K;
   std::vector<ttiga::TT3> F;
   std::vector<double> F_norm;
+  int stacked = 1;     // > 1: block system of that many right-hand sides merged into one mode
+  int stack_mode = 0;  // the mode (0, 1, 2) that carries the right-hand-side index
 };
 
 struct tt_iga_solution {
@@ -50,6 +52,8 @@ struct tt_iga_solution {
   int p = 0;
   ttiga::BoundaryLayout bl;
   ttiga::TT3 u;
+  int stacked = 1;     // > 1: solution of a block system (slice it with tt_iga_solution_unstack)
+  int stack_mode = 0;
 };
 
 namespace ttiga {
