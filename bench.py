@@ -39,9 +39,9 @@ FP64_ALU_PEAK_TFLOPS = 1.258  # 152 SMs x 2 FP64 FMA/clk x 2 FLOP x 2.07 GHz (no
 # DRAM bytes (read + write) per launch of the timed kernel, mean over the six launches of
 # one step of this workload, from one ncu capture whose summary is committed with the
 # profiles.  Valid only for the sources it was taken from: reported as null once they change.
-PCG_TRAFFIC_BYTES = 374528
+PCG_TRAFFIC_BYTES = 395989
 PCG_TRAFFIC_SOURCES = ("pcg_fused.cu", "pcg_fused.cuh", "bbprec.cu", "bbprec.cuh", "amen.cu")
-PCG_TRAFFIC_SHA256 = "f9210eae60659b1c119dc0b8659064bd318bfaf8a702cb68819d5ff6246f8177"
+PCG_TRAFFIC_SHA256 = "aec15915d009da7984759da06f78fc14b9a65d6e67b597fb95882190e1759782"
 
 
 def pcg_traffic():

@@ -464,8 +464,13 @@ struct Amen {
     rho = (int)std::min<long long>(rho, std::max<long long>(0, right_cap - r));
     if (o.max_rank > 0) rho = std::min(rho, std::max(0, o.max_rank - r));
     const int rn = r + rho;
-    DBuf Ue(c, (size_t)rows * rn * sizeof(double));
-    copy2d(c, Ue.d(), rn, QU.d(), b, rows, r);
+    // new core Qe = [QU[:, :r] | Qz]: the enrichment columns E (residual projected on z's
+    // right interface) are orthogonalised against the orthonormal QU[:, :r] by two classical
+    // Gram-Schmidt passes, and only these rho columns go through a QR.  In the factor
+    // Re of [QU[:, :r] | E] = Qe Re the first r columns are [I; 0], so the next core takes
+    // C = Re[:, :r] SVt[:r] = [SVt[:r]; 0].
+    DBuf Qe(c, (size_t)rows * rn * sizeof(double));
+    copy2d(c, Qe.d(), rn, QU.d(), b, rows, r);
     if (rho > 0) {
       const int zr = z.r[k + 1];
       DBuf ez(c, (size_t)rows * zr * sizeof(double)), bz(c, (size_t)rows * zr * sizeof(double));
@@ -473,13 +478,19 @@ struct Amen {
       apply_local<double>(c, w64, PhiL[k].d(), a, a, A[k], A[k].A, PhiRz[k].d(), zr, b, xt.d(), bz.d());
       k_sub<<<grid1d((long long)rows * zr, 256), 256, 0, c->stream>>>(ez.d(), bz.d(), (long long)rows * zr);
       TTI_LAUNCH();
-      copy2d(c, Ue.d() + r, rn, bz.d(), zr, rows, rho);
+      DBuf E(c, (size_t)rows * rho * sizeof(double)), W(c, (size_t)r * rho * sizeof(double));
+      copy2d(c, E.d(), rho, bz.d(), zr, rows, rho);
+      for (int pass = 0; pass < 2; ++pass) {
+        gemm<double>(c, true, false, r, rho, rows, 1.0, QU.d(), b, 0, E.d(), rho, 0, 0.0, W.d(), rho, 0, 1);
+        gemm<double>(c, false, false, rows, rho, r, -1.0, QU.d(), b, 0, W.d(), rho, 0, 1.0, E.d(), rho, 0, 1);
+      }
+      DBuf Qz(c, (size_t)rows * rho * sizeof(double)), Rz(c, (size_t)rho * rho * sizeof(double));
+      qr(c, rows, rho, E.d(), rho, Qz.d(), Rz.d());
+      copy2d(c, Qe.d() + r, rn, Qz.d(), rho, rows, rho);
     }
-    DBuf Qe(c, (size_t)rows * rn * sizeof(double)), Re(c, (size_t)rn * rn * sizeof(double));
-    qr(c, rows, rn, Ue.d(), rn, Qe.d(), Re.d());
-    // C = Re[:, :r] SVt[:r]  -> rn x b ; next core <- C * core_{k+1}
     DBuf C(c, (size_t)rn * b * sizeof(double));
-    gemm<double>(c, false, false, rn, b, r, 1.0, Re.d(), rn, 0, SVt.d(), b, 0, 0.0, C.d(), b, 0, 1);
+    if (rho > 0) c->zero(C.get(), (size_t)rn * b * sizeof(double));
+    copy2d(c, C.d(), b, SVt.d(), b, r, b);
     const long long cols = (long long)n(k + 1) * u.r[k + 2];
     DBuf next(c, (size_t)rn * cols * sizeof(double));
     gemm<double>(c, false, false, rn, (int)cols, b, 1.0, C.d(), b, 0, u.core[k + 1].d(), cols, 0, 0.0, next.d(), cols,

@@ -116,15 +116,120 @@ __device__ __forceinline__ void trace_mark(unsigned long long *trace, int cap, i
   ++slot;
 }
 
+// Banded triangular solves of one band system by one warp, in FP32 out of
+// shared memory.  The forward solve y_i = (r_i - sum_k L_i[k] y_{i-PB+k}) d_i
+// (L_i[k] = L(i, i-PB+k), d_i the reciprocal diagonal) is an affine
+// recurrence in the state s_i = (y_{i-PB+1}, .., y_i): s_i = M_i s_{i-1} + u_i.
+// The rows are cut into 32 contiguous chunks, one per lane; each lane composes
+// the maps of its chunk, a Hillis-Steele scan over the lanes composes the chunk
+// maps (5 shuffle rounds), and each lane reruns its chunk from its true start
+// state.  The backward solve z_i = (y_i - sum_d L(i+d, i) z_{i+d}) d_i is the
+// same recurrence with the rows taken from the bottom.  The dependent chain is
+// about n/32 + 5 compositions instead of n rows.  A preconditioner needs no
+// accuracy; the recurrences of a banded SPD factor do not grow, so FP32 suffices.
+template <int PB>
+__device__ __forceinline__ void warp_band_sweep(const float *__restrict__ Ls, float *__restrict__ v, int n, int lane,
+                                                bool backward) {
+  const int c = (n + 31) >> 5;
+  const int q = backward ? 31 - lane : lane;  // chunk index of this lane
+  const int lo = min(n, q * c), hi = min(n, lo + c);
+  // coefficient of state component k for row i; the reciprocal diagonal is Ls[i (PB+1) + PB]
+  auto coef = [&](int i, int k) -> float {
+    if (!backward) return Ls[i * (PB + 1) + k];
+    const int row = i + PB - k;  // L(i + d, i) with d = PB - k
+    return row < n ? Ls[row * (PB + 1) + k] : 0.f;
+  };
+  float M[PB][PB], u[PB];
+#pragma unroll
+  for (int j = 0; j < PB; ++j) {
+#pragma unroll
+    for (int k = 0; k < PB; ++k) M[j][k] = (j == k) ? 1.f : 0.f;
+    u[j] = 0.f;
+  }
+  for (int t = 0; t < hi - lo; ++t) {
+    const int i = backward ? hi - 1 - t : lo + t;
+    const float d = Ls[i * (PB + 1) + PB];
+    float Mn[PB], un = v[i];
+#pragma unroll
+    for (int k = 0; k < PB; ++k) Mn[k] = 0.f;
+#pragma unroll
+    for (int j = 0; j < PB; ++j) {
+      const float lj = coef(i, j);
+#pragma unroll
+      for (int k = 0; k < PB; ++k) Mn[k] -= lj * M[j][k];
+      un -= lj * u[j];
+    }
+#pragma unroll
+    for (int j = 0; j + 1 < PB; ++j) {
+#pragma unroll
+      for (int k = 0; k < PB; ++k) M[j][k] = M[j + 1][k];
+      u[j] = u[j + 1];
+    }
+#pragma unroll
+    for (int k = 0; k < PB; ++k) M[PB - 1][k] = Mn[k] * d;
+    u[PB - 1] = un * d;
+  }
+  // inclusive scan: (M, u) <- (M, u) o (M', u') of the lane `off` below (earlier rows)
+#pragma unroll
+  for (int off = 1; off < 32; off <<= 1) {
+    float Mp[PB][PB], up[PB];
+#pragma unroll
+    for (int j = 0; j < PB; ++j) {
+#pragma unroll
+      for (int k = 0; k < PB; ++k) Mp[j][k] = __shfl_up_sync(0xffffffffu, M[j][k], off);
+      up[j] = __shfl_up_sync(0xffffffffu, u[j], off);
+    }
+    if (lane >= off) {
+      float Mc[PB][PB], uc[PB];
+#pragma unroll
+      for (int j = 0; j < PB; ++j) {
+        float a = u[j];
+#pragma unroll
+        for (int k = 0; k < PB; ++k) {
+          float m = 0.f;
+#pragma unroll
+          for (int l = 0; l < PB; ++l) m += M[j][l] * Mp[l][k];
+          Mc[j][k] = m;
+          a += M[j][k] * up[k];
+        }
+        uc[j] = a;
+      }
+#pragma unroll
+      for (int j = 0; j < PB; ++j) {
+#pragma unroll
+        for (int k = 0; k < PB; ++k) M[j][k] = Mc[j][k];
+        u[j] = uc[j];
+      }
+    }
+  }
+  // start state of this chunk: the composed map of the chunks before it applied to 0
+  float st[PB];
+#pragma unroll
+  for (int j = 0; j < PB; ++j) {
+    const float w = __shfl_up_sync(0xffffffffu, u[j], 1);
+    st[j] = lane == 0 ? 0.f : w;
+  }
+  for (int t = 0; t < hi - lo; ++t) {
+    const int i = backward ? hi - 1 - t : lo + t;
+    float sv = v[i];
+#pragma unroll
+    for (int k = 0; k < PB; ++k) sv -= coef(i, k) * st[k];
+    const float y = sv * Ls[i * (PB + 1) + PB];
+    v[i] = y;
+#pragma unroll
+    for (int k = 0; k + 1 < PB; ++k) st[k] = st[k + 1];
+    st[PB - 1] = y;
+  }
+}
+
 // The (alpha, beta) band systems of the preconditioner, `slots` at a time per
-// CTA.  All threads of the CTA gather each system's factor rows (FP32) and its
-// entries of r, q, p, x, apply x += alpha p, r -= alpha q (or x = 0, r = b when
-// init) in parallel, and stage r in shared memory; lane 0 of warp w then runs
-// system w's forward / backward substitution in FP32 out of shared memory
-// (the only sequential part; on GB300 a dependent FP64 operation costs about
-// 64 cycles against 4.5 for FP32, and a preconditioner needs no accuracy);
+// CTA.  All threads of the CTA apply x += alpha p, r -= alpha q (or x = 0,
+// r = b when init) to each system's entries in parallel and stage r in shared
+// memory; warp w then solves system w (warp_band_sweep, forward and backward);
 // finally the CTA scatters z in the working precision and accumulates <r, r>
-// and <r, z> in FP64 with every thread on its own chain.
+// and <r, z> in FP64 with every thread on its own chain.  The FP32 factor rows
+// of the CTA's systems are gathered into shared memory once, at init, when
+// every system has its own slot in the grid (a.resident), else per round.
 // Shared layout per slot: L[n][PB+1] (float), r[n] (float).
 template <typename T, int PB>
 __device__ __forceinline__ void band_systems(const PcgArgs<T> &a, const T *__restrict__ pcur, double alpha, bool init,
@@ -137,10 +242,12 @@ __device__ __forceinline__ void band_systems(const PcgArgs<T> &a, const T *__res
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   for (long long t0 = (long long)blockIdx.x * slots; t0 < npair; t0 += (long long)gridDim.x * slots) {
     const int cnt = (int)((npair - t0 < slots) ? (npair - t0) : slots);
-    for (int e = threadIdx.x; e < cnt * n * (PB + 1); e += blockDim.x) {
-      const int s_ = e / (n * (PB + 1)), rem = e - s_ * (n * (PB + 1));
-      const int i = rem / (PB + 1), k = rem - i * (PB + 1);
-      esm[s_ * per + rem] = a.Lf[((long long)i * (PB + 1) + k) * npair + t0 + s_];
+    if (init || !a.resident) {
+      for (int e = threadIdx.x; e < cnt * n * (PB + 1); e += blockDim.x) {
+        const int s_ = e / (n * (PB + 1)), rem = e - s_ * (n * (PB + 1));
+        const int i = rem / (PB + 1), k = rem - i * (PB + 1);
+        esm[s_ * per + rem] = a.Lf[((long long)i * (PB + 1) + k) * npair + t0 + s_];
+      }
     }
     double rr_th = 0.0;
     for (int e = threadIdx.x; e < cnt * n; e += blockDim.x) {
@@ -161,36 +268,12 @@ __device__ __forceinline__ void band_systems(const PcgArgs<T> &a, const T *__res
     }
     rr_out += rr_th;
     __syncthreads();
-    if (warp < cnt && lane == 0) {
+    if (warp < cnt) {
       const float *Ls = esm + warp * per;
-      float *rs = esm + warp * per + n * (PB + 1);  // overwritten by z
-      float w[PB];
-#pragma unroll
-      for (int k = 0; k < PB; ++k) w[k] = 0.f;
-      for (int i = 0; i < n; ++i) {
-        const float *Li = Ls + i * (PB + 1);
-        float sv = rs[i];
-#pragma unroll
-        for (int k = 0; k < PB; ++k) sv -= Li[k] * w[k];
-        const float y = sv * Li[PB];
-        rs[i] = y;
-#pragma unroll
-        for (int k = 0; k + 1 < PB; ++k) w[k] = w[k + 1];
-        w[PB - 1] = y;
-      }
-#pragma unroll
-      for (int k = 0; k < PB; ++k) w[k] = 0.f;  // w[d-1] = z_{i+d}
-      for (int i = n - 1; i >= 0; --i) {
-        float sv = rs[i];
-#pragma unroll
-        for (int d = 1; d <= PB; ++d)
-          if (i + d < n) sv -= Ls[(i + d) * (PB + 1) + (PB - d)] * w[d - 1];
-        const float zi = sv * Ls[i * (PB + 1) + PB];
-        rs[i] = zi;
-#pragma unroll
-        for (int d = PB - 1; d > 0; --d) w[d] = w[d - 1];
-        w[0] = zi;
-      }
+      float *rs = esm + warp * per + n * (PB + 1);  // r, overwritten by y, then by z
+      warp_band_sweep<PB>(Ls, rs, n, lane, false);
+      __syncwarp();
+      warp_band_sweep<PB>(Ls, rs, n, lane, true);
     }
     __syncthreads();
     double rz_th = 0.0;
@@ -745,6 +828,16 @@ template <typename T> int pcg_fused_grid(Ctx *c, PcgArgs<T> &a) {
   const long long npair = a.edge ? 1 : (long long)a.rl * a.rr;
   long long g = std::max(nslab, (npair + a.slots - 1) / a.slots);
   g = std::max<long long>(1, std::min(g, cap));
+  if (!a.edge) {
+    // spread the band systems over the grid the dense phase needs anyway: fewer per
+    // CTA shortens the gathers and scatters; with one slot each, the factors stay
+    // resident in shared memory for the whole solve
+    a.slots = (int)std::min<long long>(a.slots, (npair + g - 1) / g);
+    a.resident = (long long)a.slots * g >= npair ? 1 : 0;
+    a.smem = (int)((size_t)a.slots * a.n * (a.p + 2) * sizeof(float));
+  } else {
+    a.resident = 0;
+  }
   a.t1_stride = (long long)a.rl * (S + 2 * a.p) * a.rr * a.Rr;
   a.t2_stride = (long long)a.Rl * a.rl * S * a.rr;
   return (int)g;

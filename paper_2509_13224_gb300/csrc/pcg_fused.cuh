@@ -28,6 +28,7 @@ template <typename T> struct PcgArgs {
   double tol2;    // stop when ||b - B x||^2 <= tol2
   int maxit;
   int slots;      // band systems staged per CTA at a time (set by pcg_fused_grid)
+  int resident;   // 1: every band system has its own slot, factors gathered once (set by pcg_fused_grid)
   int slab;       // mode rows per slab of the dense phase (set by pcg_fused_grid)
   long long t1_stride, t2_stride;  // per-CTA scratch sizes in elements (set by pcg_fused_grid)
   int smem;       // dynamic shared memory bytes (set by pcg_fused_grid)
