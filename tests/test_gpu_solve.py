@@ -43,6 +43,10 @@ def _tt_solve(tt, ctx, geo, n, p, modes, precision, tol):
     (synthetic.TWISTED_ANNULUS, 10, 2, []),
     (synthetic.TWISTED_ANNULUS, 9, 3, [(0.2, (1.0, 1.0, 0.0), 0.7)]),
     (synthetic.QUARTER_CYLINDER, 16, 2, []),
+    # degrees 4 and 5: the band block-Jacobi systems (interface blocks above 8) run the
+    # warp-scan triangular solves with bandwidths 4 and 5
+    (synthetic.TWISTED_ANNULUS, 12, 4, [(0.2, (1.0, 1.0, 0.0), 0.7)]),
+    (synthetic.TWISTED_ANNULUS, 11, 5, [(0.2, (1.0, 1.0, 0.0), 0.7)]),
 ])
 def test_fp64_solution_matches_oracle(tt, ctx, geo, n, p, modes):
     from oracle.iga import to_flat
