@@ -139,6 +139,8 @@ struct Amen {
   int trunc_hint[2] = {0, 0};  // rank chosen by the last truncation of cores 0 and 1
   // scratch scalars on the device: [0] rz, [1] pq, [2] rz_new, [8..] partials
   DBuf scal;
+  // fork / join events of the preconditioner build on a helper stream (created on first use)
+  cudaEvent_t ev_in = nullptr, ev_out = nullptr;
 
   Amen(Ctx *c_, const tt_iga_system *s, const tt_iga_solve_opts &opts)
       : c(c_), S(s), F(s->F[opts.rhs_index]), Fnorm(s->F_norm[opts.rhs_index]), o(opts), w64{c_}, w32{c_} {
@@ -159,6 +161,13 @@ struct Amen {
       }
     }
   }
+
+  ~Amen() {
+    if (ev_in) cudaEventDestroy(ev_in);
+    if (ev_out) cudaEventDestroy(ev_out);
+  }
+  Amen(const Amen &) = delete;
+  Amen &operator=(const Amen &) = delete;
 
   int rl(int k) const { return u.r[k]; }
   int rr(int k) const { return u.r[k + 1]; }
@@ -316,19 +325,30 @@ struct Amen {
                      bool *checked = nullptr) {
     const long long N = (long long)rl(k) * n(k) * rr(k);
     DBuf rbuf(c, N * sizeof(double));
-    const double res0 = residual64(k, rhs, x, rbuf.d());
-    if (checked && res0 <= check_below) {
-      *checked = true;
-      return res0;
-    }
-    if (res0 <= tol_abs) return res0;
-    const int maxit = o.local_maxit;
     const size_t Lsz = (size_t)n(k) * (S->p + 1) * rl(k) * rr(k);
     // Small interface blocks (m = rl rr <= 8): exact block-band preconditioner.
     // Otherwise band block-Jacobi over the interface pairs.
     const bool edge = bb_eligible(rl(k) * rr(k), n(k), S->p);
     BBPrec bb;
     DBuf L;
+    // The preconditioner does not depend on the initial residual: it is built on a
+    // helper stream while this stream evaluates that residual (whose norm the host
+    // waits for); this stream joins the helper before anything uses or frees it.
+    // Only while this is the one live context: several contexts (batch lanes, a
+    // server's lanes) already overlap their work, and the extra stream and events
+    // of every local solve then cost more than they hide.  Sequential too with a
+    // caller-supplied allocator, whose streams helpers must not touch, and under
+    // the verbose stage timers.
+    Ctx *const parent = c;
+    Ctx *hb = (c->alloc_fn || o.verbose >= 2 || g_live_contexts.load(std::memory_order_relaxed) > 1) ? c : c->sub(0);
+    if (hb != parent) {
+      if (!ev_in) {
+        TTI_CUDA(cudaEventCreateWithFlags(&ev_in, cudaEventDisableTiming));
+        TTI_CUDA(cudaEventCreateWithFlags(&ev_out, cudaEventDisableTiming));
+      }
+      TTI_CUDA(cudaEventRecord(ev_in, parent->stream));
+      TTI_CUDA(cudaStreamWaitEvent(hb->stream, ev_in, 0));
+    }
     if (edge) {
       cudaEvent_t ev[2] = {nullptr, nullptr};
       DBuf clk;
@@ -338,7 +358,7 @@ struct Amen {
         TTI_CUDA(cudaEventCreate(&ev[1]));
         TTI_CUDA(cudaEventRecord(ev[0], c->stream));
       }
-      bb_prec_build(c, PhiL[k].d(), rl(k), A[k], PhiR[k].d(), rr(k), bb, clk.as<unsigned long long>());
+      bb_prec_build(hb, PhiL[k].d(), rl(k), A[k], PhiR[k].d(), rr(k), bb, clk.as<unsigned long long>());
       if (o.verbose >= 2) {
         float ms = 0.f;
         unsigned long long ck[3];
@@ -353,9 +373,30 @@ struct Amen {
         cudaEventDestroy(ev[1]);
       }
     } else {
-      L = DBuf(c, Lsz * sizeof(float));
-      precond_build<float>(c, PhiL[k].d(), rl(k), A[k], PhiR[k].d(), rr(k), L.as<float>());
+      L = DBuf(hb, Lsz * sizeof(float));
+      precond_build<float>(hb, PhiL[k].d(), rl(k), A[k], PhiR[k].d(), rr(k), L.as<float>());
     }
+    if (hb != parent) {
+      TTI_CUDA(cudaEventRecord(ev_out, hb->stream));
+      L.rehome(parent);
+      bb.Linv.rehome(parent);
+      bb.G.rehome(parent);
+      bb.H.rehome(parent);
+    }
+    double res0;
+    try {
+      res0 = residual64(k, rhs, x, rbuf.d());
+    } catch (...) {
+      if (hb != parent) cudaStreamWaitEvent(parent->stream, ev_out, 0);
+      throw;
+    }
+    if (hb != parent) TTI_CUDA(cudaStreamWaitEvent(parent->stream, ev_out, 0));
+    if (checked && res0 <= check_below) {
+      *checked = true;
+      return res0;
+    }
+    if (res0 <= tol_abs) return res0;
+    const int maxit = o.local_maxit;
     const BBPrec *bbp = edge ? &bb : nullptr;
     if (o.precision == TT_IGA_FP64) {
       // preconditioner factors in FP32 (see pcg_fused.cu, bbprec.cu)

@@ -13,6 +13,7 @@
 
 namespace ttiga {
 std::atomic<unsigned long long> g_launches{0};
+std::atomic<int> g_live_contexts{0};
 
 // Read and clear the device status word; map it to a status code.
 static int device_status(Ctx *c) {
@@ -95,6 +96,7 @@ int tt_iga_ctx_create(tt_iga_ctx **out, const tt_iga_ctx_opts *o) {
   TTI_CUDA(cudaMemset(c->dstatus, 0, 64));
   TTI_CUDA(cudaMalloc(&c->dscratch, Ctx::kScratchDoubles * sizeof(double)));
   *out = c;
+  g_live_contexts.fetch_add(1, std::memory_order_relaxed);
   return TT_IGA_OK;
   }
   catch (const ttiga::Error &e) {
@@ -106,6 +108,7 @@ int tt_iga_ctx_create(tt_iga_ctx **out, const tt_iga_ctx_opts *o) {
 
 void tt_iga_ctx_destroy(tt_iga_ctx *c) {
   if (!c) return;
+  g_live_contexts.fetch_sub(1, std::memory_order_relaxed);
   cudaStreamSynchronize(c->stream);
   c->release_subs();
   if (c->dstatus) cudaFree(c->dstatus);

@@ -45,6 +45,8 @@ struct Error : std::runtime_error {
 
 // Kernel launches issued by the library (process-wide), for launch accounting.
 extern std::atomic<unsigned long long> g_launches;
+// Contexts created by tt_iga_ctx_create and not yet destroyed (helpers not counted).
+extern std::atomic<int> g_live_contexts;
 #define TTI_LAUNCH()                                                 \
   do {                                                               \
     ::ttiga::g_launches.fetch_add(1, std::memory_order_relaxed);     \
