@@ -4,10 +4,9 @@
 // preconditioners, the TT sums and the rounding all apply unchanged: the
 // operator is I (x) K, i.e. that core of K repeated on the diagonal blocks of
 // the merged mode, and the block solution carries all solutions in one TT
-// whose ranks span all of them.  The
-// interfaces, the local operators and their preconditioner factors are
-// built once per step for all right-hand sides, and every local PCG works on
-// all of them at once.
+// whose ranks span all of them.  The interfaces, the local operators and
+// their preconditioner factors are built once per step for all right-hand
+// sides, and every local PCG works on all of them at once.
 #include <algorithm>
 #include <cmath>
 

@@ -48,11 +48,6 @@ static void embed(Ctx *c, double *dst, int RA, int m, int RB, const double *src,
   TTI_LAUNCH();
 }
 
-void tt_embed(Ctx *c, double *dst, int RA, int m, int RB, const double *src, int ra, int rb, int oa, int ob,
-              double s) {
-  embed(c, dst, RA, m, RB, src, ra, rb, oa, ob, s);
-}
-
 void tt_copy(Ctx *c, const TT3 &x, TT3 &y) {
   for (int k = 0; k < 3; ++k) y.m[k] = x.m[k];
   for (int k = 0; k < 4; ++k) y.r[k] = x.r[k];

@@ -4,9 +4,6 @@
 
 namespace ttiga {
 
-// dst[RA][m][RB] block at rank offsets (oa, ob) = s * src[ra][m][rb] (the rest of dst untouched).
-void tt_embed(Ctx *c, double *dst, int RA, int m, int RB, const double *src, int ra, int rb, int oa, int ob,
-              double s);
 // Deep copy.
 void tt_copy(Ctx *c, const TT3 &x, TT3 &y);
 // y = a x + b y as a TT of rank r_x + r_y (block cores); a is applied to core 1.
