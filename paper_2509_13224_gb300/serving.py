@@ -53,11 +53,15 @@ class Server:
     """lanes: concurrent solves; budget_bytes: device memory allowed for admitted requests."""
 
     def __init__(self, device=0, lanes=4, budget_bytes=None, precision_policy="auto", keep_cores=False,
-                 cross_tol=1e-10, round_tol=1e-12):
-        import torch
+                 cross_tol=1e-10, round_tol=1e-12, runner=None):
+        """runner: None (each request is solved by libtt_iga.so on the lane's context) or a
+        callable runner(request, t0) -> record with the keys of _run_one, for driving the
+        scheduler without a GPU."""
         self.device = device
         self.lanes = int(lanes)
+        self.runner = runner
         if budget_bytes is None:
+            import torch
             free, _ = torch.cuda.mem_get_info(device)
             budget_bytes = int(0.8 * free)
         self.budget = int(budget_bytes)
@@ -107,7 +111,6 @@ class Server:
     def serve(self, requests, realtime=True):
         """Run an open-loop session; requests carry arrival times (s from the session start).
         Returns (records in completion order, summary dict)."""
-        import torch
         pending = sorted(requests, key=lambda r: r.arrival)
         arrived = queue.Queue()
         records = []
@@ -146,21 +149,25 @@ class Server:
                     self._cv.wait(timeout=0.002)
 
         def lane():
-            torch.cuda.set_device(self.device)
-            ctx = tt_iga_ctx_create(None, self.device)
+            ctx = None
+            if self.runner is None:
+                import torch
+                torch.cuda.set_device(self.device)
+                ctx = tt_iga_ctx_create(None, self.device)
             try:
                 while True:
                     req, need = admit()
                     if req is None:
                         return
-                    rec = self._run_one(ctx, req, t0)
+                    rec = self._run_one(ctx, req, t0) if self.runner is None else self.runner(req, t0)
                     with self._cv:
                         self.in_use -= need
                         self._cv.notify_all()
                     with lock:
                         records.append(rec)
             finally:
-                tt_iga_ctx_destroy(ctx)
+                if ctx is not None:
+                    tt_iga_ctx_destroy(ctx)
 
         ta = threading.Thread(target=arrivals, daemon=True)
         ta.start()
