@@ -7,7 +7,9 @@ part of u(x) equal to d^2 u / d x_k^2 with no truncation error; the oracle uses
 this to build f = -Laplace(u) for the manufactured solutions (Section 3.1).
 
 Pinned in tests/test_oracle_manufactured.py against a hand-derived closed form
-of the Laplacian in cylindrical coordinates and against finite differences.
+of the Laplacian in cylindrical coordinates, against finite differences, and
+primitive by primitive (log, sin, cos, products, quotients) against
+hand-differentiated first and second derivatives.
 """
 import numpy as np
 

@@ -69,3 +69,22 @@ def test_solution_vanishes_on_all_faces(geom):
             axes[d] = np.array([end])
             X, _ = geom.map(*axes)
             assert np.max(np.abs(m.u(X))) < 1e-13
+
+
+def test_hyperdual_primitives_against_closed_forms():
+    """Value, first and second derivative carried by each primitive and by the arithmetic:
+    log(x^2 + 1) -> 2x / (1 + x^2), 2 (1 - x^2) / (1 + x^2)^2; sin(3x) / x and cos(x)^2
+    against their hand-differentiated forms."""
+    from oracle import hyperdual as hd
+    x = np.linspace(0.3, 2.7, 9)
+    X = hd.HD(x, 1.0, 1.0)
+    f = hd.log(X * X + 1.0)
+    assert np.allclose(f.a, np.log(x * x + 1), rtol=0, atol=1e-15)
+    assert np.allclose(f.b, 2 * x / (1 + x * x), rtol=1e-14) and np.allclose(f.c, f.b)
+    assert np.allclose(f.d, 2 * (1 - x * x) / (1 + x * x) ** 2, rtol=1e-13, atol=1e-15)
+    g = hd.sin(3.0 * X) / X
+    d1 = 3 * np.cos(3 * x) / x - np.sin(3 * x) / x ** 2
+    d2 = -9 * np.sin(3 * x) / x - 6 * np.cos(3 * x) / x ** 2 + 2 * np.sin(3 * x) / x ** 3
+    assert np.allclose(g.b, d1, rtol=1e-13) and np.allclose(g.d, d2, rtol=1e-12, atol=1e-14)
+    h = hd.cos(X) * hd.cos(X)
+    assert np.allclose(h.b, -np.sin(2 * x), atol=1e-15) and np.allclose(h.d, -2 * np.cos(2 * x), atol=1e-14)
