@@ -190,3 +190,54 @@ def test_batch_block_and_per_rhs_both_meet_the_tolerance(tt):
     items, keep = tt.batch_items(inst[:1], rhs_solve=7)
     code, _, _ = tt.tt_iga_batch_solve(items, lanes=1)
     assert code == tt.ERR_ARG
+
+
+def test_eight_right_hand_sides_in_one_block_solve(tt, ctx):
+    """The batch limit of right-hand sides: every slice meets the tolerance and equals its plain solve."""
+    n, p, nb = 7, 2, 8
+    rhs = [tt.rhs_desc(_modes(k)) for k in range(nb)]
+    g, s = _system(tt, ctx, synthetic.TWISTED_ANNULUS, p, n, rhs)
+    pts = synthetic.random_points(64, seed=31)
+    sols, st, rr = tt.tt_iga_solve_block(ctx, s, tt.solve_opts(tol=1e-11))
+    try:
+        assert st["converged"] and len(sols) == nb
+        ub = [_eval(tt, ctx, u, pts) for u in sols]
+        up = []
+        for k in range(nb):
+            u, _ = tt.tt_iga_solve(ctx, s, tt.solve_opts(tol=1e-11, rhs_index=k))
+            up.append(_eval(tt, ctx, u, pts))
+            tt.tt_iga_solution_destroy(u)
+    finally:
+        for u in sols:
+            tt.tt_iga_solution_destroy(u)
+        tt.tt_iga_system_destroy(s)
+        tt.tt_iga_geom_destroy(g)
+    assert all(0 <= r <= 1e-11 for r in rr), rr
+    for k in range(nb):
+        assert np.max(np.abs(ub[k] - up[k])) < 1e-8 * np.max(np.abs(up[k]))
+
+
+def test_mixed_precision_block_solve(tt, ctx):
+    """FP32 local solves inside FP64 refinement on the block system: every right-hand side meets
+    1e-10 and agrees with its FP64 solve to the accuracy that residual allows."""
+    n, p, nb = 9, 2, 3
+    rhs = [tt.rhs_desc(_modes(k)) for k in range(nb)]
+    g, s = _system(tt, ctx, synthetic.QUARTER_CYLINDER, p, n, rhs)
+    pts = synthetic.random_points(64, seed=32)
+    sols, st, rr = tt.tt_iga_solve_block(ctx, s, tt.solve_opts(tol=1e-10, precision=tt.MIXED_FP32))
+    try:
+        assert st["converged"] and st["local_matvecs"] > st["local_matvecs_fp64"]
+        ub = [_eval(tt, ctx, u, pts) for u in sols]
+        up = []
+        for k in range(nb):
+            u, _ = tt.tt_iga_solve(ctx, s, tt.solve_opts(tol=1e-12, rhs_index=k))
+            up.append(_eval(tt, ctx, u, pts))
+            tt.tt_iga_solution_destroy(u)
+    finally:
+        for u in sols:
+            tt.tt_iga_solution_destroy(u)
+        tt.tt_iga_system_destroy(s)
+        tt.tt_iga_geom_destroy(g)
+    assert all(0 <= r <= 1e-10 for r in rr), rr
+    for k in range(nb):
+        assert np.max(np.abs(ub[k] - up[k])) < 1e-6 * np.max(np.abs(up[k]))
