@@ -302,7 +302,11 @@ int tt_iga_residual(tt_iga_ctx *ctx, const tt_iga_system *s, const tt_iga_soluti
  * doubles, may be NULL) receives ||F_k||.  A solution of the block system
  * (tt_iga_solve with rhs_index 0) is sliced by tt_iga_solution_unstack: block
  * k times scale, the solution of right-hand side k of s (its TT ranks are the
- * block solution's).  tt_iga_eval and tt_iga_l2_error reject block solutions. */
+ * block solution's).  tt_iga_eval and tt_iga_l2_error reject block solutions.
+ * TT_IGA_ERR_ARG for a mode outside 0..2, a system that is already a block
+ * system, a zero right-hand side, a block index outside 0..n_rhs-1 or a
+ * non-finite scale.  The new handles belong to the caller (release with
+ * tt_iga_system_destroy / tt_iga_solution_destroy). */
 int tt_iga_system_stack(tt_iga_ctx *ctx, const tt_iga_system *s, int mode, double eps, tt_iga_system **out,
                         double *scales);
 int tt_iga_solution_unstack(tt_iga_ctx *ctx, const tt_iga_solution *ub, int k, double scale,
