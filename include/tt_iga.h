@@ -98,11 +98,6 @@ int tt_iga_profile_enable(tt_iga_ctx *ctx, int family);
 /* Synchronise and return the summed event time (ms), the number of timed
  * launches and their summed algorithmic FLOPs. */
 int tt_iga_profile_read(tt_iga_ctx *ctx, double *ms_total, long long *launches, double *flops_total);
-/* Measured FMA throughput of the context's GPU (TFLOP/s, one FMA = 2 FLOP): a
- * kernel of independent FMA chains over every SM, timed with CUDA events on the
- * context stream (about 10 ms).  Either output may be NULL.  The denominators
- * of the ALU-bound rooflines; the library has no counterpart in the paper. */
-int tt_iga_fma_peaks(tt_iga_ctx *ctx, double *fp64_tflops, double *fp32_tflops);
 
 /* --------------------------------------------------------------- geometry */
 
@@ -271,7 +266,8 @@ typedef struct {
 typedef struct {
   int sweeps;
   int ranks[2];
-  double rel_residual;      /* exact ||F - K u|| / ||F|| from TT arithmetic, or -1 if skipped */
+  double rel_residual;      /* exact ||F - K u|| / ||F|| (see tt_iga_residual), or -1 if it could not
+                               be computed: converged then rests on the local residuals */
   double local_residual;    /* largest relative local residual of the last sweep */
   long long local_matvecs;  /* local operator applications (all precisions) */
   long long local_matvecs_fp64;
@@ -287,9 +283,23 @@ void tt_iga_solution_destroy(tt_iga_solution *u);
 /* TT ranks of the solution. */
 int tt_iga_solution_ranks(const tt_iga_solution *u, int ranks[2]);
 /* Exact relative residual ||F - K u||_2 / ||F||_2 of u against right-hand side k,
- * computed in TT arithmetic with orthogonal projections (FP64). */
+ * computed in TT arithmetic with orthogonal projections (FP64) while the TT rank
+ * of F - K u stays within 256; above that, for problems of at most 2^22
+ * unknowns, by expanding F and K u to dense vectors on the device.
+ * TT_IGA_ERR_TOO_LARGE when neither applies. */
 int tt_iga_residual(tt_iga_ctx *ctx, const tt_iga_system *s, const tt_iga_solution *u, int k,
                     double *rel_residual);
+
+/* tt_iga_solve started from the iterate u0 instead of a random rank-2 TT
+ * (AMEn of Section 4.1.2 with a given initial guess): a solution of a nearby
+ * problem, or one rebuilt from exported cores by tt_iga_import_cores, so that
+ * a solve can resume from a checkpoint.  u0's mode sizes (and block layout)
+ * must equal those of s; its ranks are kept as the starting ranks (1..256).
+ * The result is a new handle; u0 is not modified.  Return codes as
+ * tt_iga_solve, plus TT_IGA_ERR_STATE when a handle belongs to another
+ * context. */
+int tt_iga_solve_from(tt_iga_ctx *ctx, const tt_iga_system *s, const tt_iga_solve_opts *opts, const tt_iga_solution *u0,
+                      tt_iga_solution **out, tt_iga_stats *st);
 
 /* Several right-hand sides as one block-TT solve (AMEn of Section 4.1.2 on the
  * block system).  tt_iga_system_stack builds the block system of all n_rhs
@@ -332,6 +342,17 @@ int tt_iga_solve_block(tt_iga_ctx *ctx, const tt_iga_system *s, const tt_iga_sol
 int tt_iga_solution_cores(tt_iga_ctx *ctx, const tt_iga_solution *u, double *out, size_t cap, int modes[3],
                           int ranks[4]);
 
+/* The inverse of tt_iga_solution_cores: a solution of system s rebuilt from
+ * host TT cores in the TT format of Section 4.1.1 (core 1 [1][m1][r1], core 2
+ * [r1][m2][r2], core 3 [r2][m3][1] back to back, FP64; host pointer, read
+ * during the call only).  modes[3] must equal the system's mode sizes (the
+ * unknowns per direction) and ranks[4] = {1, r1, r2, 1} with 1 <= r1, r2 <=
+ * 256; the solution takes the system's degree, boundary layout (lift) and
+ * block layout.  A solution exported, imported and evaluated gives the same
+ * values.  TT_IGA_ERR_ARG for mismatched sizes or a non-finite core entry. */
+int tt_iga_import_cores(tt_iga_ctx *ctx, const tt_iga_system *s, const double *cores, const int modes[3],
+                        const int ranks[4], tt_iga_solution **out);
+
 /* ------------------------------------------------------------ evaluation */
 
 /* u_h(xi) = sum_a u_a N_a(xi) at m parametric points xi[m][3] in [0,1]^3.
@@ -344,6 +365,20 @@ int tt_iga_eval(tt_iga_ctx *ctx, const tt_iga_solution *u, int m, const double *
  * data on the radial faces only, taken from u's boundary conditions). */
 int tt_iga_l2_error(tt_iga_ctx *ctx, const tt_iga_geom *g, const tt_iga_solution *u,
                     const tt_iga_rhs_desc *rhs, double *rel_l2);
+
+/* Relative L2 difference of two solutions on the mapped domain of g (Eq.
+ * L2norm applied to u_h - v_h):
+ *   sqrt( int (u_h - v_h)^2 dOmega / int v_h^2 dOmega ),
+ * with the Gauss rule of the discretisation (nq points per element and
+ * direction) and det J by TT-cross to g's cross tolerance.  Computed in TT
+ * arithmetic: the mass matrix int N_a N_b det J is assembled per direction
+ * like the stiffness (Section 4.2.1, selector (N, N) in every direction), and
+ * w = u - v is rounded (QR + SVD, Section 4.2.1) before w^T M w is formed, so
+ * the difference of two nearly equal solutions is resolved to about 1e-15 of
+ * ||v||.  u and v must share g's discretisation and boundary layout and carry
+ * no Dirichlet lift (TT_IGA_ERR_ARG otherwise). */
+int tt_iga_l2_diff(tt_iga_ctx *ctx, const tt_iga_geom *g, const tt_iga_solution *u, const tt_iga_solution *v,
+                   double *rel_l2);
 
 /* ------------------------------------------------------------ batching */
 
@@ -458,27 +493,39 @@ int tt_iga_qr(tt_iga_ctx *ctx, int m, int k, const double *A, int lda, double *Q
 /* SVD of a small square matrix A (device, k x k): A = U diag(s) V^T by
  * one-sided Jacobi, FP64, singular values descending.  k <= 256. */
 int tt_iga_svd_small(tt_iga_ctx *ctx, int k, const double *A, double *U, double *s, double *V);
-/* Allocation-free SVD (no counterpart in the paper; a library service).
+/* Allocation-free SVD.  The paper has no counterpart: this is a library
+ * service for callers that cannot allocate device memory.  Such callers are,
+ * for example, a serving process that reserved all of the GPU's memory for its
+ * own pools at start-up and forbids any further cudaMalloc, code whose
+ * allocator is not reachable from where it runs (a plug-in handed only a
+ * stream and buffers), and code on a latency budget that an allocation, or
+ * its failure under memory pressure, would break.
  *
- * Same result as tt_iga_svd_small, for callers that cannot allocate device
- * memory: code that runs while a CUDA stream is being captured into a graph
- * (an allocation there either breaks the capture or becomes part of the
- * graph), and hosts that reserve all device memory up front and forbid other
- * allocations.  It takes no context (creating one allocates) and runs on
- * `stream` (a cudaStream_t; NULL is the legacy default stream).  A, U, s, V
- * are caller-owned device buffers as in tt_iga_svd_small.
+ * Same factorisation as tt_iga_svd_small (A = U diag(s) V^T by one-sided
+ * Jacobi, FP64, singular values descending).  It takes no context (creating
+ * one allocates) and runs on `stream` (a cudaStream_t; NULL is the legacy
+ * default stream).  A, U, s, V are caller-owned device buffers as in
+ * tt_iga_svd_small; info (device int, may be NULL) receives 0 when the Jacobi
+ * sweeps converged and 1 when they had not after 60 sweeps (the factors are
+ * then those of the last sweep).  Outputs are valid once `stream` has been
+ * synchronised.
  *
- * Scratch: a fixed 1 MiB device array inside the library (two 256 x 256 FP64
- * panels), held by every GPU that loads the library until the process exits.
+ * Scratch: a fixed 1 MiB array inside the library (two 256 x 256 FP64 panels),
+ * which every GPU that loads the library holds until the process exits.  No
+ * cudaMalloc, cudaFree or allocating library routine is called.
  * Limit: k <= 256; larger k returns TT_IGA_ERR_TOO_LARGE and launches nothing.
- * The first call on a device looks up the array's device address once
- * (cudaGetSymbolAddress, no allocation); make that first call before any
- * stream capture.  All calls share the array: calls whose kernels overlap on
- * the GPU (different streams, no ordering between them) race on it and must
- * not be issued.  Returns TT_IGA_OK once the kernel is enqueued; results are
- * valid after `stream` is synchronised.  No error message is recorded
- * (there is no context); the return code says what went wrong. */
-int tt_iga_svd_small_noalloc(void *stream, int k, const double *A, double *U, double *s, double *V);
+ * The first call on a device, with that device current, looks up the array's
+ * device address (cudaGetSymbolAddress, no allocation) and caches it; make
+ * that first call before any stream capture.  A cudaDeviceReset invalidates
+ * the cached address, so do not call this entry point after one.
+ * All calls share the array and every call overwrites it before reading it:
+ * calls whose kernels can overlap on the GPU (different streams with no
+ * ordering between them) race on it and must not be issued.
+ * Returns TT_IGA_OK once the kernel is enqueued, TT_IGA_ERR_ARG for a null
+ * buffer, TT_IGA_ERR_CUDA when the launch itself fails (its own return code;
+ * an error left by other work is neither reported nor cleared).  No message is
+ * recorded (there is no context). */
+int tt_iga_svd_small_noalloc(void *stream, int k, const double *A, double *U, double *s, double *V, int *info);
 /* Maximum-volume row selection (Goreinov et al. 2010) of a tall matrix U
  * (device, m x r): device outputs rows[r] (int32) and B = U U[rows,:]^{-1}
  * (device, m x r).  Stops when max |B| <= 1 + delta or after maxit swaps. */

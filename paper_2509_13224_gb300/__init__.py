@@ -126,6 +126,11 @@ _SIGS = {
     "tt_iga_solution_unstack": (ctypes.c_int, [_vp, _vp, ctypes.c_int, ctypes.c_double, ctypes.POINTER(_vp)]),
     "tt_iga_solve_block": (ctypes.c_int, [_vp, _vp, ctypes.POINTER(SolveOpts), ctypes.c_int, ctypes.POINTER(_vp),
                                           ctypes.POINTER(Stats), _c_double_p]),
+    "tt_iga_solve_from": (ctypes.c_int, [_vp, _vp, ctypes.POINTER(SolveOpts), _vp, ctypes.POINTER(_vp),
+                                         ctypes.POINTER(Stats)]),
+    "tt_iga_import_cores": (ctypes.c_int, [_vp, _vp, _c_double_p, ctypes.POINTER(ctypes.c_int * 3),
+                                           ctypes.POINTER(ctypes.c_int * 4), ctypes.POINTER(_vp)]),
+    "tt_iga_l2_diff": (ctypes.c_int, [_vp, _vp, _vp, _vp, _c_double_p]),
     "tt_iga_solution_destroy": (None, [_vp]),
     "tt_iga_solution_ranks": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_int * 2)]),
     "tt_iga_residual": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int, _c_double_p]),
@@ -155,9 +160,8 @@ _SIGS = {
                                        ctypes.c_int]),
     "tt_iga_qr": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, _vp, ctypes.c_int, _vp, _vp]),
     "tt_iga_svd_small": (ctypes.c_int, [_vp, ctypes.c_int, _vp, _vp, _vp, _vp]),
-    "tt_iga_svd_small_noalloc": (ctypes.c_int, [_vp, ctypes.c_int, _vp, _vp, _vp, _vp]),
+    "tt_iga_svd_small_noalloc": (ctypes.c_int, [_vp, ctypes.c_int, _vp, _vp, _vp, _vp, _vp]),
     "tt_iga_maxvol": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, _vp, ctypes.c_double, ctypes.c_int, _vp, _vp]),
-    "tt_iga_fma_peaks": (ctypes.c_int, [_vp, _c_double_p, _c_double_p]),
 }
 for _name, (_res, _args) in _SIGS.items():
     _fn = getattr(_lib, _name)
@@ -289,13 +293,6 @@ def tt_iga_profile_read(ctx):
     return ms.value, n.value, w.value
 
 
-def tt_iga_fma_peaks(ctx):
-    """Measured (FP64, FP32) FMA throughput of the context's GPU in TFLOP/s."""
-    a, b = ctypes.c_double(), ctypes.c_double()
-    _check(ctx, _lib.tt_iga_fma_peaks(ctx, ctypes.byref(a), ctypes.byref(b)))
-    return a.value, b.value
-
-
 def tt_iga_solution_cores(ctx, u, out=None):
     """Solution TT cores copied to host. With out (a float64 numpy buffer, ideally pinned) fills it in place."""
     import numpy as np
@@ -422,6 +419,42 @@ def tt_iga_solve(ctx, s, opts, allow_not_converged=False):
 
 def tt_iga_solution_destroy(u):
     _lib.tt_iga_solution_destroy(u)
+
+
+def tt_iga_solve_from(ctx, s, opts, u0, allow_not_converged=False):
+    """AMEn solve of s started from the iterate u0 (a solution handle); returns (handle, stats)."""
+    h = ctypes.c_void_p()
+    st = Stats()
+    allow = (ERR_NOT_CONVERGED,) if allow_not_converged else ()
+    code = _lib.tt_iga_solve_from(ctx, s, ctypes.byref(opts), u0, ctypes.byref(h), ctypes.byref(st))
+    if code != OK and code not in allow:
+        msg = tt_iga_last_error(ctx)
+        if h.value:
+            _lib.tt_iga_solution_destroy(h)
+        raise TTIgaError(code, msg)
+    return h, st.as_dict()
+
+
+def tt_iga_import_cores(ctx, s, cores):
+    """Solution of system s from host TT cores (three float64 arrays [r0, m, r1], as returned by
+    tt_iga_solution_cores)."""
+    import numpy as np
+    cores = [np.ascontiguousarray(c, dtype=np.float64) for c in cores]
+    modes = (ctypes.c_int * 3)(*[int(c.shape[1]) for c in cores])
+    ranks = (ctypes.c_int * 4)(int(cores[0].shape[0]), int(cores[0].shape[2]), int(cores[1].shape[2]),
+                               int(cores[2].shape[2]))
+    flat = np.concatenate([c.reshape(-1) for c in cores])
+    h = ctypes.c_void_p()
+    _check(ctx, _lib.tt_iga_import_cores(ctx, s, flat.ctypes.data_as(_c_double_p), ctypes.byref(modes),
+                                         ctypes.byref(ranks), ctypes.byref(h)))
+    return h
+
+
+def tt_iga_l2_diff(ctx, g, u, v):
+    """Relative L2 difference ||u_h - v_h|| / ||v_h|| over the mapped domain of g."""
+    r = ctypes.c_double()
+    _check(ctx, _lib.tt_iga_l2_diff(ctx, g, u, v, ctypes.byref(r)))
+    return r.value
 
 
 def tt_iga_system_stack(ctx, s, mode=1, eps=0.0):
@@ -624,14 +657,15 @@ def tt_iga_svd_small(ctx, A, U, s, V):
     _check(ctx, _lib.tt_iga_svd_small(ctx, int(A.shape[0]), _ptr(A), _ptr(U), _ptr(s), _ptr(V)))
 
 
-def tt_iga_svd_small_noalloc(stream, A, U, s, V):
+def tt_iga_svd_small_noalloc(stream, A, U, s, V, info=None):
     """Allocation-free SVD on `stream` (torch.cuda.Stream, raw handle or None for the legacy default stream).
 
+    info: optional int32 CUDA tensor of one element, set to 0 (converged) or 1 (not converged).
     Returns the status code instead of raising, so callers can see ERR_TOO_LARGE for k > 256."""
     h = None
     if stream is not None:
         h = stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
-    return int(_lib.tt_iga_svd_small_noalloc(h, int(A.shape[0]), _ptr(A), _ptr(U), _ptr(s), _ptr(V)))
+    return int(_lib.tt_iga_svd_small_noalloc(h, int(A.shape[0]), _ptr(A), _ptr(U), _ptr(s), _ptr(V), _ptr(info)))
 
 
 def tt_iga_maxvol(ctx, U, rows, B, delta=1e-2, maxit=100):

@@ -2,7 +2,9 @@
 
 Each CUDA translation unit under csrc/ is compiled in parallel into
 _build/*.o, then linked into paper_2509_13224_gb300/libtt_iga.so.  Objects are
-rebuilt when their source or any header is newer.
+rebuilt when their source or any header is newer.  build_probe() compiles the
+benchmark's FMA throughput probe (fma_probe.cu beside bench.py) into
+_build/libfma_probe.so; it is not part of the solver library.
 """
 import glob
 import os
@@ -15,6 +17,8 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(HERE, "libtt_iga.so")
+PROBE_SRC = os.path.join(ROOT, "fma_probe.cu")
+PROBE_LIB = os.path.join(BUILD, "libfma_probe.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
          "-diag-suppress", "177"]
@@ -64,6 +68,20 @@ def build(verbose=False, force=False):
             sys.stderr.write(r.stdout + r.stderr)
             raise RuntimeError("link of libtt_iga.so failed")
     return LIB
+
+
+def build_probe(verbose=False):
+    """Compile the benchmark's FMA throughput probe into its own shared library; returns its path."""
+    os.makedirs(BUILD, exist_ok=True)
+    if os.path.exists(PROBE_LIB) and os.path.getmtime(PROBE_LIB) >= os.path.getmtime(PROBE_SRC):
+        return PROBE_LIB
+    cmd = [_nvcc()] + ARCH + FLAGS + ["-shared", PROBE_SRC, "-o", PROBE_LIB]
+    r = subprocess.run(cmd, capture_output=True, text=True)
+    if verbose or r.returncode != 0:
+        sys.stderr.write(" ".join(cmd) + "\n" + r.stdout + r.stderr)
+    if r.returncode != 0:
+        raise RuntimeError("nvcc failed for fma_probe.cu")
+    return PROBE_LIB
 
 
 if __name__ == "__main__":

@@ -118,6 +118,39 @@ template <typename T> void dot_dev(Ctx *c, const T *x, const T *y, long long n, 
   TTI_LAUNCH();
 }
 
+// ||F - K u|| / Fnorm for the band TT operator K (cores Kc, ranks R) and a TT u.
+// The TT of F - K u has ranks f + R r; while they stay within the QR limit (256)
+// its norm comes from orthogonalisation (TT arithmetic).  Above it, F and K u are
+// expanded to dense vectors by GEMM chains and subtracted entry by entry (the
+// difference is resolved to FP64 rounding of ||F||), as long as the vectors
+// (2^22 entries) and the cores of K u (2^27 doubles) stay small; otherwise -1.
+double residual_norm(Ctx *c, const TT3 &F, double Fnorm, const TT3 &K, const int n[3], int b, int p, const TT3 &u) {
+  TT3 Ku;
+  for (int k = 0; k < 3; ++k) Ku.m[k] = n[k];
+  for (int k = 0; k < 4; ++k) Ku.r[k] = K.r[k] * u.r[k];
+  const bool tt_ok = Ku.r[1] + F.r[1] <= 256 && Ku.r[2] + F.r[2] <= 256;
+  const long long N = (long long)n[0] * n[1] * n[2];
+  size_t ku_max = 0;
+  for (int k = 0; k < 3; ++k) ku_max = std::max(ku_max, Ku.core_elems(k));
+  if (!tt_ok && (N > (1LL << 22) || ku_max > ((size_t)1 << 27))) return -1.0;
+  Ku.alloc(c);
+  for (int k = 0; k < 3; ++k) {
+    BandCore A{K.core[k].d(), nullptr, K.r[k], n[k], b, p, K.r[k + 1]};
+    tt_matvec_core(c, A, u.core[k].d(), u.r[k], u.r[k + 1], Ku.core[k].d());
+  }
+  if (tt_ok) {
+    TT3 W;
+    tt_sum(c, F, 1.0, Ku, -1.0, W);
+    return tt_norm(c, W) / Fnorm;
+  }
+  DBuf fd(c, N * sizeof(double)), kd(c, N * sizeof(double));
+  tt_dense(c, F, fd.d());
+  tt_dense(c, Ku, kd.d());
+  k_sub<<<grid1d(N, 256), 256, 0, c->stream>>>(fd.d(), kd.d(), N);
+  TTI_LAUNCH();
+  return host_nrm2(c, kd.d(), N) / Fnorm;
+}
+
 }  // namespace
 
 struct Amen {
@@ -142,8 +175,10 @@ struct Amen {
   // fork / join events of the preconditioner build on a helper stream (created on first use)
   cudaEvent_t ev_in = nullptr, ev_out = nullptr;
 
-  Amen(Ctx *c_, const tt_iga_system *s, const tt_iga_solve_opts &opts)
-      : c(c_), S(s), F(s->F[opts.rhs_index]), Fnorm(s->F_norm[opts.rhs_index]), o(opts), w64{c_}, w32{c_} {
+  const TT3 *u0 = nullptr;  // initial iterate (warm start), or null for a random rank-2 TT
+
+  Amen(Ctx *c_, const tt_iga_system *s, const tt_iga_solve_opts &opts, const TT3 *start)
+      : c(c_), S(s), F(s->F[opts.rhs_index]), Fnorm(s->F_norm[opts.rhs_index]), o(opts), u0(start), w64{c_}, w32{c_} {
     for (int k = 0; k < 4; ++k) { R[k] = S->K.r[k]; f[k] = F.r[k]; }
     for (int k = 0; k < 3; ++k) {
       A[k].A = S->K.core[k].d();
@@ -205,8 +240,12 @@ struct Amen {
 
   void init() {
     const int m[3] = {n(0), n(1), n(2)};
-    const int r0 = std::max(1, std::min(2, std::min(m[0], m[2])));
-    random_tt(c, u, m, r0, r0, 0x5EED5EEDULL + 31 * o.rhs_index);
+    if (u0) {
+      tt_copy(c, *u0, u);
+    } else {
+      const int r0 = std::max(1, std::min(2, std::min(m[0], m[2])));
+      random_tt(c, u, m, r0, r0, 0x5EED5EEDULL + 31 * o.rhs_index);
+    }
     tt_orth_rl(c, u);
     const int rho = std::max(0, o.kickrank);
     if (rho > 0) {
@@ -564,18 +603,7 @@ struct Amen {
     z.core[2] = std::move(bz);
   }
 
-  double exact_residual() {
-    // W = F - K u with cores [F_k | (K u)_k] in block form; ||W|| by orthogonalisation.
-    TT3 Ku;
-    for (int k = 0; k < 3; ++k) Ku.m[k] = n(k);
-    for (int k = 0; k < 4; ++k) Ku.r[k] = R[k] * u.r[k];
-    if (Ku.r[1] + f[1] > 256 || Ku.r[2] + f[2] > 256) return -1.0;
-    Ku.alloc(c);
-    for (int k = 0; k < 3; ++k) tt_matvec_core(c, A[k], u.core[k].d(), u.r[k], u.r[k + 1], Ku.core[k].d());
-    TT3 W;
-    tt_sum(c, F, 1.0, Ku, -1.0, W);
-    return tt_norm(c, W) / Fnorm;
-  }
+  double exact_residual() { return residual_norm(c, F, Fnorm, S->K, S->n, S->b, S->p, u); }
 
   int run(tt_iga_solution *out) {
     init();
@@ -688,12 +716,13 @@ struct Amen {
 };
 
 
-int amen_solve(Ctx *c, const tt_iga_system *s, const tt_iga_solve_opts &o, tt_iga_solution *out, tt_iga_stats *st) {
+int amen_solve(Ctx *c, const tt_iga_system *s, const tt_iga_solve_opts &o, tt_iga_solution *out, tt_iga_stats *st,
+               const tt_iga_solution *start) {
   cudaEvent_t e0, e1;
   TTI_CUDA(cudaEventCreate(&e0));
   TTI_CUDA(cudaEventCreate(&e1));
   TTI_CUDA(cudaEventRecord(e0, c->stream));
-  Amen a(c, s, o);
+  Amen a(c, s, o, start ? &start->u : nullptr);
   int status = a.run(out);
   TTI_CUDA(cudaEventRecord(e1, c->stream));
   TTI_CUDA(cudaEventSynchronize(e1));
@@ -707,21 +736,7 @@ int amen_solve(Ctx *c, const tt_iga_system *s, const tt_iga_solve_opts &o, tt_ig
 }
 
 double exact_residual(Ctx *c, const tt_iga_system *s, const tt_iga_solution *sol, int k) {
-  // Same construction as Amen::exact_residual, without the rank cap.
-  const TT3 &F = s->F[k];
-  TT3 Ku;
-  for (int d = 0; d < 3; ++d) Ku.m[d] = s->n[d];
-  for (int d = 0; d < 4; ++d) Ku.r[d] = s->K.r[d] * sol->u.r[d];
-  TTI_CHECK_ARG(Ku.r[1] + F.r[1] <= 256 && Ku.r[2] + F.r[2] <= 256, "residual: TT rank %d/%d above 256",
-                Ku.r[1] + F.r[1], Ku.r[2] + F.r[2]);
-  Ku.alloc(c);
-  for (int d = 0; d < 3; ++d) {
-    BandCore A{s->K.core[d].d(), nullptr, s->K.r[d], s->n[d], s->b, s->p, s->K.r[d + 1]};
-    tt_matvec_core(c, A, sol->u.core[d].d(), sol->u.r[d], sol->u.r[d + 1], Ku.core[d].d());
-  }
-  TT3 W;
-  tt_sum(c, F, 1.0, Ku, -1.0, W);
-  return tt_norm(c, W) / s->F_norm[k];
+  return residual_norm(c, s->F[k], s->F_norm[k], s->K, s->n, s->b, s->p, sol->u);
 }
 
 }  // namespace ttiga

@@ -381,6 +381,27 @@ void assemble_system(Ctx *c, const tt_iga_geom *g, const tt_iga_rhs_desc *rhs, i
   }
 }
 
+// Mass matrix on the mapped domain, M_ab = int N_a N_b det J dxi, restricted to the
+// unknowns of bl: det J on the tensor Gauss grid by TT-cross (component 6 of the
+// point evaluator) to the geometry's cross tolerance, then the per-direction
+// quadrature contraction of Section 4.2.1 with the selector (N, N) in every
+// direction (no derivative), the same Gauss rule as the stiffness.
+void mass_matrix(Ctx *c, const tt_iga_geom *g, const BoundaryLayout &bl, TT3 &M) {
+  const int p = g->desc.p, b = 2 * p + 1;
+  CrossResult dj;
+  cross3(c, g->s, g->gp, rhs_params(nullptr), 6, g->desc.cross_tol, g->desc.max_rank, g->desc.seed + 15485863ULL, 0.0,
+         dj);
+  TTI_CHECK_ARG(!dj.zero, "mass matrix: det J vanishes on the sampled grid");
+  if (!dj.converged) fail(TT_IGA_ERR_NOT_CONVERGED, "mass matrix: TT-cross of det J did not validate");
+  for (int d = 0; d < 3; ++d) M.m[d] = g->s[d].n * b;
+  for (int k = 0; k < 4; ++k) M.r[k] = dj.tt.r[k];
+  M.alloc(c);
+  for (int d = 0; d < 3; ++d)
+    stiffness_core(c, g->s[d].n, p, g->s[d].nq, g->s[d].wts.d(), g->s[d].N.d(), g->s[d].dN.d(), dj.tt.core[d].d(),
+                   dj.tt.r[d], dj.tt.r[d + 1], 0, 0, M.core[d].d());
+  restrict_tt(c, M, bl, p, true);
+}
+
 // K(row, col) of the restricted band TT operator at index pairs.
 __global__ void k_op_entries(const double *M1, const double *M2, const double *M3, int n1, int n2, int n3, int p,
                              int r1, int r2, int m, const int *rows, const int *cols, double *out) {

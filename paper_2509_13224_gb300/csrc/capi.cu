@@ -144,14 +144,6 @@ int tt_iga_profile_enable(tt_iga_ctx *c, int family) {
   API_CATCH(c)
 }
 
-int tt_iga_fma_peaks(tt_iga_ctx *c, double *fp64_tflops, double *fp32_tflops) {
-  if (!c) return TT_IGA_ERR_ARG;
-  API_TRY
-  ttiga::fma_peaks(c, fp64_tflops, fp32_tflops);
-  return TT_IGA_OK;
-  API_CATCH(c)
-}
-
 int tt_iga_profile_read(tt_iga_ctx *c, double *ms_total, long long *launches, double *flops_total) {
   if (!c) return TT_IGA_ERR_ARG;
   API_TRY
@@ -482,9 +474,7 @@ int tt_iga_solve_block(tt_iga_ctx *c, const tt_iga_system *s, const tt_iga_solve
     sols[k].reset(new tt_iga_solution());
     unstack_solution(c, &ub, k, scale[k], sols[k].get());
     if (rel_res) {
-      rel_res[k] = -1.0;
-      if (s->K.r[1] * ub.u.r[1] + s->F[k].r[1] <= 256 && s->K.r[2] * ub.u.r[2] + s->F[k].r[2] <= 256)
-        rel_res[k] = exact_residual(c, s, sols[k].get(), k);
+      rel_res[k] = exact_residual(c, s, sols[k].get(), k);
     }
   }
   for (int k = 0; k < nb; ++k) out[k] = sols[k].release();
@@ -509,6 +499,8 @@ int tt_iga_residual(tt_iga_ctx *c, const tt_iga_system *s, const tt_iga_solution
   API_TRY
   TTI_CHECK_ARG(k >= 0 && k < (int)s->F.size(), "residual: rhs %d out of range", k);
   *rel = exact_residual(c, s, u, k);
+  if (*rel < 0.0)
+    fail(TT_IGA_ERR_TOO_LARGE, "residual: the TT rank of F - K u is above 256 and the problem too large to expand");
   return TT_IGA_OK;
   API_CATCH(c)
 }
@@ -533,6 +525,71 @@ int tt_iga_solution_cores(tt_iga_ctx *c, const tt_iga_solution *u, double *out, 
   }
   c->sync();
   return TT_IGA_OK;
+  API_CATCH(c)
+}
+
+int tt_iga_import_cores(tt_iga_ctx *c, const tt_iga_system *s, const double *cores, const int modes[3],
+                        const int ranks[4], tt_iga_solution **out) {
+  if (!c || !s || !cores || !modes || !ranks || !out) return TT_IGA_ERR_ARG;
+  *out = nullptr;
+  API_TRY
+  if (s->ctx != c) fail(TT_IGA_ERR_STATE, "import_cores: system belongs to another context");
+  TTI_CHECK_ARG(ranks[0] == 1 && ranks[3] == 1, "import_cores: ranks[0] and ranks[3] must be 1");
+  for (int d = 0; d < 3; ++d)
+    TTI_CHECK_ARG(modes[d] == s->n[d], "import_cores: mode %d has size %d, the system %d", d, modes[d], s->n[d]);
+  for (int k = 1; k <= 2; ++k)
+    TTI_CHECK_ARG(ranks[k] >= 1 && ranks[k] <= 256, "import_cores: rank %d = %d outside 1..256", k, ranks[k]);
+  auto *U = new tt_iga_solution();
+  std::unique_ptr<tt_iga_solution> guard(U);
+  U->ctx = c;
+  U->p = s->p;
+  U->bl = s->bl;
+  U->stacked = s->stacked;
+  U->stack_mode = s->stack_mode;
+  for (int d = 0; d < 3; ++d) U->n[d] = U->u.m[d] = modes[d];
+  for (int k = 0; k < 4; ++k) U->u.r[k] = ranks[k];
+  U->u.alloc(c);
+  size_t off = 0;
+  for (int k = 0; k < 3; ++k) {
+    const size_t ne = U->u.core_elems(k);
+    for (size_t i = 0; i < ne; ++i)
+      TTI_CHECK_ARG(std::isfinite(cores[off + i]), "import_cores: core %d holds a non-finite value", k);
+    TTI_CUDA(cudaMemcpyAsync(U->u.core[k].get(), cores + off, ne * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+    off += ne;
+  }
+  c->sync();  // the host array may be released when the call returns
+  *out = guard.release();
+  return TT_IGA_OK;
+  API_CATCH(c)
+}
+
+int tt_iga_solve_from(tt_iga_ctx *c, const tt_iga_system *s, const tt_iga_solve_opts *opts, const tt_iga_solution *u0,
+                      tt_iga_solution **out, tt_iga_stats *st) {
+  if (!c || !s || !u0 || !out) return TT_IGA_ERR_ARG;
+  *out = nullptr;
+  API_TRY
+  if (s->ctx != c || u0->ctx != c) fail(TT_IGA_ERR_STATE, "solve_from: handles belong to another context");
+  const tt_iga_solve_opts o = solve_defaults(opts);
+  TTI_CHECK_ARG(o.rhs_index >= 0 && o.rhs_index < (int)s->F.size(), "solve_from: rhs_index %d out of range",
+                o.rhs_index);
+  for (int d = 0; d < 3; ++d)
+    TTI_CHECK_ARG(u0->u.m[d] == s->n[d], "solve_from: the initial iterate's mode %d has size %d, the system %d", d,
+                  u0->u.m[d], s->n[d]);
+  TTI_CHECK_ARG(u0->stacked == s->stacked, "solve_from: block layouts differ");
+  auto *U = new tt_iga_solution();
+  U->bl = s->bl;
+  U->stacked = s->stacked;
+  U->stack_mode = s->stack_mode;
+  std::unique_ptr<tt_iga_solution> guard(U);
+  int status = amen_solve(c, s, o, U, st, u0);
+  const int ds = device_status(c);
+  *out = guard.release();
+  if (ds != TT_IGA_OK && status == TT_IGA_OK) {
+    c->last_error = "solve_from: device-side breakdown flag raised";
+    return ds;
+  }
+  if (status != TT_IGA_OK) c->last_error = "solve_from: AMEn did not reach the tolerance within max_sweeps";
+  return status;
   API_CATCH(c)
 }
 
@@ -566,6 +623,29 @@ int tt_iga_l2_error(tt_iga_ctx *c, const tt_iga_geom *g, const tt_iga_solution *
                   "only and at least one radial Dirichlet face");
   }
   *rel = l2_error(c, g, u, rhs);
+  return TT_IGA_OK;
+  API_CATCH(c)
+}
+
+static bool same_layout(const BoundaryLayout &a, const BoundaryLayout &b) {
+  for (int d = 0; d < 3; ++d)
+    if (a.lo[d] != b.lo[d] || a.hi[d] != b.hi[d] || a.nfull[d] != b.nfull[d]) return false;
+  return a.lift_dir == b.lift_dir && a.lift_lo == b.lift_lo && a.lift_hi == b.lift_hi;
+}
+
+int tt_iga_l2_diff(tt_iga_ctx *c, const tt_iga_geom *g, const tt_iga_solution *u, const tt_iga_solution *v,
+                   double *rel) {
+  if (!c || !g || !u || !v || !rel) return TT_IGA_ERR_ARG;
+  API_TRY
+  TTI_CHECK_ARG(u->stacked == 1 && v->stacked == 1, "l2_diff: block solution (slice it first)");
+  TTI_CHECK_ARG(u->p == v->p && u->p == g->desc.p, "l2_diff: degrees differ");
+  for (int d = 0; d < 3; ++d)
+    TTI_CHECK_ARG(u->n[d] == v->n[d] && v->bl.nfull[d] == g->s[d].n, "l2_diff: discretisations differ");
+  TTI_CHECK_ARG(same_layout(u->bl, v->bl), "l2_diff: boundary layouts differ");
+  TTI_CHECK_ARG(v->bl.lift_dir < 0, "l2_diff: solutions with a Dirichlet lift are not supported");
+  const double r = l2_diff(c, g, u, v);
+  if (r < 0.0) fail(TT_IGA_ERR_ARG, "l2_diff: the reference solution v is zero");
+  *rel = r;
   return TT_IGA_OK;
   API_CATCH(c)
 }
@@ -747,9 +827,9 @@ int tt_iga_svd_small(tt_iga_ctx *c, int k, const double *A, double *U, double *s
   API_CATCH(c)
 }
 
-int tt_iga_svd_small_noalloc(void *stream, int k, const double *A, double *U, double *s, double *V) {
+int tt_iga_svd_small_noalloc(void *stream, int k, const double *A, double *U, double *s, double *V, int *info) {
   try {
-    return svd_small_noalloc(static_cast<cudaStream_t>(stream), k, A, U, s, V);
+    return svd_small_noalloc(static_cast<cudaStream_t>(stream), k, A, U, s, V, info);
   } catch (...) {
     return TT_IGA_ERR_CUDA;
   }

@@ -189,8 +189,6 @@ void run_concurrent(Ctx *c, int n, const std::function<void(int, Ctx *)> &f);
 // cudaFuncSetAttribute(MaxDynamicSharedMemorySize) once per (kernel, device), thread-safe.
 void set_smem_limit_once(const void *kernel, int bytes);
 
-// Measured FMA throughput (TFLOP/s) of c's device, see probe.cu.
-void fma_peaks(Ctx *c, double *fp64_tflops, double *fp32_tflops);
 inline void DBuf::release() {
   if (p_ && ctx_) ctx_->free(p_, bytes_);
   p_ = nullptr;

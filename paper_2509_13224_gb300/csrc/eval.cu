@@ -4,9 +4,11 @@
 // Gauss points per element and direction.
 #include <algorithm>
 
+#include "amen_ops.cuh"
 #include "eval.cuh"
 #include "geom_device.cuh"
 #include "linalg.cuh"
+#include "tt.cuh"
 
 namespace ttiga {
 
@@ -222,6 +224,40 @@ double l2_error(Ctx *c, const tt_iga_geom *g, const tt_iga_solution *u, const tt
   double num = 0.0, den = 0.0;
   for (int i = 0; i < nb; ++i) { num += h[2 * i]; den += h[2 * i + 1]; }
   return den > 0.0 ? sqrt(num / den) : sqrt(num);
+}
+
+// w^T M w of a TT vector w and a band TT-matrix M by the left interface
+// recursion of the AMEn contractions (PhiL of a 1 x 1 x 1 start, three cores).
+static double quadratic_form(Ctx *c, const TT3 &M, const int n[3], int p, const TT3 &w) {
+  Work<double> wk{c};
+  DBuf phi(c, sizeof(double));
+  const double one = 1.0;
+  c->h2d(phi.get(), &one, sizeof one);
+  for (int k = 0; k < 3; ++k) {
+    BandCore A{M.core[k].d(), nullptr, M.r[k], n[k], 2 * p + 1, p, M.r[k + 1]};
+    DBuf next(c, (size_t)w.r[k + 1] * M.r[k + 1] * w.r[k + 1] * sizeof(double));
+    left_update(c, wk, w.core[k].d(), w.r[k], w.r[k + 1], phi.d(), A, w.core[k].d(), w.r[k], w.r[k + 1], next.d());
+    phi = std::move(next);
+  }
+  double v = 0.0;
+  c->d2h(&v, phi.get(), sizeof v);
+  return v;
+}
+
+double l2_diff(Ctx *c, const tt_iga_geom *g, const tt_iga_solution *u, const tt_iga_solution *v) {
+  TT3 M;
+  mass_matrix(c, g, v->bl, M);
+  // w = u - v, rounded first: the rounding's orthogonalisation resolves the difference of two
+  // nearly equal TTs to FP64 accuracy relative to ||u||, so the quadratic form of w carries no
+  // cancellation between the two solutions
+  TT3 w;
+  tt_sum(c, u->u, 1.0, v->u, -1.0, w);
+  const double wn = tt_round(c, w, 1e-13, 0);
+  const double den = quadratic_form(c, M, v->n, v->p, v->u);
+  if (!(wn > 0.0)) return 0.0;
+  const double num = quadratic_form(c, M, v->n, v->p, w);
+  if (!(den > 0.0)) return -1.0;
+  return sqrt(std::max(num, 0.0) / den);
 }
 
 }  // namespace ttiga

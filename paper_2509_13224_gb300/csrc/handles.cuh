@@ -74,6 +74,9 @@ void load_core(Ctx *c, int n, int p, int nq, const double *wts, const double *N,
 BoundaryLayout boundary_layout(const tt_iga_bc_desc *bc, const int nfull[3]);
 void assemble_system(Ctx *c, const tt_iga_geom *g, const tt_iga_rhs_desc *rhs, int n_rhs, double round_tol,
                      const BoundaryLayout &bl, tt_iga_system *out);
+// Restricted mass matrix M_ab = int N_a N_b det J (band TT-matrix, mode sizes
+// (n_d - lo_d - hi_d)(2p+1)); det J by TT-cross to the geometry's tolerance.
+void mass_matrix(Ctx *c, const tt_iga_geom *g, const BoundaryLayout &bl, TT3 &M);
 // Dense restricted operator entries for (row, col) multi-index pairs (device arrays).
 void operator_entries(Ctx *c, const tt_iga_system *s, int m, const int *rows, const int *cols, double *out);
 

@@ -573,10 +573,12 @@ void qr(Ctx *c, int m, int k, const double *A, long long lda, double *Q, double 
 // precision; an angle that is only FP32-accurate leaves a relative 1e-7 of the
 // off-diagonal entry, which later sweeps remove (convergence is tested in FP64:
 // g^2 <= tol^2 a b).  A tangent that FP32 cannot represent is computed in FP64.
+// Non-convergence after 60 sweeps raises DS_BREAKDOWN in *status (may be null)
+// and writes 1 to *info (may be null; 0 when the sweeps converged).
 template <int G>
 __global__ void __launch_bounds__(1024) k_jacobi_svd(int k, const double *__restrict__ A, double *__restrict__ U,
                                                     double *__restrict__ S, double *__restrict__ V,
-                                                    double *Wg, double *Vg, int use_smem, int *status) {
+                                                    double *Wg, double *Vg, int use_smem, int *status, int *info) {
   extern __shared__ double smem[];
   __shared__ int perm[256];
   __shared__ double nrm[256];
@@ -671,6 +673,7 @@ __global__ void __launch_bounds__(1024) k_jacobi_svd(int k, const double *__rest
     if (!any) break;
   }
   if (sweep == 60 && tid == 0 && status) atomicMax(status, (int)DS_BREAKDOWN);
+  if (tid == 0 && info) *info = (sweep == 60) ? 1 : 0;
   for (int cc = warp; cc < k; cc += nw) {
     double s = 0.0;
     for (int i = lane; i < k; i += 32) s += W[(size_t)cc * k + i] * W[(size_t)cc * k + i];
@@ -700,24 +703,29 @@ __global__ void __launch_bounds__(1024) k_jacobi_svd(int k, const double *__rest
 constexpr size_t kSvdSmemMax = 200 * 1024;  // W and V panels in shared memory up to this size
 
 // Lane group and CTA size for a k x k SVD: every pair of a round gets a group.
-static void svd_launch(cudaStream_t st, int k, const double *A, double *U, double *s, double *V, double *Wg,
-                       double *Vg, int use_smem, size_t bytes, int *status) {
+// Returns the launch's own error code (cudaLaunchKernel), so a caller never
+// reports an error left behind by unrelated earlier work on the thread.
+static cudaError_t svd_launch(cudaStream_t st, int k, const double *A, double *U, double *s, double *V, double *Wg,
+                              double *Vg, int use_smem, size_t bytes, int *status, int *info) {
   const int kp = k + (k & 1), pairs = kp / 2;
   const int G = k <= 4 ? 4 : (k <= 8 ? 8 : (k <= 16 ? 16 : 32));
   const int threads = std::min(1024, std::max(32, (pairs * G + 31) / 32 * 32));
+  const void *fn;
   switch (G) {
-    case 4: k_jacobi_svd<4><<<1, threads, bytes, st>>>(k, A, U, s, V, Wg, Vg, use_smem, status); break;
-    case 8: k_jacobi_svd<8><<<1, threads, bytes, st>>>(k, A, U, s, V, Wg, Vg, use_smem, status); break;
-    case 16: k_jacobi_svd<16><<<1, threads, bytes, st>>>(k, A, U, s, V, Wg, Vg, use_smem, status); break;
+    case 4: fn = (const void *)k_jacobi_svd<4>; break;
+    case 8: fn = (const void *)k_jacobi_svd<8>; break;
+    case 16: fn = (const void *)k_jacobi_svd<16>; break;
     default:
       // the limit is raised once to the largest size any call uses: a per-call value could
       // be lowered by a concurrent call on another thread between its setting and this launch;
       // raised whenever shared memory is used, since the kernel's static arrays count against
       // the default 48 KB too
-      if (bytes > 0) set_smem_limit_once((const void *)k_jacobi_svd<32>, (int)kSvdSmemMax);
-      k_jacobi_svd<32><<<1, threads, bytes, st>>>(k, A, U, s, V, Wg, Vg, use_smem, status);
+      fn = (const void *)k_jacobi_svd<32>;
+      if (bytes > 0) set_smem_limit_once(fn, (int)kSvdSmemMax);
       break;
   }
+  void *args[] = {&k, &A, &U, &s, &V, &Wg, &Vg, &use_smem, &status, &info};
+  return cudaLaunchKernel(fn, dim3(1), dim3(threads), args, bytes, st);
 }
 
 void svd_small(Ctx *c, int k, const double *A, double *U, double *s, double *V) {
@@ -731,8 +739,7 @@ void svd_small(Ctx *c, int k, const double *A, double *U, double *s, double *V) 
     Vg = DBuf(c, (size_t)kp * k * sizeof(double));
     bytes = 0;
   }
-  svd_launch(c->stream, k, A, U, s, V, Wg.d(), Vg.d(), use_smem, bytes, c->dstatus);
-  const cudaError_t e = cudaGetLastError();
+  const cudaError_t e = svd_launch(c->stream, k, A, U, s, V, Wg.d(), Vg.d(), use_smem, bytes, c->dstatus, nullptr);
   if (e != cudaSuccess) {
     const int kp2 = k + (k & 1), G = k <= 4 ? 4 : (k <= 8 ? 8 : (k <= 16 ? 16 : 32));
     fail(TT_IGA_ERR_CUDA, "svd_small launch (k=%d, lanes per pair %d, threads %d, shared bytes %zu): %s", k, G,
@@ -745,8 +752,10 @@ void svd_small(Ctx *c, int k, const double *A, double *U, double *s, double *V) 
 //
 // Fixed scratch of the one-sided Jacobi SVD for callers that cannot allocate
 // device memory: two 256 x 256 FP64 panels (1 MiB) resident on every device
-// that loads the library, shared by all calls (each call overwrites both
-// panels before reading them, so nothing needs clearing between calls).
+// that loads the library, shared by all calls.  Each call overwrites both
+// panels before reading them (the kernel copies A into W and sets V to the
+// identity first), so nothing needs clearing between calls; the convergence
+// flag goes to the caller's own `info` word, not to the shared array.
 
 static __device__ __align__(256) double g_svd_scratch[2 * 256 * 256];
 
@@ -756,7 +765,7 @@ std::mutex g_scratch_mu;
 double *g_scratch_ptr[kMaxDevices] = {nullptr};
 }  // namespace
 
-int svd_small_noalloc(cudaStream_t stream, int k, const double *A, double *U, double *s, double *V) {
+int svd_small_noalloc(cudaStream_t stream, int k, const double *A, double *U, double *s, double *V, int *info) {
   if (k < 1 || k > 256) return TT_IGA_ERR_TOO_LARGE;
   if (!A || !U || !s || !V) return TT_IGA_ERR_ARG;
   int dev = 0;
@@ -765,16 +774,20 @@ int svd_small_noalloc(cudaStream_t stream, int k, const double *A, double *U, do
   {
     std::lock_guard<std::mutex> lock(g_scratch_mu);
     if (!g_scratch_ptr[dev]) {
-      // host code only holds a stand-in for the symbol: ask the runtime for its device address
+      // set-up, once per device with that device current: host code only holds a
+      // stand-in for the symbol, so ask the runtime for the array's device address
       void *p = nullptr;
       if (cudaGetSymbolAddress(&p, g_svd_scratch) != cudaSuccess || !p) return TT_IGA_ERR_CUDA;
       g_scratch_ptr[dev] = static_cast<double *>(p);
     }
     scratch = g_scratch_ptr[dev];
   }
-  svd_launch(stream, k, A, U, s, V, scratch, scratch + 256 * 256, 0, 0, nullptr);
+  // the launch's own return code: an error left by someone else's earlier work is
+  // neither reported as ours nor cleared
+  const cudaError_t e = svd_launch(stream, k, A, U, s, V, scratch, scratch + 256 * 256, 0, 0, nullptr, info);
+  if (e != cudaSuccess) return TT_IGA_ERR_CUDA;
   g_launches.fetch_add(1, std::memory_order_relaxed);
-  return cudaGetLastError() == cudaSuccess ? TT_IGA_OK : TT_IGA_ERR_CUDA;
+  return TT_IGA_OK;
 }
 
 // ----------------------------------------------------------------- maxvol

@@ -28,8 +28,9 @@ void qr(Ctx *c, int m, int k, const double *A, long long lda, double *Q, double 
 void svd_small(Ctx *c, int k, const double *A, double *U, double *s, double *V);
 
 // Allocation-free variant of svd_small on `stream` (k <= 256) using the
-// library's fixed device scratch; returns a tt_iga_status.
-int svd_small_noalloc(cudaStream_t stream, int k, const double *A, double *U, double *s, double *V);
+// library's fixed device scratch; *info (device, may be null) receives 0 when the
+// Jacobi sweeps converged, 1 otherwise.  Returns a tt_iga_status.
+int svd_small_noalloc(cudaStream_t stream, int k, const double *A, double *U, double *s, double *V, int *info);
 
 // Batched maxvol on `count` tall matrices U_b (m_b x r_b, row-major, ld r_b,
 // contiguous at offsets off[b] in doubles): rows_b[r_b] and B_b = U_b U_b[rows]^{-1}.

@@ -225,6 +225,15 @@ __global__ void k_tt_full(const double *G1, const double *G2, const double *G3, 
   }
 }
 
+void tt_dense(Ctx *c, const TT3 &x, double *out) {
+  // T[i1][(i2, b)] = G1[i1][a] G2[a][(i2, b)];  out[(i1, i2)][i3] = T[(i1, i2)][b] G3[b][i3]
+  const int m1 = x.m[0], m2 = x.m[1], m3 = x.m[2], r1 = x.r[1], r2 = x.r[2];
+  DBuf T(c, (size_t)m1 * m2 * r2 * sizeof(double));
+  gemm<double>(c, false, false, m1, m2 * r2, r1, 1.0, x.core[0].d(), r1, 0, x.core[1].d(), (long long)m2 * r2, 0, 0.0,
+               T.d(), (long long)m2 * r2, 0, 1);
+  gemm<double>(c, false, false, m1 * m2, m3, r2, 1.0, T.d(), r2, 0, x.core[2].d(), m3, 0, 0.0, out, m3, 0, 1);
+}
+
 void tt_full(Ctx *c, const TT3 &x, double *out) {
   long long tot = (long long)x.m[0] * x.m[1] * x.m[2];
   k_tt_full<<<grid1d(tot, 256), 256, 0, c->stream>>>(x.core[0].d(), x.core[1].d(), x.core[2].d(), x.m[0], x.m[1],

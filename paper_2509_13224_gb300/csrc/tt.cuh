@@ -24,6 +24,9 @@ double tt_norm(Ctx *c, const TT3 &x);
 void tt_eval_points(Ctx *c, const TT3 &x, int m, const int *idx, double *out);
 // Dense tensor out[i3][i2][i1] (i1 fastest; device) of a small TT.
 void tt_full(Ctx *c, const TT3 &x, double *out);
+// Dense tensor out[i1][i2][i3] (i3 fastest; device) by two GEMMs: cost m1 r1 m2 r2 + m1 m2 r2 m3,
+// for TTs whose ranks are too large for the per-entry kernel of tt_full.
+void tt_dense(Ctx *c, const TT3 &x, double *out);
 // W[j][l] = S[j] V[l][j] for j < r: the first r rows of diag(S) V^T (V is k x k).
 void svt(Ctx *c, const double *S, const double *V, int k, int r, double *W);
 // Transposes of a core (row-major r0 x (m r1) <-> (m r1) x r0).

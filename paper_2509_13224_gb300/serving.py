@@ -19,9 +19,14 @@ import time
 
 import numpy as np
 
-from . import (FP64, MIXED_FP32, geom_desc, rhs_desc, solve_opts, tt_iga_assemble, tt_iga_ctx_create,
-               tt_iga_ctx_destroy, tt_iga_geom_destroy, tt_iga_geometry, tt_iga_solution_cores,
-               tt_iga_solution_destroy, tt_iga_solve, tt_iga_system_destroy)
+from . import (FP64, MIXED_FP32, MIXED_TF32, geom_desc, rhs_desc, solve_opts, tt_iga_assemble, tt_iga_ctx_create,
+               tt_iga_ctx_destroy, tt_iga_geom_destroy, tt_iga_geometry, tt_iga_import_cores, tt_iga_l2_diff,
+               tt_iga_solution_cores, tt_iga_solution_destroy, tt_iga_solve, tt_iga_system_destroy)
+
+
+# The "auto" policy solves requests with a tolerance at or above this in mixed precision
+# and tighter ones in FP64.
+AUTO_MIXED_MIN_TOL = 1e-7
 
 
 def footprint_bytes(n, p, rank=48, op_rank=24, rhs_rank=16):
@@ -53,10 +58,11 @@ class Server:
     """lanes: concurrent solves; budget_bytes: device memory allowed for admitted requests."""
 
     def __init__(self, device=0, lanes=4, budget_bytes=None, precision_policy="auto", keep_cores=False,
-                 cross_tol=1e-10, round_tol=1e-12, runner=None):
+                 cross_tol=1e-10, round_tol=1e-12, runner=None, mixed_precision=MIXED_FP32):
         """runner: None (each request is solved by libtt_iga.so on the lane's context) or a
         callable runner(request, t0) -> record with the keys of _run_one, for driving the
-        scheduler without a GPU."""
+        scheduler without a GPU.  mixed_precision: the precision mode of mixed requests
+        (MIXED_FP32 or MIXED_TF32)."""
         self.device = device
         self.lanes = int(lanes)
         self.runner = runner
@@ -67,6 +73,7 @@ class Server:
         self.budget = int(budget_bytes)
         self.in_use = 0
         self.policy = precision_policy
+        self.mixed = mixed_precision
         self.keep_cores = keep_cores
         self.cross_tol, self.round_tol = cross_tol, round_tol
         self._cv = threading.Condition()
@@ -77,14 +84,14 @@ class Server:
         if self.policy == "fp64":
             return FP64
         if self.policy == "mixed":
-            return MIXED_FP32
-        return MIXED_FP32 if req.tol >= 1e-7 else FP64
+            return self.mixed
+        return self.mixed if req.tol >= AUTO_MIXED_MIN_TOL else FP64
 
     def _run_one(self, ctx, req, t0):
         rec = {"rid": req.rid, "n": req.n, "p": req.p, "tol": req.tol, "dofs": req.n ** 3,
                "arrival": req.arrival}
         prec = self._precision(req)
-        rec["precision"] = "fp64" if prec == FP64 else "mixed_fp32"
+        rec["precision"] = {FP64: "fp64", MIXED_FP32: "mixed_fp32", MIXED_TF32: "mixed_tf32"}[prec]
         rec["start"] = time.perf_counter() - t0
         g = s = u = None
         try:
@@ -189,6 +196,58 @@ def summarize(records, wall):
     return {"requests": len(records), "ok": len(ok), "p50_ms": float(np.percentile(lat, 50) * 1e3),
             "p99_ms": float(np.percentile(lat, 99) * 1e3), "dofs_per_s": dofs / span if ok else 0.0,
             "wall_s": wall}
+
+
+def summarize_by(records, key):
+    """summarize() per value of records[key] (e.g. the requested tolerance), over the session's wall."""
+    groups = {}
+    for r in records:
+        groups.setdefault(r.get(key), []).append(r)
+    out = {}
+    for k, recs in sorted(groups.items(), key=lambda kv: str(kv[0])):
+        ok = [r for r in recs if r.get("status") == 0]
+        lat = np.array([r["latency"] for r in ok]) if ok else np.array([math.nan])
+        span = (max(r["end"] for r in ok) - min(r["arrival"] for r in ok)) if ok else math.nan
+        out[str(k)] = {"requests": len(recs), "ok": len(ok), "p50_ms": float(np.percentile(lat, 50) * 1e3),
+                       "p99_ms": float(np.percentile(lat, 99) * 1e3),
+                       "dofs_per_s": sum(r["dofs"] for r in ok) / span if ok else 0.0}
+    return out
+
+
+def accuracy_vs(requests, records, reference, device=0, cross_tol=1e-10, round_tol=1e-12):
+    """Relative L2 difference of each request's solution in `records` from its solution in
+    `reference` (both kept with keep_cores): the request's system is rebuilt, both solutions are
+    imported from their cores and compared on the mapped domain (tt_iga_l2_diff).  Returns
+    {"per_request": {rid: diff}, "max_by_tol": ..., "median_by_tol": ...}."""
+    by_id = {r.rid: r for r in requests}
+    ref = {r["rid"]: r for r in reference if r.get("status") == 0 and "cores" in r}
+    ctx = tt_iga_ctx_create(None, device)
+    per = {}
+    try:
+        for rec in records:
+            rid = rec["rid"]
+            if rec.get("status") != 0 or "cores" not in rec or rid not in ref:
+                continue
+            req = by_id[rid]
+            g = tt_iga_geometry(ctx, geom_desc(req.geometry, req.p, req.n, cross_tol=cross_tol, seed=req.seed))
+            s = tt_iga_assemble(ctx, g, [rhs_desc(req.modes)], round_tol=round_tol)
+            u = tt_iga_import_cores(ctx, s, rec["cores"])
+            v = tt_iga_import_cores(ctx, s, ref[rid]["cores"])
+            try:
+                per[rid] = tt_iga_l2_diff(ctx, g, u, v)
+            finally:
+                tt_iga_solution_destroy(u)
+                tt_iga_solution_destroy(v)
+                tt_iga_system_destroy(s)
+                tt_iga_geom_destroy(g)
+    finally:
+        tt_iga_ctx_destroy(ctx)
+    by_tol = {}
+    for rid, e in per.items():
+        by_tol.setdefault(str(by_id[rid].tol), []).append(e)
+    return {"per_request": per, "compared": len(per),
+            "max_by_tol": {k: float(max(v)) for k, v in by_tol.items()},
+            "median_by_tol": {k: float(np.median(v)) for k, v in by_tol.items()}}
 
 
 def synthetic_stream(count, rate_hz, seed, n_lo=32, n_hi=1024, tols=(1e-6, 1e-8)):
