@@ -247,11 +247,19 @@ enum { TT_IGA_FP64 = 0, TT_IGA_MIXED_FP32 = 1, TT_IGA_MIXED_TF32 = 2 };
 /* AMEn options (Section 4.1.2).  tol: target relative residual
  * ||F - K u||_2 / ||F||_2.  precision FP64: every operator application,
  * inner product, residual and update in FP64 (the band block-Jacobi
- * preconditioner of the local PCG is factorised in FP64 and applied in FP32;
- * it shapes the iteration only).  MIXED_FP32: the local PCG runs in FP32
- * inside FP64 iterative refinement of each local system; interfaces,
- * residuals and QR/SVD truncation stay FP64.  MIXED_TF32 is reserved and
- * returns TT_IGA_ERR_ARG.  Zero fields take the defaults in brackets. */
+ * preconditioner of the local PCG is factorised and applied in FP32; it
+ * shapes the iteration only).  MIXED_FP32: the local PCG runs in FP32 on the
+ * CUDA cores inside FP64 iterative refinement of each local system;
+ * interfaces, residuals and QR/SVD truncation stay FP64.  MIXED_TF32: as
+ * MIXED_FP32, with the two dense contractions of each local operator
+ * application (the right-interface stage p PhiR^T and the left-interface stage
+ * PhiL T2) on the tensor cores: tcgen05 kind::tf32 MMAs with FP32
+ * accumulators in tensor memory, each operand split into TF32 high and low
+ * parts and three products summed (3xTF32, about FP32 accuracy); the banded
+ * operator stage and the preconditioner stay on CUDA cores.  A local system
+ * whose operands do not fit the kernel's shared-memory and tensor-memory budget
+ * is solved on CUDA cores (stats.local_matvecs_tensor counts the applications
+ * that used the tensor cores).  Zero fields take the defaults in brackets. */
 typedef struct {
   double tol;       /* [1e-8] */
   int precision;    /* [TT_IGA_FP64] */
@@ -273,6 +281,7 @@ typedef struct {
   long long local_matvecs_fp64;
   double ms_total;          /* device time of the solve (CUDA events) */
   int converged;
+  long long local_matvecs_tensor;  /* local operator applications on the tensor cores (MIXED_TF32) */
 } tt_iga_stats;
 
 /* Solve K u = F for right-hand side opts->rhs_index.  On ERR_NOT_CONVERGED the

@@ -88,12 +88,13 @@ class Stats(ctypes.Structure):
     _fields_ = [("sweeps", ctypes.c_int), ("ranks", ctypes.c_int * 2), ("rel_residual", ctypes.c_double),
                 ("local_residual", ctypes.c_double), ("local_matvecs", ctypes.c_longlong),
                 ("local_matvecs_fp64", ctypes.c_longlong), ("ms_total", ctypes.c_double),
-                ("converged", ctypes.c_int)]
+                ("converged", ctypes.c_int), ("local_matvecs_tensor", ctypes.c_longlong)]
 
     def as_dict(self):
         return {"sweeps": self.sweeps, "ranks": [self.ranks[0], self.ranks[1]],
                 "rel_residual": self.rel_residual, "local_residual": self.local_residual,
                 "local_matvecs": self.local_matvecs, "local_matvecs_fp64": self.local_matvecs_fp64,
+                "local_matvecs_tensor": self.local_matvecs_tensor,
                 "ms_total": self.ms_total, "converged": bool(self.converged)}
 
 

@@ -293,11 +293,12 @@ struct Amen {
     a.rl = rl(k); a.rr = rr(k); a.Rl = R[k]; a.Rr = R[k + 1]; a.n = n(k); a.p = S->p;
     a.tol2 = tol * tol;
     a.maxit = maxit;
+    a.tc = (sizeof(T) == 4 && o.precision == TT_IGA_MIXED_TF32) ? 1 : 0;
     const int grid = pcg_fused_grid<T>(c, a);
-    DBuf vec(c, 5 * N * sizeof(T)), t1(c, (size_t)grid * a.t1_stride * sizeof(T)),
-        t2(c, (size_t)grid * a.t2_stride * sizeof(T)), aux(c, (3 * (size_t)grid + 8) * sizeof(double));
+    const size_t slab_scratch = a.dense_off >= 0 ? 0 : (size_t)grid * a.dense_stride;  // none in shared memory
+    DBuf vec(c, 5 * N * sizeof(T)), scr(c, slab_scratch * sizeof(T)), aux(c, (3 * (size_t)grid + 8) * sizeof(double));
     a.r = vec.as<T>(); a.z = a.r + N; a.pv = a.z + N; a.pv2 = a.pv + N; a.q = a.pv2 + N;
-    a.T1 = t1.as<T>(); a.T2 = t2.as<T>();
+    a.scratch = scr.as<T>();
     a.part = aux.d();
     a.out = aux.d() + 3 * grid;
     a.bar = reinterpret_cast<Barrier *>(aux.d() + 3 * grid + 2);
@@ -323,7 +324,8 @@ struct Amen {
       }
       fprintf(stderr, "[tt_iga pcg] core %d %s %s grid %d slab %d n %d rl %d rr %d R %d/%d it %d init %.1f us, per "
                       "iteration dense %.1f precond %.1f us\n",
-              k, sizeof(T) == 8 ? "fp64" : "fp32", a.edge ? "block-band" : "band-jacobi", grid, a.slab, a.n, a.rl, a.rr,
+              k, sizeof(T) == 8 ? "fp64" : (a.tc ? "fp32+tf32-tc" : "fp32"), a.edge ? "block-band" : "band-jacobi", grid,
+              a.slab, a.n, a.rl, a.rr,
               a.Rl, a.Rr, (int)hout[0],
               (tr[1] - tr[0]) * 1e-3, iters ? ph[0] / iters * 1e-3 : 0.0, iters ? ph[1] / iters * 1e-3 : 0.0);
       if (a.edge) {
@@ -336,7 +338,9 @@ struct Amen {
     }
     int err = 0;
     memcpy(&err, &hout[3], sizeof(int));
-    if (err) fail(TT_IGA_ERR_TIMEOUT, "pcg: a %s wait ran out", err == 2 ? "staging copy" : "grid barrier");
+    if (err)
+      fail(TT_IGA_ERR_TIMEOUT, "pcg: a %s wait ran out",
+           err == 2 ? "staging copy" : (err == 3 ? "tensor-core completion" : "grid barrier"));
     const int it = (int)hout[0];
     last_pcg_converged = (it < maxit) && hout[1] <= a.tol2;
     {
@@ -351,6 +355,7 @@ struct Amen {
     }
     st.local_matvecs += it;
     if (sizeof(T) == 8) st.local_matvecs_fp64 += it;
+    if (a.tc) st.local_matvecs_tensor += it;
     return it;
   }
 

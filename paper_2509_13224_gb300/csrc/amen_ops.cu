@@ -156,31 +156,48 @@ template <typename T> __device__ __forceinline__ T recip_sqrt(T v);
 template <> __device__ __forceinline__ float recip_sqrt<float>(float v) { return rsqrtf(v); }
 template <> __device__ __forceinline__ double recip_sqrt<double>(double v) { return 1.0 / sqrt(v); }
 
+// Symmetrised band entries in the factor's type, S[i][k][pair] = (A(i, i-PB+k) +
+// A(i-PB+k, i)) / 2 for k < PB (0 outside the matrix) and S[i][PB][pair] = A(i, i),
+// from P[a][i][o][b] (pair = a rr + b): one thread per entry, so the FP64 reads and
+// conversions leave the sequential factorisation below.
 template <typename T, int PB>
-__global__ void k_band_cholesky(const double *__restrict__ Pm, int rl, int n, int rr, T *__restrict__ L, int *status) {
-  // rows are loaded in groups of RG, one group ahead, so the memory latency is
-  // exposed once per group instead of once per row
-  constexpr int RG = 4;
+__global__ void k_band_sym(const double *__restrict__ Pm, int rl, int n, int rr, T *__restrict__ S) {
   const int npair = rl * rr, b = 2 * PB + 1;
-  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < npair; t += gridDim.x * blockDim.x) {
+  const long long tot = (long long)n * (PB + 1) * npair;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < tot; e += (long long)gridDim.x * blockDim.x) {
+    const int t = (int)(e % npair);
+    const long long q = e / npair;
+    const int k = (int)(q % (PB + 1)), i = (int)(q / (PB + 1));
     const int a = t / rr, bb = t % rr;
     const double *Pp = Pm + (long long)a * n * b * rr + bb;
+    T v;
+    if (k == PB) {
+      v = (T)Pp[((long long)i * b + PB) * rr];
+    } else {
+      const int j = i - PB + k;
+      v = (j >= 0) ? (T)(0.5 * (Pp[((long long)i * b + k) * rr] + Pp[((long long)j * b + (2 * PB - k)) * rr])) : T(0);
+    }
+    S[e] = v;
+  }
+}
+
+template <typename T, int PB>
+__global__ void k_band_cholesky(const T *__restrict__ S, int rl, int n, int rr, T *__restrict__ L, int *status) {
+  // rows are loaded in groups of RG, one group ahead (coalesced over the pairs of a
+  // warp), so the memory latency is exposed once per group instead of once per row
+  constexpr int RG = 8;
+  const int npair = rl * rr;
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < npair; t += gridDim.x * blockDim.x) {
     T win[PB][PB + 1];
 #pragma unroll
     for (int q = 0; q < PB; ++q)
 #pragma unroll
       for (int k = 0; k <= PB; ++k) win[q][k] = T(0);
     bool bad = false;
-    // symmetrised band entries of a row: A(i, i-PB+k) for k <= PB
     auto load_row = [&](int i, T *out) {
       if (i >= n) return;
 #pragma unroll
-      for (int k = 0; k < PB; ++k) {
-        const int j = i - PB + k;
-        out[k] = (j >= 0) ? (T)(0.5 * (Pp[((long long)i * b + k) * rr] + Pp[((long long)j * b + (2 * PB - k)) * rr]))
-                          : T(0);
-      }
-      out[PB] = (T)Pp[((long long)i * b + PB) * rr];
+      for (int k = 0; k <= PB; ++k) out[k] = S[((long long)i * (PB + 1) + k) * npair + t];
     };
     T nxt[RG][PB + 1];
 #pragma unroll
@@ -232,6 +249,17 @@ __global__ void k_band_cholesky(const double *__restrict__ Pm, int rl, int n, in
   }
 }
 
+template <typename T, int PB> static void band_factor(Ctx *c, const double *P, int rl, int n, int rr, T *L) {
+  DBuf Sb(c, (size_t)n * (PB + 1) * rl * rr * sizeof(T));
+  const long long tot = (long long)n * (PB + 1) * rl * rr;
+  k_band_sym<T, PB><<<grid1d(tot, 256), 256, 0, c->stream>>>(P, rl, n, rr, Sb.as<T>());
+  TTI_LAUNCH();
+  // one pair per thread; small CTAs spread the independent chains over many SMs
+  const unsigned grid = grid1d((long long)rl * rr, 32), blk = 32;
+  k_band_cholesky<T, PB><<<grid, blk, 0, c->stream>>>(Sb.as<T>(), rl, n, rr, L, c->dstatus);
+  TTI_LAUNCH();
+}
+
 template <typename T>
 void precond_build(Ctx *c, const double *PhiL, int rl, const BandCore &A, const double *PhiR, int rr, T *L) {
   const int n = A.n, b = A.b, Rl = A.Rl, Rr = A.Rr;
@@ -247,80 +275,19 @@ void precond_build(Ctx *c, const double *PhiL, int rl, const BandCore &A, const 
   DBuf P(c, (size_t)rl * n * b * rr * sizeof(double));
   gemm<double>(c, false, false, rl, n * b * rr, Rl, 1.0, dL.d(), Rl, 0, W.d(), (long long)n * b * rr, 0, 0.0, P.d(),
                (long long)n * b * rr, 0, 1);
-  const unsigned grid = grid1d((long long)rl * rr, 32), blk = 32;
   switch (A.p) {
-    case 1: k_band_cholesky<T, 1><<<grid, blk, 0, c->stream>>>(P.d(), rl, n, rr, L, c->dstatus); break;
-    case 2: k_band_cholesky<T, 2><<<grid, blk, 0, c->stream>>>(P.d(), rl, n, rr, L, c->dstatus); break;
-    case 3: k_band_cholesky<T, 3><<<grid, blk, 0, c->stream>>>(P.d(), rl, n, rr, L, c->dstatus); break;
-    case 4: k_band_cholesky<T, 4><<<grid, blk, 0, c->stream>>>(P.d(), rl, n, rr, L, c->dstatus); break;
-    case 5: k_band_cholesky<T, 5><<<grid, blk, 0, c->stream>>>(P.d(), rl, n, rr, L, c->dstatus); break;
-    case 6: k_band_cholesky<T, 6><<<grid, blk, 0, c->stream>>>(P.d(), rl, n, rr, L, c->dstatus); break;
-    case 7: k_band_cholesky<T, 7><<<grid, blk, 0, c->stream>>>(P.d(), rl, n, rr, L, c->dstatus); break;
+    case 1: band_factor<T, 1>(c, P.d(), rl, n, rr, L); break;
+    case 2: band_factor<T, 2>(c, P.d(), rl, n, rr, L); break;
+    case 3: band_factor<T, 3>(c, P.d(), rl, n, rr, L); break;
+    case 4: band_factor<T, 4>(c, P.d(), rl, n, rr, L); break;
+    case 5: band_factor<T, 5>(c, P.d(), rl, n, rr, L); break;
+    case 6: band_factor<T, 6>(c, P.d(), rl, n, rr, L); break;
+    case 7: band_factor<T, 7>(c, P.d(), rl, n, rr, L); break;
     default: fail(TT_IGA_ERR_ARG, "preconditioner: degree %d outside 1..7", A.p);
   }
-  TTI_LAUNCH();
 }
-template void precond_build<double>(Ctx *, const double *, int, const BandCore &, const double *, int, double *);
 template void precond_build<float>(Ctx *, const double *, int, const BandCore &, const double *, int, float *);
 
-// Solve L L^T z = r per (alpha, beta) pair with the factors of k_band_cholesky
-// (reciprocal diagonal in slot PB).  Forward: y_i = (r_i - sum_k L(i,i-PB+k)
-// y_{i-PB+k}) / L(i,i); backward: z_i = (y_i - sum_{d=1..PB} L(i+d,i) z_{i+d}) /
-// L(i,i).  The last PB solution values are kept in registers; the factor
-// loads do not depend on them and pipeline freely.
-template <typename T, int PB>
-__global__ void k_band_solve(const T *__restrict__ L, int rl, int n, int rr, const T *__restrict__ r,
-                             T *__restrict__ z) {
-  const int npair = rl * rr;
-  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < npair; t += gridDim.x * blockDim.x) {
-    const int a = t / rr, bb = t % rr;
-    const long long base = (long long)a * n * rr + bb;
-    T w[PB];
-#pragma unroll
-    for (int k = 0; k < PB; ++k) w[k] = T(0);
-    for (int i = 0; i < n; ++i) {
-      const T *Li = L + (long long)i * (PB + 1) * npair + t;
-      T sv = r[base + (long long)i * rr];
-#pragma unroll
-      for (int k = 0; k < PB; ++k) sv -= Li[(long long)k * npair] * w[k];
-      const T y = sv * Li[(long long)PB * npair];
-      z[base + (long long)i * rr] = y;
-#pragma unroll
-      for (int k = 0; k + 1 < PB; ++k) w[k] = w[k + 1];
-      w[PB - 1] = y;
-    }
-#pragma unroll
-    for (int k = 0; k < PB; ++k) w[k] = T(0);  // w[d-1] = z_{i+d}
-    for (int i = n - 1; i >= 0; --i) {
-      T sv = z[base + (long long)i * rr];
-#pragma unroll
-      for (int d = 1; d <= PB; ++d)
-        if (i + d < n) sv -= L[((long long)(i + d) * (PB + 1) + (PB - d)) * npair + t] * w[d - 1];
-      const T zi = sv * L[((long long)i * (PB + 1) + PB) * npair + t];
-      z[base + (long long)i * rr] = zi;
-#pragma unroll
-      for (int d = PB - 1; d > 0; --d) w[d] = w[d - 1];
-      w[0] = zi;
-    }
-  }
-}
-
-template <typename T> void precond_apply(Ctx *c, const T *L, int rl, int n, int p, int rr, const T *r, T *z) {
-  const unsigned grid = grid1d((long long)rl * rr, 32), blk = 32;
-  switch (p) {
-    case 1: k_band_solve<T, 1><<<grid, blk, 0, c->stream>>>(L, rl, n, rr, r, z); break;
-    case 2: k_band_solve<T, 2><<<grid, blk, 0, c->stream>>>(L, rl, n, rr, r, z); break;
-    case 3: k_band_solve<T, 3><<<grid, blk, 0, c->stream>>>(L, rl, n, rr, r, z); break;
-    case 4: k_band_solve<T, 4><<<grid, blk, 0, c->stream>>>(L, rl, n, rr, r, z); break;
-    case 5: k_band_solve<T, 5><<<grid, blk, 0, c->stream>>>(L, rl, n, rr, r, z); break;
-    case 6: k_band_solve<T, 6><<<grid, blk, 0, c->stream>>>(L, rl, n, rr, r, z); break;
-    case 7: k_band_solve<T, 7><<<grid, blk, 0, c->stream>>>(L, rl, n, rr, r, z); break;
-    default: fail(TT_IGA_ERR_ARG, "preconditioner: degree %d outside 1..7", p);
-  }
-  TTI_LAUNCH();
-}
-template void precond_apply<double>(Ctx *, const double *, int, int, int, int, const double *, double *);
-template void precond_apply<float>(Ctx *, const float *, int, int, int, int, const float *, float *);
 
 // out[(g,a)][i][(d,c)] = sum_o A[g][i][o][d] U[a][i+o-p][c]
 __global__ void k_tt_matvec_core(const double *__restrict__ A, int Rl, int n, int b, int p, int Rr,

@@ -51,7 +51,6 @@ void rhs_right_update(Ctx *c, Work<double> &w, const double *Z, int tl, int tr, 
 // factorised by band Cholesky.  L layout: [n][p+1][rl*rr] (pair index fastest).
 template <typename T>
 void precond_build(Ctx *c, const double *PhiL, int rl, const BandCore &A, const double *PhiR, int rr, T *L);
-template <typename T> void precond_apply(Ctx *c, const T *L, int rl, int n, int p, int rr, const T *r, T *z);
 
 // Matrix-vector product of the band TT-matrix with a TT core: out[(g,a)][i][(d,b)].
 void tt_matvec_core(Ctx *c, const BandCore &A, const double *U, int ul, int ur, double *out);

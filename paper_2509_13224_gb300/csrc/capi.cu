@@ -388,8 +388,8 @@ static tt_iga_solve_opts solve_defaults(const tt_iga_solve_opts *opts) {
   if (o.max_rank <= 0) o.max_rank = 256;
   o.max_rank = std::min(o.max_rank, 240);
   if (o.local_maxit <= 0) o.local_maxit = 500;
-  TTI_CHECK_ARG(o.precision == TT_IGA_FP64 || o.precision == TT_IGA_MIXED_FP32,
-                "solve: precision %d not available (FP64 and MIXED_FP32 are built)", o.precision);
+  TTI_CHECK_ARG(o.precision == TT_IGA_FP64 || o.precision == TT_IGA_MIXED_FP32 || o.precision == TT_IGA_MIXED_TF32,
+                "solve: precision %d is not one of FP64, MIXED_FP32, MIXED_TF32", o.precision);
   return o;
 }
 

@@ -14,9 +14,12 @@
 // iteration limit; on expiry it raises an error flag and the kernel returns.
 #include <algorithm>
 
+#include <type_traits>
+
 #include "amen_ops.cuh"
 #include "bbprec.cuh"
 #include "pcg_fused.cuh"
+#include "tc_tf32.cuh"
 
 namespace ttiga {
 
@@ -27,7 +30,7 @@ struct Barrier {
 
 namespace {
 
-constexpr size_t kPcgSmemBytes = 200 * 1024;
+constexpr size_t kPcgSmemBytes = 220 * 1024;
 constexpr long long kSpinLimit = 1LL << 22;  // polls of about 0.25-0.5 us: one to two seconds
 
 __device__ __forceinline__ unsigned int ld_acquire(const unsigned int *p) {
@@ -641,6 +644,58 @@ __global__ void __launch_bounds__(256, 1) k_pcg_fused(PcgArgs<T> a) {
 
   int slot = 0;
   trace_mark(a.trace, a.trace_cap, slot);
+  // The interfaces do not change during the solve: with room for them they are copied
+  // into shared memory once (PhiR rows padded to an odd stride against bank conflicts).
+  extern __shared__ __align__(16) unsigned char dsm_raw[];
+  const int phr_ld = a.iface_off >= 0 ? a.phr_ld : rr;  // row stride of PhiR where it is read from
+  const T *PhiRs = a.PhiR, *PhiLs = a.PhiL;
+  if (a.iface_off >= 0) {
+    T *pr_s = reinterpret_cast<T *>(dsm_raw + a.iface_off);
+    T *pl_s = pr_s + (long long)rr * Rr * phr_ld;
+    for (int e = threadIdx.x; e < rr * Rr * rr; e += blockDim.x) pr_s[(e / rr) * phr_ld + e % rr] = a.PhiR[e];
+    for (int e = threadIdx.x; e < rl * Rl * rl; e += blockDim.x) pl_s[e] = a.PhiL[e];
+    PhiRs = pr_s;
+    PhiLs = pl_s;
+    __syncthreads();
+  }
+  // Tensor-core stages (MIXED_TF32, FP32 PCG only): TMEM for the accumulators, one
+  // completion barrier, and the two interface operands split into TF32 high and low
+  // parts in the canonical K-major layout, built once per solve.
+  constexpr bool kTc = std::is_same<T, float>::value;
+  __shared__ uint32_t tc_tmem;
+  __shared__ __align__(8) uint64_t tc_bar;
+  uint32_t tc_phase = 0;
+  const int szPR = tc::operand_bytes(a.tcNA, a.tcKA), szPL = tc::operand_bytes(a.tcNC, a.tcKC),
+            szPS = tc::operand_bytes(a.tcMA, a.tcKA);
+  unsigned char *opPRh = dsm_raw + (a.tc ? a.tc_off : 0);
+  unsigned char *opPRl = opPRh + szPR, *opPLh = opPRl + szPR, *opPLl = opPLh + szPL;
+  unsigned char *opPSh = opPLl + szPL, *opPSl = opPSh + szPS;
+  unsigned char *opT2h = opPSl + szPS, *opT2l = opT2h + tc::operand_bytes(a.tcMC, a.tcKC);
+  if constexpr (kTc) {
+    if (a.tc) {
+      if (threadIdx.x < 32) tc::tmem_alloc(&tc_tmem, (uint32_t)a.tc_cols);
+      if (threadIdx.x == 0) tc::mbar_init1(&tc_bar);
+      for (int e = threadIdx.x; e < a.tcNA * a.tcKA; e += blockDim.x) {
+        const int r = e / a.tcKA, k = e % a.tcKA;  // row c Rr + d, column f
+        const float x = (r < rr * Rr && k < rr) ? (float)a.PhiR[(long long)r * rr + k] : 0.f;
+        const float h = tc::to_tf32(x);
+        *reinterpret_cast<float *>(opPRh + tc::operand_offset(r, k, a.tcKA)) = h;
+        *reinterpret_cast<float *>(opPRl + tc::operand_offset(r, k, a.tcKA)) = tc::to_tf32(x - h);
+      }
+      for (int e = threadIdx.x; e < a.tcNC * a.tcKC; e += blockDim.x) {
+        const int r = e / a.tcKC, k = e % a.tcKC;  // row al, column g rl + aa
+        const float x = (r < rl && k < Rl * rl) ? (float)a.PhiL[(long long)r * Rl * rl + k] : 0.f;
+        const float h = tc::to_tf32(x);
+        *reinterpret_cast<float *>(opPLh + tc::operand_offset(r, k, a.tcKC)) = h;
+        *reinterpret_cast<float *>(opPLl + tc::operand_offset(r, k, a.tcKC)) = tc::to_tf32(x - h);
+      }
+      tc::fence_proxy_async();
+      tc::fence_before_sync();
+      __syncthreads();
+      tc::fence_after_sync();
+    }
+  }
+  bool aborted = false;
   __shared__ __align__(8) unsigned long long bb_bars[2];
   unsigned bb_ph = 0;
   if (a.edge && blockIdx.x == 0) {
@@ -657,95 +712,288 @@ __global__ void __launch_bounds__(256, 1) k_pcg_fused(PcgArgs<T> a) {
   else band_systems<T, PB>(a, nullptr, 0.0, true, rr_loc, rz_loc);
   cta_partial(rr_loc, p_rr);
   cta_partial(rz_loc, p_rz);
-  if (!grid_sync(a.bar, G, a.err)) return;
+  if (!grid_sync(a.bar, G, a.err)) aborted = true;
   trace_mark(a.trace, a.trace_cap, slot);
-  double res2 = grid_total(p_rr);
-  double rz = grid_total(p_rz), rz_prev = 1.0;
+  double res2 = aborted ? 0.0 : grid_total(p_rr);
+  double rz = aborted ? 0.0 : grid_total(p_rz), rz_prev = 1.0;
   int it = 0;
-  for (; it < a.maxit && res2 > a.tol2; ++it) {
+  for (; !aborted && it < a.maxit && res2 > a.tol2; ++it) {
     const double beta = (it == 0 || rz_prev == 0.0) ? 0.0 : rz / rz_prev;
     T *pcur = (it & 1) ? a.pv2 : a.pv;
     const T *pprev = (it & 1) ? a.pv : a.pv2;
     // A+B+C on slabs of S mode rows, one slab per CTA at a time, so only CTA barriers
-    // are needed: T1 on the slab plus its +-p halo rows (recomputed from z and p_prev),
-    // T2 and q on the slab rows, <p, q> partial.  p rows of the slab are written once.
+    // are needed: p on the slab plus its +-p halo rows (recomputed from z and p_prev),
+    // T1 on those rows, T2 and q on the slab rows, <p, q> partial.  p rows of the slab
+    // are written once.  The slab scratch lives in shared memory when it fits.
     double pq_loc = 0.0;
     {
       const int S = a.slab, nslab = (n + S - 1) / S;
-      T *T1s = a.T1 + (long long)blockIdx.x * a.t1_stride;
-      T *T2s = a.T2 + (long long)blockIdx.x * a.t2_stride;
+      T *Ps = a.dense_off >= 0 ? reinterpret_cast<T *>(dsm_raw + a.dense_off)
+                               : a.scratch + (long long)blockIdx.x * a.dense_stride;
+      T *T1s = Ps + a.p_stride;
+      T *T2s = T1s + a.t1_stride;
       for (int sl = blockIdx.x; sl < nslab; sl += G) {
         const int i0 = sl * S, i1 = min(n, i0 + S);
         const int j0 = max(0, i0 - PB), j1 = min(n, i1 + PB);
         const int nj = j1 - j0, ni = i1 - i0;
-        // A: T1s[aa][jj][c][d] = sum_f p[aa][j][f] PhiR[c][d][f], p = z + beta p_prev
-        const int nA1 = rl * nj * rr * Rr;
-        for (int e = threadIdx.x; e < nA1; e += blockDim.x) {
-          const int d = e % Rr;
-          int t = e / Rr;
-          const int c = t % rr;
-          t /= rr;
-          const int jj = t % nj, aa = t / nj;
-          const int j = j0 + jj;
-          const long long row = (long long)aa * n + j;
-          const T *zr = a.z + row * rr;
-          const T *pr = pprev + row * rr;
-          const T *ph = a.PhiR + ((long long)c * Rr + d) * rr;
-          const bool writer = (c == 0 && d == 0 && j >= i0 && j < i1);
-          T s0 = T(0), s1 = T(0);
-          for (int f = 0; f < rr; ++f) {
-            const T pf = (it == 0) ? zr[f] : zr[f] + (T)beta * pr[f];
-            if (writer) pcur[row * rr + f] = pf;
-            if (f & 1) s1 += pf * ph[f]; else s0 += pf * ph[f];
+        // A0: Ps[aa][jj][f] = z + beta p_prev on the slab and halo rows (contiguous in f, jj)
+        const int nP = rl * nj * rr;
+        bool use_tc = false;
+        if constexpr (kTc) use_tc = a.tc != 0;
+        if (!use_tc) {
+          for (int e = threadIdx.x; e < nP; e += blockDim.x) {
+            const int f = e % rr;
+            const int t = e / rr;
+            const int jj = t % nj, aa = t / nj;
+            const int j = j0 + jj;
+            const long long idx = ((long long)aa * n + j) * rr + f;
+            const T pf = (it == 0) ? a.z[idx] : a.z[idx] + (T)beta * pprev[idx];
+            Ps[e] = pf;
+            if (j >= i0 && j < i1) pcur[idx] = pf;
           }
-          T1s[e] = s0 + s1;
+          __syncthreads();
+        }
+        if constexpr (kTc) {
+          if (use_tc) {
+            // A0 with the tensor-core operand: every padded position of the Ps operand
+            // (rows aa nj + jj, columns f) gets its TF32 high and low parts or zero; the
+            // positions of the T2 operand that stage B does not write are zeroed.  Then
+            // T1 = Ps PhiR^T by tcgen05 (3xTF32), read back from TMEM into T1s.
+            for (int e = threadIdx.x; e < a.tcMA * a.tcKA; e += blockDim.x) {
+              const int t = e / a.tcKA, f = e % a.tcKA;
+              float pf = 0.f;
+              if (t < rl * nj && f < rr) {
+                const int jj = t % nj, aa = t / nj;
+                const int j = j0 + jj;
+                const long long idx = ((long long)aa * n + j) * rr + f;
+                pf = (it == 0) ? (float)a.z[idx] : (float)(a.z[idx] + (T)beta * pprev[idx]);
+                Ps[t * rr + f] = (T)pf;
+                if (j >= i0 && j < i1) pcur[idx] = (T)pf;
+              }
+              const float h = tc::to_tf32(pf);
+              *reinterpret_cast<float *>(opPSh + tc::operand_offset(t, f, a.tcKA)) = h;
+              *reinterpret_cast<float *>(opPSl + tc::operand_offset(t, f, a.tcKA)) = tc::to_tf32(pf - h);
+            }
+            for (int e = threadIdx.x; e < a.tcMC * a.tcKC; e += blockDim.x) {
+              const int m = e / a.tcKC, q = e % a.tcKC;
+              if (m >= ni * rr || q >= Rl * rl) {
+                *reinterpret_cast<float *>(opT2h + tc::operand_offset(m, q, a.tcKC)) = 0.f;
+                *reinterpret_cast<float *>(opT2l + tc::operand_offset(m, q, a.tcKC)) = 0.f;
+              }
+            }
+            tc::fence_proxy_async();
+            tc::fence_before_sync();
+            __syncthreads();
+            tc::fence_after_sync();
+            const int nMT = a.tcMA / 128;
+            if (threadIdx.x == 0) {
+              const uint32_t id = tc::idesc_tf32(128, a.tcNA);
+              const uint32_t sboA = tc::sbo_bytes(a.tcKA);
+              for (int mt = 0; mt < nMT; ++mt)
+                for (int st = 0; st < a.tcKA / 8; ++st) {
+                  const uint32_t ao = (uint32_t)mt * 16 * sboA + 256u * st, bo = 256u * st;
+                  const uint64_t ah = tc::smem_desc(tc::smem_u32addr(opPSh) + ao, tc::kLBO, sboA);
+                  const uint64_t al = tc::smem_desc(tc::smem_u32addr(opPSl) + ao, tc::kLBO, sboA);
+                  const uint64_t bh = tc::smem_desc(tc::smem_u32addr(opPRh) + bo, tc::kLBO, sboA);
+                  const uint64_t bl = tc::smem_desc(tc::smem_u32addr(opPRl) + bo, tc::kLBO, sboA);
+                  const uint32_t d = tc_tmem + (uint32_t)(mt * a.tcNA);
+                  tc::mma_tf32(d, ah, bh, id, st > 0);
+                  tc::mma_tf32(d, ah, bl, id, true);
+                  tc::mma_tf32(d, al, bh, id, true);
+                }
+              tc::mma_commit(&tc_bar);
+            }
+            if (!tc::mbar_wait_parity(&tc_bar, tc_phase, kSpinLimit) && (threadIdx.x & 31) == 0) atomicExch(a.err, 3);
+            tc_phase ^= 1u;
+            tc::fence_after_sync();
+            {
+              const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, wq = warp & 3;
+              const int ncd = rr * Rr;
+              for (int mt = warp >> 2; mt < nMT; mt += (int)(blockDim.x >> 7)) {
+                const int r = mt * 128 + 32 * wq + lane;
+                for (int c0 = 0; c0 < a.tcNA; c0 += 16) {
+                  float v[16];
+                  tc::tmem_ld16(tc_tmem + ((uint32_t)(32 * wq) << 16) + (uint32_t)(mt * a.tcNA + c0), v);
+                  if (r < rl * nj) {
+#pragma unroll
+                    for (int k = 0; k < 16; ++k)
+                      if (c0 + k < ncd) T1s[(long long)r * ncd + c0 + k] = v[k];
+                  }
+                }
+              }
+            }
+            tc::fence_before_sync();
+            __syncthreads();
+          }
+        }
+        // The three stages are register-tiled: each thread computes TW = 4 neighbouring
+        // outputs, so one load of the shared operand feeds TW independent FMA chains.
+        // Indices past the last output are clamped for the loads and not stored.
+        constexpr int TW = 4;
+        // A1: T1s[aa][jj][c][d] = sum_f Ps[aa][jj][f] PhiR[c][d][f], TW consecutive d
+        const int nd4 = (Rr + TW - 1) / TW;
+        const int nA1 = use_tc ? 0 : rl * nj * rr * nd4;
+        for (int e = threadIdx.x; e < nA1; e += blockDim.x) {
+          const int d0 = (e % nd4) * TW;
+          const int t2 = e / nd4;
+          const int c = t2 % rr, t = t2 / rr;
+          const T *pr = Ps + (long long)t * rr;
+          const T *ph[TW];
+#pragma unroll
+          for (int k = 0; k < TW; ++k) ph[k] = PhiRs + (long long)(c * Rr + min(d0 + k, Rr - 1)) * phr_ld;
+          T sa[TW];
+#pragma unroll
+          for (int k = 0; k < TW; ++k) sa[k] = T(0);
+          for (int f = 0; f < rr; ++f) {
+            const T pv = pr[f];
+#pragma unroll
+            for (int k = 0; k < TW; ++k) sa[k] += pv * ph[k][f];
+          }
+          T *dst = T1s + ((long long)t * rr + c) * Rr + d0;
+#pragma unroll
+          for (int k = 0; k < TW; ++k)
+            if (d0 + k < Rr) dst[k] = sa[k];
         }
         __syncthreads();
-        // B: T2s[g][aa][ii][c] = sum_{o, d} A[g][i][o][d] T1s[aa][i+o-p-j0][c][d]
-        const int nB1 = Rl * rl * ni * rr;
+        // B: T2s[g][aa][ii][c] = sum_{o, d} A[g][i][o][d] T1s[aa][i+o-p-j0][c][d], TW consecutive c
+        const int nc4 = (rr + TW - 1) / TW;
+        const int nB1 = Rl * rl * ni * nc4;
         for (int e = threadIdx.x; e < nB1; e += blockDim.x) {
-          const int c = e % rr;
-          int t = e / rr;
+          const int c0 = (e % nc4) * TW;
+          int t = e / nc4;
           const int ii = t % ni;
           t /= ni;
           const int aa = t % rl, g = t / rl;
           const int i = i0 + ii;
           const T *Ar = a.A + ((long long)g * n + i) * b * Rr;
-          T s0 = T(0), s1 = T(0);
+          int cofs[TW];
+#pragma unroll
+          for (int k = 0; k < TW; ++k) cofs[k] = min(c0 + k, rr - 1) * Rr;
+          T sb[TW];
+#pragma unroll
+          for (int k = 0; k < TW; ++k) sb[k] = T(0);
 #pragma unroll
           for (int o = 0; o < b; ++o) {
             const int j = i + o - PB;
             if (j < 0 || j >= n) continue;
             const T *Ao = Ar + o * Rr;
-            const T *Tj = T1s + (((long long)aa * nj + (j - j0)) * rr + c) * Rr;
-            if (o & 1)
-              for (int d = 0; d < Rr; ++d) s1 += Ao[d] * Tj[d];
-            else
-              for (int d = 0; d < Rr; ++d) s0 += Ao[d] * Tj[d];
+            const T *Tj = T1s + ((long long)aa * nj + (j - j0)) * rr * Rr;
+            for (int d = 0; d < Rr; ++d) {
+              const T av = Ao[d];
+#pragma unroll
+              for (int k = 0; k < TW; ++k) sb[k] += av * Tj[cofs[k] + d];
+            }
           }
-          T2s[e] = s0 + s1;
+          if constexpr (kTc) {
+            if (use_tc) {
+              // the T2 operand of stage C: row ii rr + c, column g rl + aa, TF32 high and low parts
+#pragma unroll
+              for (int k = 0; k < TW; ++k) {
+                if (c0 + k >= rr) continue;
+                const int m = ii * rr + c0 + k, q = g * rl + aa;
+                const float x = (float)sb[k], h = tc::to_tf32(x);
+                *reinterpret_cast<float *>(opT2h + tc::operand_offset(m, q, a.tcKC)) = h;
+                *reinterpret_cast<float *>(opT2l + tc::operand_offset(m, q, a.tcKC)) = tc::to_tf32(x - h);
+              }
+              continue;
+            }
+          }
+          T *dst = T2s + (((long long)g * rl + aa) * ni + ii) * rr + c0;
+#pragma unroll
+          for (int k = 0; k < TW; ++k)
+            if (c0 + k < rr) dst[k] = sb[k];
+        }
+        if constexpr (kTc) {
+          if (use_tc) tc::fence_proxy_async();
         }
         __syncthreads();
-        // C: q[al][i][c] = sum_{g, aa} PhiL[al][g][aa] T2s[g][aa][ii][c];  <p, q>
-        const int nC1 = rl * ni * rr;
+        // C: q[al][i][c] = sum_{g, aa} PhiL[al][g][aa] T2s[g][aa][ii][c], TW consecutive c;  <p, q>
+        if constexpr (kTc) {
+          if (use_tc) {
+            // C on the tensor cores: q^T[(ii, c)][al] = sum_q T2[(ii, c)][q] PhiL[al][q] (3xTF32)
+            tc::fence_after_sync();
+            const int nMT = a.tcMA / 128, nMC = a.tcMC / 128;
+            const uint32_t col0 = (uint32_t)(nMT * a.tcNA);
+            if (threadIdx.x == 0) {
+              const uint32_t id = tc::idesc_tf32(128, a.tcNC);
+              const uint32_t sboC = tc::sbo_bytes(a.tcKC);
+              for (int mc = 0; mc < nMC; ++mc)
+                for (int st = 0; st < a.tcKC / 8; ++st) {
+                  const uint32_t ao = (uint32_t)mc * 16 * sboC + 256u * st, bo = 256u * st;
+                  const uint64_t ah = tc::smem_desc(tc::smem_u32addr(opT2h) + ao, tc::kLBO, sboC);
+                  const uint64_t al = tc::smem_desc(tc::smem_u32addr(opT2l) + ao, tc::kLBO, sboC);
+                  const uint64_t bh = tc::smem_desc(tc::smem_u32addr(opPLh) + bo, tc::kLBO, sboC);
+                  const uint64_t bl = tc::smem_desc(tc::smem_u32addr(opPLl) + bo, tc::kLBO, sboC);
+                  const uint32_t d = tc_tmem + col0 + (uint32_t)(mc * a.tcNC);
+                  tc::mma_tf32(d, ah, bh, id, st > 0);
+                  tc::mma_tf32(d, ah, bl, id, true);
+                  tc::mma_tf32(d, al, bh, id, true);
+                }
+              tc::mma_commit(&tc_bar);
+            }
+            if (!tc::mbar_wait_parity(&tc_bar, tc_phase, kSpinLimit) && (threadIdx.x & 31) == 0) atomicExch(a.err, 3);
+            tc_phase ^= 1u;
+            tc::fence_after_sync();
+            const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, wq = warp & 3;
+            for (int mc = warp >> 2; mc < nMC; mc += (int)(blockDim.x >> 7)) {
+              const int m = mc * 128 + 32 * wq + lane;
+              for (int c0 = 0; c0 < a.tcNC; c0 += 16) {
+                float v[16];
+                tc::tmem_ld16(tc_tmem + ((uint32_t)(32 * wq) << 16) + col0 + (uint32_t)(mc * a.tcNC + c0), v);
+                if (m < ni * rr) {
+                  const int ii = m / rr, c = m % rr;
+#pragma unroll
+                  for (int k = 0; k < 16; ++k) {
+                    const int al = c0 + k;
+                    if (al >= rl) continue;
+                    const long long idx = ((long long)al * n + i0 + ii) * rr + c;
+                    a.q[idx] = (T)v[k];
+                    pq_loc += (double)Ps[((long long)al * nj + (i0 + ii - j0)) * rr + c] * (double)v[k];
+                  }
+                }
+              }
+            }
+            tc::fence_before_sync();
+            __syncthreads();
+            continue;
+          }
+        }
+        const int nC1 = rl * ni * nc4;
         const int ga = Rl * rl;
         for (int e = threadIdx.x; e < nC1; e += blockDim.x) {
-          const int c = e % rr;
-          const int t = e / rr;
+          const int c0 = (e % nc4) * TW;
+          const int t = e / nc4;
           const int ii = t % ni, al = t / ni;
-          const T *ph = a.PhiL + (long long)al * ga;
-          T s4[4] = {T(0), T(0), T(0), T(0)};
-          for (int q = 0; q < ga; ++q) s4[q & 3] += ph[q] * T2s[((long long)q * ni + ii) * rr + c];
-          const T sv = (s4[0] + s4[1]) + (s4[2] + s4[3]);
-          const long long idx = ((long long)al * n + i0 + ii) * rr + c;
-          a.q[idx] = sv;
-          pq_loc += (double)pcur[idx] * (double)sv;
+          const T *ph = PhiLs + (long long)al * ga;
+          int cidx[TW];
+#pragma unroll
+          for (int k = 0; k < TW; ++k) cidx[k] = min(c0 + k, rr - 1);
+          T sc[TW];
+#pragma unroll
+          for (int k = 0; k < TW; ++k) sc[k] = T(0);
+          for (int q = 0; q < ga; ++q) {
+            const T pv = ph[q];
+            const T *row = T2s + ((long long)q * ni + ii) * rr;
+#pragma unroll
+            for (int k = 0; k < TW; ++k) sc[k] += pv * row[cidx[k]];
+          }
+#pragma unroll
+          for (int k = 0; k < TW; ++k) {
+            if (c0 + k >= rr) continue;
+            const int c = c0 + k;
+            const long long idx = ((long long)al * n + i0 + ii) * rr + c;
+            a.q[idx] = sc[k];
+            pq_loc += (double)Ps[((long long)al * nj + (i0 + ii - j0)) * rr + c] * (double)sc[k];
+          }
         }
         __syncthreads();
       }
     }
     cta_partial(pq_loc, p_pq);
-    if (!grid_sync(a.bar, G, a.err)) return;
+    if (!grid_sync(a.bar, G, a.err)) {
+      aborted = true;
+      break;
+    }
     trace_mark(a.trace, a.trace_cap, slot);
     // E: x += alpha p, r -= alpha q, z = P^{-1} r per band system;  <r, r>, <r, z>
     const double pq = grid_total(p_pq);
@@ -757,18 +1005,31 @@ __global__ void __launch_bounds__(256, 1) k_pcg_fused(PcgArgs<T> a) {
     else band_systems<T, PB>(a, pcur, alpha, false, rr_loc, rz_loc);
     cta_partial(rr_loc, p_rr);
     cta_partial(rz_loc, p_rz);
-    if (!grid_sync(a.bar, G, a.err)) return;
+    if (!grid_sync(a.bar, G, a.err)) {
+      aborted = true;
+      break;
+    }
     trace_mark(a.trace, a.trace_cap, slot);
     res2 = grid_total(p_rr);
     rz_prev = rz;
     rz = grid_total(p_rz);
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) {
-    a.out[0] = (double)it;
-    a.out[1] = res2;
+    if (!aborted) {
+      a.out[0] = (double)it;
+      a.out[1] = res2;
+    }
     if (a.edge) {
       mbar_inval(&bb_bars[0]);
       mbar_inval(&bb_bars[1]);
+    }
+  }
+  if constexpr (kTc) {
+    if (a.tc) {
+      tc::fence_before_sync();
+      __syncthreads();
+      if (threadIdx.x < 32) tc::tmem_dealloc(tc_tmem, (uint32_t)a.tc_cols);
+      if (threadIdx.x == 0) tc::mbar_inval1(&tc_bar);
     }
   }
 }
@@ -838,8 +1099,98 @@ template <typename T> int pcg_fused_grid(Ctx *c, PcgArgs<T> &a) {
   } else {
     a.resident = 0;
   }
+  a.p_stride = (long long)a.rl * (S + 2 * a.p) * a.rr;
   a.t1_stride = (long long)a.rl * (S + 2 * a.p) * a.rr * a.Rr;
   a.t2_stride = (long long)a.Rl * a.rl * S * a.rr;
+  a.dense_stride = a.p_stride + a.t1_stride + a.t2_stride;
+  a.phr_ld = a.rr | 1;
+  // Shared memory after the preconditioner's area: the slab scratch of the dense phase
+  // (p, T1, T2), then the interfaces, each when it fits (the block-band staging gives
+  // up chunk rows for them, down to 8); otherwise the slab scratch is in global memory
+  // (one region per CTA) and the interfaces are read from global memory.  The grid
+  // must stay co-resident.
+  const size_t dense = (size_t)a.dense_stride * sizeof(T);
+  const size_t iface = ((size_t)a.rr * a.Rr * a.phr_ld + (size_t)a.rl * a.Rl * a.rl) * sizeof(T);
+  const size_t pre_smem = (size_t)a.smem;
+  const int pre_ch = a.bb_ch;
+  auto place = [&](bool want_iface, size_t reserve) {  // reserve: bytes kept free after the slab scratch
+    a.dense_off = -1;
+    a.iface_off = -1;
+    const size_t extra = dense + (want_iface ? iface : 0) + reserve;
+    if (a.edge) {
+      const size_t vec = 2 * (size_t)a.n * a.bbM * sizeof(float),
+                   row = (size_t)a.p * a.bbM * bb_stride(a.bbM) * sizeof(float);
+      const size_t base = (vec + 15) / 16 * 16;
+      if (base + extra + 16 + 2 * 8 * row > kPcgSmemBytes) return;
+      a.bb_ch = (int)std::min<size_t>(32, (kPcgSmemBytes - base - extra - 16) / (2 * row));
+      const size_t off = (vec + 2 * (size_t)a.bb_ch * row + 15) / 16 * 16;
+      a.dense_off = (int)off;
+      a.smem = (int)(off + dense);
+    } else {
+      const size_t off = (pre_smem + 15) / 16 * 16;
+      if (off + extra + 16 > kPcgSmemBytes) return;
+      a.dense_off = (int)off;
+      a.smem = (int)(off + dense);
+    }
+    if (want_iface) {
+      const size_t off = ((size_t)a.smem + 15) / 16 * 16;
+      a.iface_off = (int)off;
+      a.smem = (int)(off + iface);
+    }
+  };
+  // Tensor-core stages: padded shapes, TMEM columns and the operand area after the
+  // slab scratch (the shared interface copies are not needed then).  Cleared when the
+  // operands do not fit, when TMEM would need more than 256 columns per CTA, or when the
+  // slab scratch itself is not in shared memory.
+  size_t tc_bytes = 0;
+  if (a.tc) {
+    auto up = [](long long v, long long m) { return (int)((v + m - 1) / m * m); };
+    a.tcMA = up((long long)a.rl * (S + 2 * a.p), 128);
+    a.tcNA = up((long long)a.rr * a.Rr, 16);
+    a.tcKA = up(a.rr, 8);
+    a.tcMC = up((long long)S * a.rr, 128);
+    a.tcNC = up(a.rl, 16);
+    a.tcKC = up((long long)a.Rl * a.rl, 8);
+    const long long cols = (long long)(a.tcMA / 128) * a.tcNA + (long long)(a.tcMC / 128) * a.tcNC;
+    int tcols = 32;
+    while (tcols < cols) tcols *= 2;
+    a.tc_cols = tcols;
+    tc_bytes = 2 * (size_t)(tc::operand_bytes(a.tcNA, a.tcKA) + tc::operand_bytes(a.tcNC, a.tcKC) +
+                            tc::operand_bytes(a.tcMA, a.tcKA) + tc::operand_bytes(a.tcMC, a.tcKC));
+    if (a.tcNA > 256 || a.tcNC > 256 || cols > 256) a.tc = 0;
+  }
+  if (a.tc) {
+    place(false, tc_bytes + 128);
+    if (a.dense_off >= 0) {
+      const size_t off = ((size_t)a.smem + 127) / 128 * 128;
+      if (off + tc_bytes <= kPcgSmemBytes) {
+        a.tc_off = (int)off;
+        a.smem = (int)(off + tc_bytes);
+      } else {
+        a.tc = 0;
+      }
+    } else {
+      a.tc = 0;
+    }
+  }
+  if (!a.tc) {
+    place(true, 0);
+    if (a.dense_off < 0) place(false, 0);
+  }
+  if (a.dense_off >= 0) {
+    int per_sm2 = 0;
+    TTI_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm2, k, 256, a.smem));
+    if ((long long)per_sm2 * c->num_sms < g) {
+      a.dense_off = -1;
+      a.tc = 0;
+    }
+  }
+  if (a.dense_off < 0) {
+    // the sizes chosen above, slab scratch in global memory, interfaces from global memory
+    a.iface_off = -1;
+    a.smem = (int)pre_smem;
+    a.bb_ch = pre_ch;
+  }
   return (int)g;
 }
 

@@ -16,8 +16,9 @@ template <typename T> struct PcgArgs {
   int bb_ch;      // block rows per staged chunk of G / H (set by pcg_fused_grid)
   const T *b;     // right-hand side [rl][n][rr]
   T *x, *r, *z, *pv, *pv2, *q;  // solution and work vectors [rl][n][rr] (pv, pv2: p double buffer)
-  T *T1;          // per-CTA slab scratch, grid x t1_stride: [rl][S+2p][rr][Rr]
-  T *T2;          // per-CTA slab scratch, grid x t2_stride: [Rl][rl][S][rr]
+  // per-CTA slab scratch of the dense phase, grid x dense_stride, used when dense_off < 0:
+  // p [rl][S+2p][rr], T1 [rl][S+2p][rr][Rr], T2 [Rl][rl][S][rr] back to back
+  T *scratch;
   double *part;   // 3 * grid partial sums
   struct Barrier *bar;
   int *err;       // set to 1 when a grid barrier wait runs out
@@ -30,8 +31,20 @@ template <typename T> struct PcgArgs {
   int slots;      // band systems staged per CTA at a time (set by pcg_fused_grid)
   int resident;   // 1: every band system has its own slot, factors gathered once (set by pcg_fused_grid)
   int slab;       // mode rows per slab of the dense phase (set by pcg_fused_grid)
-  long long t1_stride, t2_stride;  // per-CTA scratch sizes in elements (set by pcg_fused_grid)
+  long long p_stride, t1_stride, t2_stride, dense_stride;  // slab scratch sizes in elements (set by pcg_fused_grid)
+  int dense_off;  // byte offset of the slab scratch in dynamic shared memory, -1: in `scratch` (pcg_fused_grid)
+  int iface_off;  // byte offset of PhiR, PhiL copies in dynamic shared memory, -1: read from global
+  int phr_ld;     // row stride of the shared copy of PhiR (rr rounded up to odd)
   int smem;       // dynamic shared memory bytes (set by pcg_fused_grid)
+  // Tensor-core stages (FP32 PCG only): set tc = 1 to ask for them; pcg_fused_grid
+  // keeps it when the operands fit in shared memory and TMEM, else clears it.  The
+  // right- and left-interface contractions then run as tcgen05 kind::tf32 MMAs with
+  // the 3xTF32 split.  Padded shapes: stage A M = tcMA (Ps rows), N = tcNA (rr Rr),
+  // K = tcKA (rr); stage C M = tcMC (S rr), N = tcNC (rl), K = tcKC (Rl rl).
+  int tc;
+  int tc_off;     // byte offset of the operands in dynamic shared memory
+  int tc_cols;    // TMEM columns allocated per CTA
+  int tcMA, tcNA, tcKA, tcMC, tcNC, tcKC;
 };
 
 // Number of CTAs for the cooperative launch (all co-resident).

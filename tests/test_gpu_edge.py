@@ -67,7 +67,7 @@ def test_argument_errors(tt, ctx):
     s = tt.tt_iga_assemble(ctx, g, [tt.rhs_desc()], round_tol=1e-12)
     try:
         with pytest.raises(tt.TTIgaError) as e:
-            tt.tt_iga_solve(ctx, s, tt.solve_opts(precision=tt.MIXED_TF32))
+            tt.tt_iga_solve(ctx, s, tt.solve_opts(precision=7))  # not a precision mode
         assert e.value.code == tt.ERR_ARG
         with pytest.raises(tt.TTIgaError) as e:
             tt.tt_iga_solve(ctx, s, tt.solve_opts(rhs_index=3))

@@ -65,7 +65,7 @@ def test_fp64_solution_matches_oracle(tt, ctx, geo, n, p, modes):
     assert np.linalg.norm(uh - ref) <= 1e-9 * np.linalg.norm(ref), st
 
 
-@pytest.mark.parametrize("precision", ["MIXED_FP32"])
+@pytest.mark.parametrize("precision", ["MIXED_FP32", "MIXED_TF32"])
 def test_mixed_precision_matches_oracle(tt, ctx, precision):
     from oracle.iga import to_flat
     geo, n, p = synthetic.TWISTED_ANNULUS, 12, 3
@@ -81,6 +81,10 @@ def test_mixed_precision_matches_oracle(tt, ctx, precision):
     ref = to_flat(uo[1:-1, 1:-1, 1:-1])
     assert st["rel_residual"] <= 1e-10
     assert st["local_matvecs"] > st["local_matvecs_fp64"]
+    if precision == "MIXED_TF32":
+        assert st["local_matvecs_tensor"] > 0  # the tensor-core stages ran
+    else:
+        assert st["local_matvecs_tensor"] == 0
     assert np.linalg.norm(uh - ref) <= 1e-7 * np.linalg.norm(ref)
 
 
