@@ -89,6 +89,13 @@ const char *tt_iga_last_error(const tt_iga_ctx *ctx);
 int tt_iga_ctx_memory(const tt_iga_ctx *ctx, size_t *bytes_in_use, size_t *bytes_peak);
 /* Number of CUDA kernels the library has launched in this process (all contexts). */
 unsigned long long tt_iga_launch_count(void);
+/* Limit the context's cooperative kernels (the fused local PCG, one grid-wide
+ * launch per AMEn local solve) to max_sms SMs' worth of CTAs (0: the whole
+ * GPU, the default).  Several contexts solving at once (batch lanes, serving
+ * lanes) can then run their local solves side by side instead of queueing for
+ * the whole GPU; other kernels are not limited.  A smaller grid changes the
+ * order of the PCG's partial sums, so results can differ in the last bits. */
+int tt_iga_ctx_set_sm_limit(tt_iga_ctx *ctx, int max_sms);
 
 /* Live timing of one kernel family on the context stream, for roofline
  * reporting: every launch of the family is bracketed by a CUDA event pair.
@@ -269,6 +276,9 @@ typedef struct {
   int local_maxit;  /* [500] local PCG iteration cap */
   int rhs_index;    /* which right-hand side of the system to solve [0] */
   int verbose;      /* print one line per sweep to stderr */
+  double local_rtol; /* inexact local solves: each AMEn local system is solved until its residual is
+                        below max(the bound that tol implies, local_rtol x its initial residual);
+                        negative: the bound alone (every local system to full accuracy) [-1] */
 } tt_iga_solve_opts;
 
 typedef struct {
@@ -408,6 +418,12 @@ typedef struct {
   double round_tol;
   tt_iga_solve_opts opts;
   int rhs_solve;
+  /* Optional (NULL: none): host buffer of cores_cap doubles that receives the
+   * solution of every right-hand side k = 0 .. n_rhs-1 as TT cores in the layout
+   * of tt_iga_solution_cores, back to back; the result's rhs_ranks give their
+   * ranks.  TT_IGA_ERR_TOO_LARGE when they do not fit. */
+  double *cores_out;
+  size_t cores_cap;
 } tt_iga_batch_item;
 
 typedef struct {
@@ -419,19 +435,29 @@ typedef struct {
   long long dofs;            /* n1 n2 n3 times the number of right-hand sides */
   double ms_geometry, ms_assemble, ms_solve;  /* host wall clock per phase */
   double t_start_ms, t_end_ms;                /* start / end relative to the batch start */
+  int rhs_ranks[8][2];                        /* solution ranks per right-hand side (with cores_out) */
 } tt_iga_batch_result;
 
 /* Solve `count` independent instances on `device` with `lanes` concurrent
  * contexts (each its own stream and host thread, 1..64) fed from a work queue,
- * largest instance first.  results[count] (host) receives one record per
- * instance in input order; *wall_ms (may be NULL) the batch wall time.
- * Returns TT_IGA_OK or the first failing instance's status. */
-int tt_iga_batch_solve(int device, int count, const tt_iga_batch_item *items, int lanes,
+ * largest instance first.  sm_per_lane: the SM budget of each lane's
+ * cooperative kernels (tt_iga_ctx_set_sm_limit): -1 an equal share, the SM
+ * count divided by the number of lanes, so that the lanes' local PCG kernels
+ * run side by side; 0 the whole GPU for every lane (independent solves that
+ * queue for the SMs); > 0 that many SMs.  results[count] (host) receives one
+ * record per instance in input order; *wall_ms (may be NULL) the batch wall
+ * time.  Returns TT_IGA_OK or the first failing instance's status.  Results do
+ * not depend on the lane count or the SM budget beyond the grid sizes of the
+ * local PCG, whose reductions are summed in a fixed order per grid. */
+int tt_iga_batch_solve(int device, int count, const tt_iga_batch_item *items, int lanes, int sm_per_lane,
                        tt_iga_batch_result *results, double *wall_ms);
-/* Autotuner: run the batch once per candidate lane count and report the
- * fastest (*best_lanes, *best_ms); results hold the last run. */
-int tt_iga_batch_autotune(int device, int count, const tt_iga_batch_item *items, const int *candidates,
-                          int n_candidates, tt_iga_batch_result *results, int *best_lanes, double *best_ms);
+/* Autotuner: run the batch once for every pair of lane count (lane_candidates)
+ * and SM budget per lane (share_candidates, as sm_per_lane above; none given:
+ * -1) and report the fastest pair (*best_lanes, *best_sm_per_lane, may be
+ * NULL) and its wall time (*best_ms, may be NULL); results hold the last run. */
+int tt_iga_batch_autotune(int device, int count, const tt_iga_batch_item *items, const int *lane_candidates,
+                          int n_lane_candidates, const int *share_candidates, int n_share_candidates,
+                          tt_iga_batch_result *results, int *best_lanes, int *best_sm_per_lane, double *best_ms);
 
 /* ----------------------------------------------------- dense test hooks */
 

@@ -66,22 +66,25 @@ class RhsDesc(ctypes.Structure):
 class SolveOpts(ctypes.Structure):
     _fields_ = [("tol", ctypes.c_double), ("precision", ctypes.c_int), ("max_sweeps", ctypes.c_int),
                 ("kickrank", ctypes.c_int), ("max_rank", ctypes.c_int), ("local_maxit", ctypes.c_int),
-                ("rhs_index", ctypes.c_int), ("verbose", ctypes.c_int)]
+                ("rhs_index", ctypes.c_int), ("verbose", ctypes.c_int), ("local_rtol", ctypes.c_double)]
 
 
 class BatchItem(ctypes.Structure):
     _fields_ = [("geom", GeomDesc), ("n_rhs", ctypes.c_int), ("rhs", ctypes.POINTER(RhsDesc)),
-                ("round_tol", ctypes.c_double), ("opts", SolveOpts), ("rhs_solve", ctypes.c_int)]
+                ("round_tol", ctypes.c_double), ("opts", SolveOpts), ("rhs_solve", ctypes.c_int),
+                ("cores_out", _c_double_p), ("cores_cap", ctypes.c_size_t)]
 
 
 class BatchResult(ctypes.Structure):
     _fields_ = [("status", ctypes.c_int), ("ranks", ctypes.c_int * 2), ("sweeps", ctypes.c_int),
                 ("rel_residual_max", ctypes.c_double), ("dofs", ctypes.c_longlong), ("ms_geometry", ctypes.c_double),
                 ("ms_assemble", ctypes.c_double), ("ms_solve", ctypes.c_double), ("t_start_ms", ctypes.c_double),
-                ("t_end_ms", ctypes.c_double)]
+                ("t_end_ms", ctypes.c_double), ("rhs_ranks", (ctypes.c_int * 2) * 8)]
 
     def as_dict(self):
-        return {k: (list(getattr(self, k)) if k == "ranks" else getattr(self, k)) for k, _ in self._fields_}
+        d = {k: (list(getattr(self, k)) if k == "ranks" else getattr(self, k)) for k, _ in self._fields_}
+        d["rhs_ranks"] = [[self.rhs_ranks[k][0], self.rhs_ranks[k][1]] for k in range(8)]
+        return d
 
 
 class Stats(ctypes.Structure):
@@ -143,9 +146,11 @@ _SIGS = {
     "tt_iga_operator_entries": (ctypes.c_int, [_vp, _vp, ctypes.c_int, _c_int_p, _c_int_p, _c_double_p]),
     "tt_iga_vector_entries": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int, ctypes.c_int, _c_int_p, _c_double_p]),
     "tt_iga_batch_solve": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.POINTER(BatchItem), ctypes.c_int,
-                                          ctypes.POINTER(BatchResult), _c_double_p]),
+                                          ctypes.c_int, ctypes.POINTER(BatchResult), _c_double_p]),
     "tt_iga_batch_autotune": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.POINTER(BatchItem), _c_int_p,
-                                             ctypes.c_int, ctypes.POINTER(BatchResult), _c_int_p, _c_double_p]),
+                                             ctypes.c_int, _c_int_p, ctypes.c_int, ctypes.POINTER(BatchResult),
+                                             _c_int_p, _c_int_p, _c_double_p]),
+    "tt_iga_ctx_set_sm_limit": (ctypes.c_int, [_vp, ctypes.c_int]),
     "tt_iga_basis_tables": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, _vp, _vp, _vp, _vp]),
     "tt_iga_geom_points": (ctypes.c_int, [_vp, _vp, ctypes.POINTER(RhsDesc), ctypes.c_int, _vp, _vp,
                                           ctypes.POINTER(ctypes.c_longlong)]),
@@ -240,10 +245,11 @@ def rhs_desc(modes=(), constant=None, ring_log=False):
 
 
 def solve_opts(tol=1e-8, precision=FP64, max_sweeps=0, kickrank=0, max_rank=0, local_maxit=0, rhs_index=0,
-               verbose=False):
+               verbose=False, local_rtol=0.0):
     o = SolveOpts()
     o.tol, o.precision, o.max_sweeps, o.kickrank = tol, precision, max_sweeps, kickrank
     o.max_rank, o.local_maxit, o.rhs_index, o.verbose = max_rank, local_maxit, rhs_index, int(verbose)
+    o.local_rtol = float(local_rtol)
     return o
 
 
@@ -565,9 +571,10 @@ def tt_iga_vector_entries(ctx, s, u, k, idx):
 
 
 def batch_items(instances, tol=1e-8, precision=FP64, cross_tol=1e-10, round_tol=1e-12, max_rank=0,
-                rhs_solve=None):
+                rhs_solve=None, cores_cap=0):
     """BatchItem array from instance dicts (synthetic.random_instance); keeps the rhs arrays alive.
-    rhs_solve: RHS_BLOCK (default) or RHS_EACH."""
+    rhs_solve: RHS_BLOCK (default) or RHS_EACH.  cores_cap > 0: every item gets a host buffer of that
+    many doubles for its solutions' cores (keep[1][k] is item k's numpy buffer)."""
     arr = (BatchItem * len(instances))()
     keep = []
     for k, inst in enumerate(instances):
@@ -580,27 +587,60 @@ def batch_items(instances, tol=1e-8, precision=FP64, cross_tol=1e-10, round_tol=
         arr[k].round_tol = round_tol
         arr[k].opts = solve_opts(tol=tol, precision=precision)
         arr[k].rhs_solve = RHS_BLOCK if rhs_solve is None else int(rhs_solve)
-    return arr, keep
+    bufs = []
+    if cores_cap > 0:
+        import numpy as np
+        for k in range(len(instances)):
+            b = np.zeros(int(cores_cap))
+            bufs.append(b)
+            arr[k].cores_out = b.ctypes.data_as(_c_double_p)
+            arr[k].cores_cap = int(cores_cap)
+    return arr, (keep, bufs)
 
 
-def tt_iga_batch_solve(items, lanes, device=0):
-    """Returns (status, per-instance result dicts, wall ms)."""
+def batch_cores(item_buf, result, n):
+    """Split an item's cores buffer into [rhs][3 cores] with the result's ranks (unknowns n - 2)."""
+    m = n - 2
+    out, off = [], 0
+    for k in range(8):
+        r1, r2 = result["rhs_ranks"][k]
+        if r1 == 0:
+            break
+        sizes = [(1, m, r1), (r1, m, r2), (r2, m, 1)]
+        cores = []
+        for sh in sizes:
+            cnt = sh[0] * sh[1] * sh[2]
+            cores.append(item_buf[off:off + cnt].reshape(sh))
+            off += cnt
+        out.append(cores)
+    return out
+
+
+def tt_iga_batch_solve(items, lanes, device=0, sm_per_lane=-1):
+    """Returns (status, per-instance result dicts, wall ms).  sm_per_lane: -1 an equal SM share per
+    lane, 0 the whole GPU for every lane, > 0 that many SMs."""
     n = len(items)
     res = (BatchResult * max(1, n))()
     ms = ctypes.c_double()
-    code = _lib.tt_iga_batch_solve(device, n, items, lanes, res, ctypes.byref(ms))
+    code = _lib.tt_iga_batch_solve(device, n, items, lanes, sm_per_lane, res, ctypes.byref(ms))
     return code, [res[i].as_dict() for i in range(n)], ms.value
 
 
-def tt_iga_batch_autotune(items, candidates, device=0):
+def tt_iga_batch_autotune(items, candidates, device=0, shares=(-1,)):
+    """Fastest (lanes, sm_per_lane) pair over candidates x shares; returns (lanes, sm_per_lane, ms, results)."""
     n = len(items)
     res = (BatchResult * max(1, n))()
     cand = (ctypes.c_int * len(candidates))(*candidates)
-    best, ms = ctypes.c_int(), ctypes.c_double()
-    code = _lib.tt_iga_batch_autotune(device, n, items, cand, len(candidates), res, ctypes.byref(best),
-                                      ctypes.byref(ms))
+    sh = (ctypes.c_int * len(shares))(*shares)
+    best, best_share, ms = ctypes.c_int(), ctypes.c_int(), ctypes.c_double()
+    code = _lib.tt_iga_batch_autotune(device, n, items, cand, len(candidates), sh, len(shares), res,
+                                      ctypes.byref(best), ctypes.byref(best_share), ctypes.byref(ms))
     _check(None, code, (ERR_NOT_CONVERGED,))
-    return best.value, ms.value, [res[i].as_dict() for i in range(n)]
+    return best.value, best_share.value, ms.value, [res[i].as_dict() for i in range(n)]
+
+
+def tt_iga_ctx_set_sm_limit(ctx, max_sms):
+    _check(ctx, _lib.tt_iga_ctx_set_sm_limit(ctx, int(max_sms)))
 
 
 def tt_iga_basis_tables(ctx, n, p, nq, pts, wts, N, dN):

@@ -440,6 +440,11 @@ struct Amen {
       return res0;
     }
     if (res0 <= tol_abs) return res0;
+    // inexact local solve (local_rtol > 0): a local system is solved only to local_rtol times its
+    // initial residual when that is above the absolute bound.  Far from convergence (early sweeps,
+    // poor interfaces) this saves most of the PCG iterations; the exact global residual decides
+    // convergence, so the late sweeps, whose initial residuals are small, solve to full accuracy.
+    if (o.local_rtol > 0.0) tol_abs = std::max(tol_abs, o.local_rtol * res0);
     const int maxit = o.local_maxit;
     const BBPrec *bbp = edge ? &bb : nullptr;
     if (o.precision == TT_IGA_FP64) {
@@ -667,6 +672,9 @@ struct Amen {
           r0 = local_solve(k, rhs.d(), x.d(), tol_solve);
         }
         maxloc = std::max(maxloc, r0 / Fnorm);
+        if (o.verbose)
+          fprintf(stderr, "[tt_iga amen] sweep %d core %d: initial local residual %.3e of ||F||, ranks %d %d, "
+                          "local matvecs so far %lld\n", sweep + 1, k, r0 / Fnorm, rl(k), rr(k), st.local_matvecs);
         const double t1 = now_ms();
         t_solve += t1 - t0;
         if (k < 2) {

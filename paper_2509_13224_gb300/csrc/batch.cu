@@ -17,9 +17,16 @@
 
 extern "C" {
 
-int tt_iga_batch_solve(int device, int count, const tt_iga_batch_item *items, int lanes, tt_iga_batch_result *results,
-                       double *wall_ms) {
-  if (count < 0 || (count > 0 && (!items || !results)) || lanes < 1 || lanes > 64) return TT_IGA_ERR_ARG;
+int tt_iga_batch_solve(int device, int count, const tt_iga_batch_item *items, int lanes, int sm_per_lane,
+                       tt_iga_batch_result *results, double *wall_ms) {
+  if (count < 0 || (count > 0 && (!items || !results)) || lanes < 1 || lanes > 64 || sm_per_lane < -1)
+    return TT_IGA_ERR_ARG;
+  int sms = 0;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) return TT_IGA_ERR_CUDA;
+  // -1: an equal share of the SMs per lane, so the lanes' cooperative PCG kernels fit side by side.
+  // The share follows from `lanes` alone (not from how many instances there are), so an instance
+  // gets the same grids, and the same bits, alone and in a batch run with the same lanes.
+  const int share = sm_per_lane == -1 ? (lanes > 1 ? std::max(1, sms / lanes) : 0) : sm_per_lane;
   for (int i = 0; i < count; ++i)
     if (items[i].n_rhs < 1 || items[i].n_rhs > 8 || !items[i].rhs ||
         (items[i].rhs_solve != TT_IGA_RHS_BLOCK && items[i].rhs_solve != TT_IGA_RHS_EACH))
@@ -43,8 +50,10 @@ int tt_iga_batch_solve(int device, int count, const tt_iga_batch_item *items, in
     o.device = device;
     tt_iga_ctx *ctx = nullptr;
     int rc = tt_iga_ctx_create(&ctx, &o);
+    if (rc == TT_IGA_OK) rc = tt_iga_ctx_set_sm_limit(ctx, share);
     if (rc != TT_IGA_OK) {
       first_error.store(rc);
+      if (ctx) tt_iga_ctx_destroy(ctx);
       return;
     }
     for (;;) {
@@ -63,6 +72,23 @@ int tt_iga_batch_solve(int device, int count, const tt_iga_batch_item *items, in
       if (st == TT_IGA_OK) st = tt_iga_assemble(ctx, g, it.rhs, it.n_rhs, it.round_tol, &s);
       auto tc = std::chrono::steady_clock::now();
       double worst = 0.0;
+      size_t cores_off = 0;
+      // the solution cores of right-hand side k, back to back, when the item asks for them
+      auto keep_cores = [&](int k, const tt_iga_solution *u) {
+        if (!it.cores_out || !u) return;
+        int modes[3], ranks[4];
+        if (tt_iga_solution_cores(ctx, u, nullptr, 0, modes, ranks) != TT_IGA_OK) return;
+        const size_t need = (size_t)ranks[1] * modes[0] + (size_t)ranks[1] * modes[1] * ranks[2] +
+                            (size_t)ranks[2] * modes[2];
+        if (cores_off + need > it.cores_cap) {
+          if (st == TT_IGA_OK) st = TT_IGA_ERR_TOO_LARGE;
+          return;
+        }
+        tt_iga_solution_cores(ctx, u, it.cores_out + cores_off, it.cores_cap - cores_off, modes, ranks);
+        res.rhs_ranks[k][0] = ranks[1];
+        res.rhs_ranks[k][1] = ranks[2];
+        cores_off += need;
+      };
       if (st == TT_IGA_OK && it.n_rhs > 1 && it.rhs_solve == TT_IGA_RHS_BLOCK) {
         tt_iga_solution *us[8] = {};
         double rr[8];
@@ -70,6 +96,7 @@ int tt_iga_batch_solve(int device, int count, const tt_iga_batch_item *items, in
         st = tt_iga_solve_block(ctx, s, &it.opts, -1, us, &stats, rr);
         for (int k = 0; k < it.n_rhs; ++k) {
           worst = (worst < 0.0 || rr[k] < 0.0) ? -1.0 : std::max(worst, rr[k]);
+          keep_cores(k, us[k]);
           tt_iga_solution_destroy(us[k]);
         }
         res.ranks[0] = stats.ranks[0];
@@ -82,10 +109,11 @@ int tt_iga_batch_solve(int device, int count, const tt_iga_batch_item *items, in
         tt_iga_solution *u = nullptr;
         tt_iga_stats stats{};
         st = tt_iga_solve(ctx, s, &so, &u, &stats);
-        worst = std::max(worst, stats.rel_residual);
+        worst = (worst < 0.0 || stats.rel_residual < 0.0) ? -1.0 : std::max(worst, stats.rel_residual);
         res.ranks[0] = stats.ranks[0];
         res.ranks[1] = stats.ranks[1];
         res.sweeps += stats.sweeps;
+        keep_cores(k, u);
         tt_iga_solution_destroy(u);
       }
       auto td = std::chrono::steady_clock::now();
@@ -112,21 +140,29 @@ int tt_iga_batch_solve(int device, int count, const tt_iga_batch_item *items, in
   return TT_IGA_OK;
 }
 
-int tt_iga_batch_autotune(int device, int count, const tt_iga_batch_item *items, const int *candidates,
-                          int n_candidates, tt_iga_batch_result *results, int *best_lanes, double *best_ms) {
-  if (!candidates || n_candidates < 1 || !best_lanes) return TT_IGA_ERR_ARG;
+int tt_iga_batch_autotune(int device, int count, const tt_iga_batch_item *items, const int *lane_candidates,
+                          int n_lane_candidates, const int *share_candidates, int n_share_candidates,
+                          tt_iga_batch_result *results, int *best_lanes, int *best_sm_per_lane, double *best_ms) {
+  if (!lane_candidates || n_lane_candidates < 1 || !best_lanes || (n_share_candidates > 0 && !share_candidates))
+    return TT_IGA_ERR_ARG;
+  const int default_share = -1;
+  const int *shares = n_share_candidates > 0 ? share_candidates : &default_share;
+  const int ns = n_share_candidates > 0 ? n_share_candidates : 1;
   double best = 1e300;
-  int pick = candidates[0];
-  for (int c = 0; c < n_candidates; ++c) {
-    double ms = 0.0;
-    const int rc = tt_iga_batch_solve(device, count, items, candidates[c], results, &ms);
-    if (rc != TT_IGA_OK && rc != TT_IGA_ERR_NOT_CONVERGED) return rc;
-    if (ms < best) {
-      best = ms;
-      pick = candidates[c];
+  int pick = lane_candidates[0], pick_share = shares[0];
+  for (int c = 0; c < n_lane_candidates; ++c)
+    for (int q = 0; q < ns; ++q) {
+      double ms = 0.0;
+      const int rc = tt_iga_batch_solve(device, count, items, lane_candidates[c], shares[q], results, &ms);
+      if (rc != TT_IGA_OK && rc != TT_IGA_ERR_NOT_CONVERGED) return rc;
+      if (ms < best) {
+        best = ms;
+        pick = lane_candidates[c];
+        pick_share = shares[q];
+      }
     }
-  }
   *best_lanes = pick;
+  if (best_sm_per_lane) *best_sm_per_lane = pick_share;
   if (best_ms) *best_ms = best;
   return TT_IGA_OK;
 }

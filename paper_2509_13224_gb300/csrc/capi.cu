@@ -133,6 +133,13 @@ int tt_iga_ctx_memory(const tt_iga_ctx *c, size_t *in_use, size_t *peak) {
 
 unsigned long long tt_iga_launch_count(void) { return ttiga::g_launches.load(); }
 
+int tt_iga_ctx_set_sm_limit(tt_iga_ctx *c, int max_sms) {
+  if (!c || max_sms < 0) return TT_IGA_ERR_ARG;
+  c->coop_sms = max_sms;
+  for (auto &s : c->subs) s->coop_sms = max_sms;
+  return TT_IGA_OK;
+}
+
 int tt_iga_profile_enable(tt_iga_ctx *c, int family) {
   if (!c || family < 0 || family > 6) return TT_IGA_ERR_ARG;
   API_TRY
@@ -378,6 +385,9 @@ int tt_iga_system_info(const tt_iga_system *s, int op_ranks[2], int n_rhs_max, i
 // --------------------------------------------------------------------- solve
 
 // Solve options with the defaults of tt_iga_solve_opts filled in.
+// Default forcing term of the inexact local solves (tt_iga_solve_opts.local_rtol).
+constexpr double kDefaultLocalRtol = -1.0;
+
 static tt_iga_solve_opts solve_defaults(const tt_iga_solve_opts *opts) {
   tt_iga_solve_opts o{};
   if (opts) o = *opts;
@@ -388,6 +398,9 @@ static tt_iga_solve_opts solve_defaults(const tt_iga_solve_opts *opts) {
   if (o.max_rank <= 0) o.max_rank = 256;
   o.max_rank = std::min(o.max_rank, 240);
   if (o.local_maxit <= 0) o.local_maxit = 500;
+  if (o.local_rtol == 0.0) o.local_rtol = kDefaultLocalRtol;
+  TTI_CHECK_ARG(std::isfinite(o.local_rtol) && o.local_rtol < 1.0, "solve: local_rtol %g is not below 1",
+                o.local_rtol);
   TTI_CHECK_ARG(o.precision == TT_IGA_FP64 || o.precision == TT_IGA_MIXED_FP32 || o.precision == TT_IGA_MIXED_TF32,
                 "solve: precision %d is not one of FP64, MIXED_FP32, MIXED_TF32", o.precision);
   return o;

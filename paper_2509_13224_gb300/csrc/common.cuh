@@ -103,6 +103,9 @@ struct Ctx {
   std::string last_error;
   size_t in_use = 0, peak = 0;
   int num_sms = 0;
+  // SMs' worth of CTAs the context's cooperative kernels (the fused local PCG) may
+  // take (0: the whole GPU), so that concurrent contexts share the GPU.
+  int coop_sms = 0;
   // small pinned host scratch for scalar read-backs
   void *pinned = nullptr;
   size_t pinned_bytes = 0;

@@ -18,6 +18,7 @@ Ctx *Ctx::sub(int i) {
     auto s = std::make_unique<Ctx>();
     s->device = device;
     s->num_sms = num_sms;
+    s->coop_sms = coop_sms;
     s->is_sub = true;
     s->dstatus = dstatus;  // shared: kernels of every helper report into the parent's word
     TTI_CUDA(cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking));

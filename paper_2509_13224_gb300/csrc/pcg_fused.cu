@@ -252,22 +252,49 @@ __device__ __forceinline__ void band_systems(const PcgArgs<T> &a, const T *__res
         esm[s_ * per + rem] = a.Lf[((long long)i * (PB + 1) + k) * npair + t0 + s_];
       }
     }
+    // entries are taken BU per thread at a time, all loads first, so a thread waits for one
+    // memory latency per batch rather than per entry (the entries of a system are rr apart)
+    constexpr int BU = 4;
     double rr_th = 0.0;
-    for (int e = threadIdx.x; e < cnt * n; e += blockDim.x) {
-      const int s_ = e / n, i = e - s_ * n;
-      const long long t = t0 + s_;
-      const long long idx = ((t / rr) * n + i) * rr + (t % rr);
-      T r;
-      if (init) {
-        r = a.b[idx];
-        a.x[idx] = T(0);
-      } else {
-        a.x[idx] += (T)alpha * pcur[idx];
-        r = a.r[idx] - (T)alpha * a.q[idx];
+    for (int e0 = threadIdx.x; e0 < cnt * n; e0 += BU * blockDim.x) {
+      long long ix[BU];
+      int sl[BU];
+      T xv[BU], pv[BU], rv[BU], qv[BU];
+#pragma unroll
+      for (int u = 0; u < BU; ++u) {
+        const int e = e0 + u * blockDim.x;
+        ix[u] = -1;
+        xv[u] = pv[u] = rv[u] = qv[u] = T(0);
+        if (e < cnt * n) {
+          const int s_ = e / n, i = e - s_ * n;
+          const long long t = t0 + s_;
+          ix[u] = ((t / rr) * n + i) * rr + (t % rr);
+          sl[u] = s_ * per + n * (PB + 1) + i;
+          if (init) {
+            rv[u] = a.b[ix[u]];
+          } else {
+            xv[u] = a.x[ix[u]];
+            pv[u] = pcur[ix[u]];
+            rv[u] = a.r[ix[u]];
+            qv[u] = a.q[ix[u]];
+          }
+        }
       }
-      a.r[idx] = r;
-      rr_th += (double)r * (double)r;
-      esm[s_ * per + n * (PB + 1) + i] = (float)r;
+#pragma unroll
+      for (int u = 0; u < BU; ++u) {
+        if (ix[u] < 0) continue;
+        T r;
+        if (init) {
+          r = rv[u];
+          a.x[ix[u]] = T(0);
+        } else {
+          a.x[ix[u]] = xv[u] + (T)alpha * pv[u];
+          r = rv[u] - (T)alpha * qv[u];
+        }
+        a.r[ix[u]] = r;
+        rr_th += (double)r * (double)r;
+        esm[sl[u]] = (float)r;
+      }
     }
     rr_out += rr_th;
     __syncthreads();
@@ -280,13 +307,28 @@ __device__ __forceinline__ void band_systems(const PcgArgs<T> &a, const T *__res
     }
     __syncthreads();
     double rz_th = 0.0;
-    for (int e = threadIdx.x; e < cnt * n; e += blockDim.x) {
-      const int s_ = e / n, i = e - s_ * n;
-      const long long t = t0 + s_;
-      const long long idx = ((t / rr) * n + i) * rr + (t % rr);
-      const T zi = (T)esm[s_ * per + n * (PB + 1) + i];
-      a.z[idx] = zi;
-      rz_th += (double)a.r[idx] * (double)zi;
+    for (int e0 = threadIdx.x; e0 < cnt * n; e0 += BU * blockDim.x) {
+      long long ix[BU];
+      T rv[BU], zv[BU];
+#pragma unroll
+      for (int u = 0; u < BU; ++u) {
+        const int e = e0 + u * blockDim.x;
+        ix[u] = -1;
+        rv[u] = zv[u] = T(0);
+        if (e < cnt * n) {
+          const int s_ = e / n, i = e - s_ * n;
+          const long long t = t0 + s_;
+          ix[u] = ((t / rr) * n + i) * rr + (t % rr);
+          rv[u] = a.r[ix[u]];
+          zv[u] = (T)esm[s_ * per + n * (PB + 1) + i];
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < BU; ++u) {
+        if (ix[u] < 0) continue;
+        a.z[ix[u]] = zv[u];
+        rz_th += (double)rv[u] * (double)zv[u];
+      }
     }
     rz_out += rz_th;
     __syncthreads();
@@ -1080,7 +1122,8 @@ template <typename T> int pcg_fused_grid(Ctx *c, PcgArgs<T> &a) {
   int per_sm = 0;
   TTI_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, 256, a.smem));
   TTI_CHECK_ARG(per_sm >= 1, "pcg: kernel does not fit on an SM");
-  const long long cap = (long long)c->num_sms * std::max(1, std::min(per_sm, 2));
+  const int sms = (c->coop_sms > 0) ? std::min(c->coop_sms, c->num_sms) : c->num_sms;
+  const long long cap = (long long)sms * std::max(1, std::min(per_sm, 2));
   const long long row_out = (long long)a.Rl * a.rl * a.rr;
   long long S = std::max<long long>((256 + row_out - 1) / row_out, (a.n + cap - 1) / cap);
   S = std::max<long long>(1, std::min<long long>(S, a.n));

@@ -20,7 +20,8 @@ import time
 import numpy as np
 
 from . import (FP64, MIXED_FP32, MIXED_TF32, geom_desc, rhs_desc, solve_opts, tt_iga_assemble, tt_iga_ctx_create,
-               tt_iga_ctx_destroy, tt_iga_geom_destroy, tt_iga_geometry, tt_iga_import_cores, tt_iga_l2_diff,
+               tt_iga_ctx_destroy, tt_iga_ctx_set_sm_limit, tt_iga_geom_destroy, tt_iga_geometry, tt_iga_import_cores,
+               tt_iga_l2_diff,
                tt_iga_solution_cores, tt_iga_solution_destroy, tt_iga_solve, tt_iga_system_destroy)
 
 
@@ -58,11 +59,13 @@ class Server:
     """lanes: concurrent solves; budget_bytes: device memory allowed for admitted requests."""
 
     def __init__(self, device=0, lanes=4, budget_bytes=None, precision_policy="auto", keep_cores=False,
-                 cross_tol=1e-10, round_tol=1e-12, runner=None, mixed_precision=MIXED_FP32):
+                 cross_tol=1e-10, round_tol=1e-12, runner=None, mixed_precision=MIXED_FP32, sm_per_lane=-1):
         """runner: None (each request is solved by libtt_iga.so on the lane's context) or a
         callable runner(request, t0) -> record with the keys of _run_one, for driving the
         scheduler without a GPU.  mixed_precision: the precision mode of mixed requests
-        (MIXED_FP32 or MIXED_TF32)."""
+        (MIXED_FP32 or MIXED_TF32).  sm_per_lane: SM budget of each lane's local PCG kernels
+        (-1: the SM count divided by the lanes, so concurrent requests' solves run side by side;
+        0: the whole GPU)."""
         self.device = device
         self.lanes = int(lanes)
         self.runner = runner
@@ -76,6 +79,7 @@ class Server:
         self.mixed = mixed_precision
         self.keep_cores = keep_cores
         self.cross_tol, self.round_tol = cross_tol, round_tol
+        self.sm_per_lane = int(sm_per_lane)
         self._cv = threading.Condition()
 
     def _precision(self, req):
@@ -161,6 +165,11 @@ class Server:
                 import torch
                 torch.cuda.set_device(self.device)
                 ctx = tt_iga_ctx_create(None, self.device)
+                share = self.sm_per_lane
+                if share < 0:
+                    sms = torch.cuda.get_device_properties(self.device).multi_processor_count
+                    share = sms // self.lanes if self.lanes > 1 else 0
+                tt_iga_ctx_set_sm_limit(ctx, share)
             try:
                 while True:
                     req, need = admit()

@@ -24,23 +24,53 @@ def _instances(count, seed0, n_lo=16, n_hi=40):
 
 
 def test_batch_is_independent_of_concurrency(tt):
+    """With the same lanes (hence the same SM budget per lane) an instance gives the same bits alone
+    and in the batch; one lane (the whole GPU per solve) converges as well."""
     inst = _instances(6, 100)
     items, keep = tt.batch_items(inst, tol=1e-8)
     code1, res1, ms1 = tt.tt_iga_batch_solve(items, lanes=1)
     code4, res4, ms4 = tt.tt_iga_batch_solve(items, lanes=4)
     assert code1 == tt.OK and code4 == tt.OK
-    for a, b, i in zip(res1, res4, inst):
+    for k, (a, b, i) in enumerate(zip(res1, res4, inst)):
         assert a["status"] == 0 and b["status"] == 0
-        assert a["rel_residual_max"] <= 1e-8
-        assert a["ranks"] == b["ranks"] and a["sweeps"] == b["sweeps"]
-        assert a["rel_residual_max"] == b["rel_residual_max"]
+        assert a["rel_residual_max"] <= 1e-8 and b["rel_residual_max"] <= 1e-8
         assert a["dofs"] == i["n"] ** 3 * len(i["rhs"])
+        one, keep1 = tt.batch_items([i], tol=1e-8)
+        code, alone, _ = tt.tt_iga_batch_solve(one, lanes=4)
+        assert code == tt.OK
+        assert alone[0]["ranks"] == b["ranks"] and alone[0]["sweeps"] == b["sweeps"]
+        assert alone[0]["rel_residual_max"] == b["rel_residual_max"], k
+
+
+def test_batch_solutions_match_oracle(tt):
+    """A handful of batch instances (uneven geometry, degree, size and right-hand sides), every
+    right-hand side's solution against the oracle's full-grid FP64 solve."""
+    from oracle.iga import Space1D, solve
+    from oracle.manufactured import Manufactured
+    from oracle.tt import tt_full
+    from tests.gpu_util import oracle_geometry
+    inst = _instances(4, 300, n_lo=10, n_hi=16)
+    for i in inst:
+        i["rhs"] = i["rhs"][:2]
+    items, keep = tt.batch_items(inst, tol=1e-12, cross_tol=1e-13, round_tol=1e-13, cores_cap=1 << 18)
+    code, res, _ = tt.tt_iga_batch_solve(items, lanes=3)
+    assert code == tt.OK
+    for k, (i, r) in enumerate(zip(inst, res)):
+        sols = tt.batch_cores(keep[1][k], r, i["n"])
+        assert len(sols) == len(i["rhs"])
+        og = oracle_geometry(i["geometry"])
+        sp = [Space1D(i["n"], i["p"])] * 3
+        for cores, modes in zip(sols, i["rhs"]):
+            uo, _ = solve(sp, og, Manufactured(og, modes), tol=1e-14)
+            ref = uo[1:-1, 1:-1, 1:-1]
+            got = tt_full(cores)
+            assert np.linalg.norm(got - ref) <= 1e-8 * np.linalg.norm(ref), (k, i["n"], i["p"])
 
 
 def test_batch_autotune_picks_a_candidate(tt):
     items, keep = tt.batch_items(_instances(4, 200), tol=1e-6, precision=tt.MIXED_FP32)
-    best, ms, res = tt.tt_iga_batch_autotune(items, [1, 2, 4])
-    assert best in (1, 2, 4) and ms > 0
+    best, share, ms, res = tt.tt_iga_batch_autotune(items, [1, 2, 4], shares=[-1, 0])
+    assert best in (1, 2, 4) and share in (-1, 0) and ms > 0
     assert all(r["status"] == 0 for r in res)
 
 
