@@ -33,6 +33,10 @@ import time
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
+# Hardware work queues of the process (read when CUDA starts): the batched and serving measurements
+# run up to dozens of lanes, each on its own stream, and 8 queues (the default) would make
+# unrelated streams wait on each other.
+os.environ.setdefault("CUDA_DEVICE_MAX_CONNECTIONS", "32")
 
 import synthetic  # noqa: E402
 
@@ -519,7 +523,7 @@ def run_ours(args, rank, world):
     if args.batch_instances > 0:
         inst = [synthetic.random_instance(1 + k + 1000 * rank) for k in range(args.batch_instances)]
         items, keep = tt.batch_items(inst, tol=TOL, precision=mixed_prec)
-        lanes, share, ms_tune, _ = tt.tt_iga_batch_autotune(items, [4, 8, 16], shares=[-1, 0])
+        lanes, share, ms_tune, _ = tt.tt_iga_batch_autotune(items, [8, 16, 32, 48], shares=[-1, 0])
         out = {}
         # every instance's right-hand sides as one block-TT solve (the default), and, for
         # comparison, one AMEn solve per right-hand side and independent lanes
@@ -537,6 +541,7 @@ def run_ours(args, rank, world):
         batched = {"instances": args.batch_instances, "lanes": lanes, "sm_per_lane": share,
                    "rhs_total": sum(len(i["rhs"]) for i in inst),
                    "dofs_total": sum(i["n"] ** 3 * len(i["rhs"]) for i in inst),
+                   "cuda_device_max_connections": os.environ.get("CUDA_DEVICE_MAX_CONNECTIONS"),
                    "speedup_vs_independent_lanes": out["mixed_8_independent_lanes"]["wall_ms"] / out["mixed"]["wall_ms"],
                    **out}
 

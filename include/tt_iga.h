@@ -446,7 +446,13 @@ typedef struct {
  * run side by side; 0 the whole GPU for every lane (independent solves that
  * queue for the SMs); > 0 that many SMs.  results[count] (host) receives one
  * record per instance in input order; *wall_ms (may be NULL) the batch wall
- * time.  Returns TT_IGA_OK or the first failing instance's status.  Results do
+ * time.  With more than one lane, each lane runs the parts of a call
+ * sequentially on its own stream (a single context runs the coefficient fields
+ * and the operator and loads on helper streams and host threads instead): the
+ * lanes already overlap, and extra host threads would compete with them for
+ * the CPU.  Many lanes want as many hardware work queues
+ * (CUDA_DEVICE_MAX_CONNECTIONS, set before CUDA starts; the default is 8).
+ * Returns TT_IGA_OK or the first failing instance's status.  Results do
  * not depend on the lane count or the SM budget beyond the grid sizes of the
  * local PCG, whose reductions are summed in a fixed order per grid. */
 int tt_iga_batch_solve(int device, int count, const tt_iga_batch_item *items, int lanes, int sm_per_lane,

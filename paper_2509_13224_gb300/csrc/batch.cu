@@ -51,6 +51,8 @@ int tt_iga_batch_solve(int device, int count, const tt_iga_batch_item *items, in
     tt_iga_ctx *ctx = nullptr;
     int rc = tt_iga_ctx_create(&ctx, &o);
     if (rc == TT_IGA_OK) rc = tt_iga_ctx_set_sm_limit(ctx, share);
+    // the lanes overlap each other; helper threads inside a lane would only compete with them
+    if (rc == TT_IGA_OK && lanes > 1) ctx->use_helpers = false;
     if (rc != TT_IGA_OK) {
       first_error.store(rc);
       if (ctx) tt_iga_ctx_destroy(ctx);

@@ -106,6 +106,10 @@ struct Ctx {
   // SMs' worth of CTAs the context's cooperative kernels (the fused local PCG) may
   // take (0: the whole GPU), so that concurrent contexts share the GPU.
   int coop_sms = 0;
+  // Run the independent parts of a call (coefficient fields, operator and loads) on helper
+  // streams and host threads (run_concurrent).  Off for the lanes of a batch, whose contexts
+  // already overlap: there the extra host threads compete for the CPU with the lanes.
+  bool use_helpers = true;
   // small pinned host scratch for scalar read-backs
   void *pinned = nullptr;
   size_t pinned_bytes = 0;

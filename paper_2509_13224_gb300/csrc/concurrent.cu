@@ -19,6 +19,7 @@ Ctx *Ctx::sub(int i) {
     s->device = device;
     s->num_sms = num_sms;
     s->coop_sms = coop_sms;
+    s->use_helpers = use_helpers;
     s->is_sub = true;
     s->dstatus = dstatus;  // shared: kernels of every helper report into the parent's word
     TTI_CUDA(cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking));
@@ -41,7 +42,7 @@ void Ctx::release_subs() {
 }
 
 void run_concurrent(Ctx *c, int n, const std::function<void(int, Ctx *)> &f) {
-  if (n <= 1 || c->alloc_fn) {
+  if (n <= 1 || c->alloc_fn || !c->use_helpers) {
     for (int i = 0; i < n; ++i) f(i, c);
     return;
   }
