@@ -330,8 +330,9 @@ int tt_iga_solve_from(tt_iga_ctx *ctx, const tt_iga_system *s, const tt_iga_solv
  * then rounded to relative accuracy eps; 0: 1e-14).  scales (host, n_rhs
  * doubles, may be NULL) receives ||F_k||.  A solution of the block system
  * (tt_iga_solve with rhs_index 0) is sliced by tt_iga_solution_unstack: block
- * k times scale, the solution of right-hand side k of s (its TT ranks are the
- * block solution's).  tt_iga_eval and tt_iga_l2_error reject block solutions.
+ * k times scale, the solution of right-hand side k of s, rounded to 1e-14
+ * relative accuracy (so its TT ranks are its own numerical ranks, not the block
+ * solution's, which span every right-hand side).  tt_iga_eval and tt_iga_l2_error reject block solutions.
  * TT_IGA_ERR_ARG for a mode outside 0..2, a system that is already a block
  * system, a zero right-hand side, a block index outside 0..n_rhs-1 or a
  * non-finite scale.  The new handles belong to the caller (release with

@@ -128,6 +128,8 @@ void stack_system(Ctx *c, const tt_iga_system *s, int mode, double eps, tt_iga_s
   out->F_norm.push_back(nrm);
 }
 
+constexpr double kSliceRoundTol = 1e-14;
+
 void unstack_solution(Ctx *c, const tt_iga_solution *ub, int k, double scale, tt_iga_solution *out) {
   const int nb = ub->stacked, mode = ub->stack_mode;
   TTI_CHECK_ARG(nb > 1 || k == 0, "unstack: block %d of a plain solution", k);
@@ -151,6 +153,10 @@ void unstack_solution(Ctx *c, const tt_iga_solution *ub, int k, double scale, tt
                                                           u.r[d + 1], ub->u.m[d], d == mode ? k * m : 0, sd);
     TTI_LAUNCH();
   }
+  // The slice inherits the block solution's ranks, which span the subspaces of every right-hand
+  // side; rounding to 1e-14 relative accuracy keeps its own numerical rank only, so evaluation,
+  // L2 errors and residuals of the slice do not pay for the other right-hand sides.
+  if (u.r[1] > 1 || u.r[2] > 1) tt_round(c, u, kSliceRoundTol, 0);
 }
 
 }  // namespace ttiga

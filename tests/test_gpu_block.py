@@ -37,6 +37,15 @@ def _modes(k):
     return synthetic.random_modes(100 + k, count=2)
 
 
+def _oracle_solution(geo, n, p, modes):
+    """Restricted full-grid FP64 solution of the oracle (flat, i1 fastest)."""
+    from oracle.iga import Space1D, solve, to_flat
+    from oracle.manufactured import Manufactured
+    og = oracle_geometry(geo)
+    u, _ = solve([Space1D(n, p)] * 3, og, Manufactured(og, modes), tol=1e-14)
+    return to_flat(u[1:-1, 1:-1, 1:-1])
+
+
 def _system(tt, ctx, geo, p, n, rhs, bc=None):
     g = tt.tt_iga_geometry(ctx, tt.geom_desc(geo, p, n, cross_tol=1e-14, seed=7))
     if bc is None:
@@ -202,6 +211,8 @@ def test_eight_right_hand_sides_in_one_block_solve(tt, ctx):
     try:
         assert st["converged"] and len(sols) == nb
         ub = [_eval(tt, ctx, u, pts) for u in sols]
+        m = tt.tt_iga_system_info(s)["modes"]
+        dense = [tt.tt_iga_densify_solution(ctx, u, m) for u in sols]
         up = []
         for k in range(nb):
             u, _ = tt.tt_iga_solve(ctx, s, tt.solve_opts(tol=1e-11, rhs_index=k))
@@ -215,6 +226,10 @@ def test_eight_right_hand_sides_in_one_block_solve(tt, ctx):
     assert all(0 <= r <= 1e-11 for r in rr), rr
     for k in range(nb):
         assert np.max(np.abs(ub[k] - up[k])) < 1e-8 * np.max(np.abs(up[k]))
+    # and every slice against the oracle's full-grid solve of its own right-hand side
+    for k in range(nb):
+        ref = _oracle_solution(synthetic.TWISTED_ANNULUS, n, p, _modes(k))
+        assert np.linalg.norm(dense[k] - ref) <= 1e-9 * np.linalg.norm(ref), k
 
 
 def test_mixed_precision_block_solve(tt, ctx):
@@ -228,6 +243,8 @@ def test_mixed_precision_block_solve(tt, ctx):
     try:
         assert st["converged"] and st["local_matvecs"] > st["local_matvecs_fp64"]
         ub = [_eval(tt, ctx, u, pts) for u in sols]
+        m = tt.tt_iga_system_info(s)["modes"]
+        dense = [tt.tt_iga_densify_solution(ctx, u, m) for u in sols]
         up = []
         for k in range(nb):
             u, _ = tt.tt_iga_solve(ctx, s, tt.solve_opts(tol=1e-12, rhs_index=k))
@@ -241,3 +258,6 @@ def test_mixed_precision_block_solve(tt, ctx):
     assert all(0 <= r <= 1e-10 for r in rr), rr
     for k in range(nb):
         assert np.max(np.abs(ub[k] - up[k])) < 1e-6 * np.max(np.abs(up[k]))
+    for k in range(nb):
+        ref = _oracle_solution(synthetic.QUARTER_CYLINDER, n, p, _modes(k))
+        assert np.linalg.norm(dense[k] - ref) <= 1e-7 * np.linalg.norm(ref), k
