@@ -375,16 +375,29 @@ struct Amen {
     const bool edge = bb_eligible(rl(k) * rr(k), n(k), S->p);
     BBPrec bb;
     DBuf L;
+    // The lazy convergence check (check_below > 0) usually returns here: its residual is
+    // evaluated before any preconditioner is built, so a converged solve builds none.
+    double res0 = -1.0;
+    if (checked) {
+      res0 = residual64(k, rhs, x, rbuf.d());
+      if (res0 <= check_below) {
+        *checked = true;
+        return res0;
+      }
+    }
     // The preconditioner does not depend on the initial residual: it is built on a
     // helper stream while this stream evaluates that residual (whose norm the host
     // waits for); this stream joins the helper before anything uses or frees it.
+    // Not when the residual is known already (the check above).
     // Only while this is the one live context: several contexts (batch lanes, a
     // server's lanes) already overlap their work, and the extra stream and events
     // of every local solve then cost more than they hide.  Sequential too with a
     // caller-supplied allocator, whose streams helpers must not touch, and under
     // the verbose stage timers.
     Ctx *const parent = c;
-    Ctx *hb = (c->alloc_fn || o.verbose >= 2 || g_live_contexts.load(std::memory_order_relaxed) > 1) ? c : c->sub(0);
+    Ctx *hb = (res0 >= 0.0 || c->alloc_fn || o.verbose >= 2 || g_live_contexts.load(std::memory_order_relaxed) > 1)
+                  ? c
+                  : c->sub(0);
     if (hb != parent) {
       if (!ev_in) {
         TTI_CUDA(cudaEventCreateWithFlags(&ev_in, cudaEventDisableTiming));
@@ -427,18 +440,15 @@ struct Amen {
       bb.G.rehome(parent);
       bb.H.rehome(parent);
     }
-    double res0;
-    try {
-      res0 = residual64(k, rhs, x, rbuf.d());
-    } catch (...) {
-      if (hb != parent) cudaStreamWaitEvent(parent->stream, ev_out, 0);
-      throw;
+    if (res0 < 0.0) {
+      try {
+        res0 = residual64(k, rhs, x, rbuf.d());
+      } catch (...) {
+        if (hb != parent) cudaStreamWaitEvent(parent->stream, ev_out, 0);
+        throw;
+      }
     }
     if (hb != parent) TTI_CUDA(cudaStreamWaitEvent(parent->stream, ev_out, 0));
-    if (checked && res0 <= check_below) {
-      *checked = true;
-      return res0;
-    }
     if (res0 <= tol_abs) return res0;
     // inexact local solve (local_rtol > 0): a local system is solved only to local_rtol times its
     // initial residual when that is above the absolute bound.  Far from convergence (early sweeps,
