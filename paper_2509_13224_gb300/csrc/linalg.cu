@@ -382,8 +382,13 @@ __device__ __forceinline__ double cta_sum_tree(double v, double *red, double *ou
   return *out;
 }
 
+// Householder QR of each mb x k block.  With use_smem the block is read straight from
+// the source matrix (row-major, ld, `rows` rows; rows past the end read as zero) into a
+// shared-memory copy, so no separate layout pass is needed, and the reflectors are
+// written back to W at the end; otherwise W already holds the block (k_qr_load).
 __global__ void __launch_bounds__(256) k_qr_panel(double *__restrict__ W, int mb, int k, double *__restrict__ tau,
-                                                  double *__restrict__ Rout, int use_smem) {
+                                                  double *__restrict__ Rout, int use_smem,
+                                                  const double *__restrict__ src, long long ld, long long rows) {
   extern __shared__ double qsm[];
   __shared__ double red[32];
   __shared__ double sh[4];
@@ -391,7 +396,11 @@ __global__ void __launch_bounds__(256) k_qr_panel(double *__restrict__ W, int mb
   double *Wg = W + blk * (long long)mb * k;
   double *Wb = Wg;
   if (use_smem) {  // work on a shared-memory copy of the block, write the reflectors back at the end
-    for (int e = threadIdx.x; e < mb * k; e += blockDim.x) qsm[e] = Wg[e];
+    for (int e = threadIdx.x; e < mb * k; e += blockDim.x) {
+      const int i = e / k, cc = e % k;
+      const long long gr = blk * mb + i;
+      qsm[(long long)cc * mb + i] = (gr < rows) ? src[gr * ld + cc] : 0.0;
+    }
     Wb = qsm;
     __syncthreads();
   }
@@ -517,13 +526,16 @@ void qr(Ctx *c, int m, int k, const double *A, long long lda, double *Q, double 
     L.W = DBuf(c, (size_t)L.nblk * L.mb * k * sizeof(double));
     L.tau = DBuf(c, (size_t)L.nblk * k * sizeof(double));
     L.Rs = DBuf(c, (size_t)L.nblk * k * k * sizeof(double));
-    k_qr_load<<<L.nblk, 256, 0, c->stream>>>(src, ld, rows, k, L.mb, L.W.d());
-    TTI_LAUNCH();
+    const size_t sm = (size_t)L.mb * k * sizeof(double);
+    const int use = sm <= kQrSmemBytes;
+    if (!use) {
+      k_qr_load<<<L.nblk, 256, 0, c->stream>>>(src, ld, rows, k, L.mb, L.W.d());
+      TTI_LAUNCH();
+    }
     {
       ProfScope ps(c, PROF_QR, 2.0 * L.nblk * (double)L.mb * k * k);
-      const size_t sm = (size_t)L.mb * k * sizeof(double);
-      const int use = sm <= kQrSmemBytes;
-      k_qr_panel<<<L.nblk, 256, use ? sm : 0, c->stream>>>(L.W.d(), L.mb, k, L.tau.d(), L.Rs.d(), use);
+      k_qr_panel<<<L.nblk, 256, use ? sm : 0, c->stream>>>(L.W.d(), L.mb, k, L.tau.d(), L.Rs.d(), use, src, ld,
+                                                            rows);
       TTI_LAUNCH();
     }
     lv.push_back(std::move(L));
