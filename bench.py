@@ -57,7 +57,12 @@ FP32_ALU_PEAK_TFLOPS = 80.54  # 152 SMs x 128 FP32 FMA/clk x 2 FLOP x 2.07 GHz
 # (workload, precision).  Valid only for the sources they were taken from: reported as null
 # once those change.
 PCG_TRAFFIC_SOURCES = ("pcg_fused.cu", "pcg_fused.cuh", "bbprec.cu", "bbprec.cuh")
-PCG_TRAFFIC = {}  # (workload, "fp64" | "mixed") -> (bytes per launch, sha256 of the sources)
+PCG_TRAFFIC = {  # (workload, "fp64" | "mixed") -> (bytes per launch, sha256 of the sources)
+    ("twisted_annulus_p3_n512", "fp64"):
+        (1417472, "bebcaadd0336a69925c8623c36570ebc1d940806410d2eed71676bee0a7fca66"),
+    ("twisted_annulus_p3_n512", "mixed"):
+        (1094208, "bebcaadd0336a69925c8623c36570ebc1d940806410d2eed71676bee0a7fca66"),
+}
 
 
 def pcg_traffic(workload, precision):

@@ -130,6 +130,26 @@ __global__ void k_splitk_reduce(const T *__restrict__ W, int ksplit, int m, int 
   }
 }
 
+// The same with one warp per output: lanes stride over the partials and combine them by a
+// fixed shuffle tree (deterministic), for few outputs over many partials, where a thread per
+// output would walk all ksplit partials serially.
+template <typename T>
+__global__ void __launch_bounds__(256) k_splitk_reduce_warp(const T *__restrict__ W, int ksplit, int m, int n,
+                                                            T alpha, T beta, T *C, long long ldc) {
+  const long long e = blockIdx.x * 8LL + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (e >= (long long)m * n) return;  // the whole warp leaves together
+  const long long i = e / n, j = e % n;
+  T acc = T(0);
+  for (int s = lane; s < ksplit; s += 32) acc += W[((long long)s * m + i) * n + j];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if (lane == 0) {
+    T *cp = C + i * ldc + j;
+    *cp = (beta == T(0)) ? alpha * acc : alpha * acc + beta * (*cp);
+  }
+}
+
 template <typename T>
 __global__ void k_scale_mat(T *C, int m, int n, long long ldc, long long sC, T beta) {
   const long long b = blockIdx.y;
@@ -208,8 +228,12 @@ void gemm(Ctx *c, bool ta, bool tb, int m, int n, int k, T alpha, const T *A, lo
       ProfScope ps(c, sizeof(T) == 8 ? PROF_GEMM64 : PROF_OFF, 2.0 * m * (double)n * k);
       launch(dim3(cdiv(n, BN), cdiv(m, BM), ksplit), A, B, T(0), W.as<T>(), n, 0, 0, 0, ksplit, kchunk);
     }
-    k_splitk_reduce<T><<<grid1d((long long)m * n, 256), 256, 0, c->stream>>>(W.as<T>(), ksplit, m, n, alpha, beta, C,
-                                                                             ldc);
+    const long long outs = (long long)m * n;
+    if (outs <= 64LL * c->num_sms)  // up to 8 CTAs of 8 warps per SM
+      k_splitk_reduce_warp<T><<<(unsigned)cdiv(outs, 8), 256, 0, c->stream>>>(W.as<T>(), ksplit, m, n, alpha, beta,
+                                                                             C, ldc);
+    else
+      k_splitk_reduce<T><<<grid1d(outs, 256), 256, 0, c->stream>>>(W.as<T>(), ksplit, m, n, alpha, beta, C, ldc);
     TTI_LAUNCH();
     return;
   }
@@ -382,16 +406,71 @@ __device__ __forceinline__ double cta_sum_tree(double v, double *red, double *ou
   return *out;
 }
 
+// Y <- H_0 H_1 ... H_{k-1} Y for the reflectors of one block (Wb: column j holds v_j below
+// the diagonal, the unit entry implied; tb: the k tau), applied backwards, one warp per
+// column of Y.  With `ident` Y starts as the first k columns of the identity: H_j then leaves
+// the columns cc < j unchanged (v_j is zero above row j and e_cc is zero from row j on), so
+// only columns j .. k-1 are touched, half the work of a general Y.
+__device__ __forceinline__ void qr_apply_back(const double *Wb, const double *tb, int mb, int k, double *Yb,
+                                              bool ident) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int j = k - 1; j >= 0; --j) {
+    const double tj = tb[j];
+    if (tj == 0.0) continue;  // uniform over the CTA
+    const double *v = Wb + (long long)j * mb;
+    for (int cc = (ident ? j : 0) + warp; cc < k; cc += nw) {
+      double *yc = Yb + (long long)cc * mb;
+      double w = (lane == 0) ? yc[j] : 0.0, w2 = 0.0;
+      int i = j + 1 + lane;
+      for (; i + 32 < mb; i += 64) {
+        w += v[i] * yc[i];
+        w2 += v[i + 32] * yc[i + 32];
+      }
+      if (i < mb) w += v[i] * yc[i];
+      w = warp_sum(w + w2) * tj;
+      if (lane == 0) yc[j] -= w;
+      for (int i2 = j + 1 + lane; i2 < mb; i2 += 32) yc[i2] -= w * v[i2];
+    }
+    __syncthreads();
+  }
+}
+
+// Y (block-column-major, mb x k) <- Cin's k x k slice of this block stacked on zeros, or the
+// identity when Cin is null.
+__device__ __forceinline__ void qr_init_y(double *Yb, int mb, int k, const double *Cin, long long blk) {
+  for (int e = threadIdx.x; e < mb * k; e += blockDim.x) {
+    const int cc = e / mb, i = e % mb;
+    double v = 0.0;
+    if (i < k) v = Cin ? Cin[(blk * k + i) * k + cc] : (i == cc ? 1.0 : 0.0);
+    Yb[(long long)cc * mb + i] = v;
+  }
+}
+
+// Rows blk*mb .. of Out (row-major, k columns, out_rows rows) <- Y.
+__device__ __forceinline__ void qr_store_y(const double *Yb, int mb, int k, double *Out, long long out_rows,
+                                           long long blk) {
+  for (int e = threadIdx.x; e < mb * k; e += blockDim.x) {
+    const int i = e / k, cc = e % k;
+    const long long row = blk * mb + i;
+    if (row < out_rows) Out[row * k + cc] = Yb[(long long)cc * mb + i];
+  }
+}
+
 // Householder QR of each mb x k block.  With use_smem the block is read straight from
 // the source matrix (row-major, ld, `rows` rows; rows past the end read as zero) into a
 // shared-memory copy, so no separate layout pass is needed, and the reflectors are
-// written back to W at the end; otherwise W already holds the block (k_qr_load).
+// written back to W at the end; otherwise W already holds the block (k_qr_load).  With
+// Qout (one block, use_smem, room for a second mb x k panel) the block's explicit Q is
+// formed here from the reflectors still in shared memory and stored to Qout's first
+// out_rows rows, which saves the separate Q-formation launch of a single-block level.
 __global__ void __launch_bounds__(256) k_qr_panel(double *__restrict__ W, int mb, int k, double *__restrict__ tau,
                                                   double *__restrict__ Rout, int use_smem,
-                                                  const double *__restrict__ src, long long ld, long long rows) {
+                                                  const double *__restrict__ src, long long ld, long long rows,
+                                                  double *__restrict__ Qout, long long out_rows) {
   extern __shared__ double qsm[];
   __shared__ double red[32];
   __shared__ double sh[4];
+  __shared__ double tsh[256];
   const long long blk = blockIdx.x;
   double *Wg = W + blk * (long long)mb * k;
   double *Wb = Wg;
@@ -424,6 +503,7 @@ __global__ void __launch_bounds__(256) k_qr_panel(double *__restrict__ W, int mb
         sh[2] = copysign(1.0, x0) / (fabs(x0) + ab);
       }
       tb[j] = sh[0];
+      tsh[j] = sh[0];
     }
     __syncthreads();
     const double tj = sh[0], sc = sh[2];
@@ -452,51 +532,50 @@ __global__ void __launch_bounds__(256) k_qr_panel(double *__restrict__ W, int mb
     const int row = e / k, cc = e % k;
     Rout[(blk * k + row) * k + cc] = (cc >= row && row < mb) ? Wb[(long long)cc * mb + row] : 0.0;
   }
+  if (Qout) {  // one block: Q = H_0 ... H_{k-1} I from the reflectors in shared memory
+    double *Yb = qsm + (long long)mb * k;
+    qr_init_y(Yb, mb, k, nullptr, 0);
+    __syncthreads();
+    qr_apply_back(Wb, tsh, mb, k, Yb, true);
+    qr_store_y(Yb, mb, k, Qout, out_rows, 0);
+    return;  // the reflectors are not needed again
+  }
   if (use_smem)
     for (int e = tid; e < mb * k; e += blockDim.x) Wg[e] = Wb[e];
 }
 
+// Q of one tree level: each block applies its reflectors to the k x k slice of the level
+// above (Cin, or the identity at the top) stacked on zeros.  use_smem: 0 works in global
+// memory (Y), 1 keeps Y in shared memory, 2 also stages the reflectors there.
 __global__ void __launch_bounds__(256) k_qr_formq(const double *__restrict__ W, const double *__restrict__ tau,
                                                   int mb, int k, const double *__restrict__ Cin,
                                                   double *__restrict__ Y, double *__restrict__ Out,
                                                   long long out_rows, int use_smem) {
   extern __shared__ double qsm[];
+  __shared__ double tsh[256];
   const long long blk = blockIdx.x;
   const double *Wb = W + blk * (long long)mb * k;
-  const double *tb = tau + blk * k;
   double *Yb = use_smem ? qsm : Y + blk * (long long)mb * k;
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
-  for (int e = tid; e < mb * k; e += blockDim.x) {
-    const int cc = e / mb, i = e % mb;
-    double v = 0.0;
-    if (i < k) v = Cin ? Cin[(blk * k + i) * k + cc] : (i == cc ? 1.0 : 0.0);
-    Yb[(long long)cc * mb + i] = v;
+  if (use_smem == 2) {
+    double *Ws = qsm + (long long)mb * k;
+    for (int e = threadIdx.x; e < mb * k; e += blockDim.x) Ws[e] = Wb[e];
+    Wb = Ws;
   }
+  for (int j = threadIdx.x; j < k; j += blockDim.x) tsh[j] = tau[blk * k + j];
+  qr_init_y(Yb, mb, k, Cin, blk);
   __syncthreads();
-  for (int j = k - 1; j >= 0; --j) {
-    const double tj = tb[j];
-    if (tj == 0.0) continue;
-    const double *v = Wb + (long long)j * mb;
-    for (int cc = warp; cc < k; cc += nw) {
-      double *yc = Yb + (long long)cc * mb;
-      double w = (lane == 0) ? yc[j] : 0.0;
-      for (int i = j + 1 + lane; i < mb; i += 32) w += v[i] * yc[i];
-      w = warp_sum(w) * tj;
-      if (lane == 0) yc[j] -= w;
-      for (int i = j + 1 + lane; i < mb; i += 32) yc[i] -= w * v[i];
-    }
-    __syncthreads();
-  }
-  for (int e = tid; e < mb * k; e += blockDim.x) {
-    const int i = e / k, cc = e % k;
-    const long long row = blk * mb + i;
-    if (row < out_rows) Out[row * k + cc] = Yb[(long long)cc * mb + i];
-  }
+  qr_apply_back(Wb, tsh, mb, k, Yb, Cin == nullptr);
+  qr_store_y(Yb, mb, k, Out, out_rows, blk);
 }
 
+// Rows per TSQR block: 128-row blocks (4k for wide panels), or the whole matrix as one
+// block when it has at most 512 rows and little FP64 work (rows k^2 <= 32k FMAs): the
+// upper levels of a tree over narrow panels then take one launch instead of two or three.
+// Taller single blocks lose: one CTA's column chain grows with the rows.
 static int qr_block_rows(long long rows, int k) {
   int mb = std::max(4 * k, 128);
   mb = (mb + 31) / 32 * 32;
+  if (rows > mb && rows <= 512 && rows * k * (long long)k <= 32768) mb = (int)((rows + 31) / 32 * 32);
   if (rows <= mb) {
     long long r = std::max<long long>(rows, k);
     mb = (int)((r + 31) / 32 * 32);
@@ -518,6 +597,8 @@ void qr(Ctx *c, int m, int k, const double *A, long long lda, double *Q, double 
   std::vector<Level> lv;
   const double *src = A;
   long long ld = lda, rows = m;
+  DBuf top_q;           // Q of the top block, formed by its panel launch (the next level's Cin)
+  bool fused = false;   // the top level's Q is already formed
   for (;;) {
     Level L;
     L.rows = rows;
@@ -532,10 +613,24 @@ void qr(Ctx *c, int m, int k, const double *A, long long lda, double *Q, double 
       k_qr_load<<<L.nblk, 256, 0, c->stream>>>(src, ld, rows, k, L.mb, L.W.d());
       TTI_LAUNCH();
     }
+    // a single block with room for a second panel forms its Q in the same launch
+    fused = Q && L.nblk == 1 && 2 * sm <= kQrSmemBytes;
+    double *qout = nullptr;
+    long long out_rows = 0;
+    if (fused) {
+      if (lv.empty()) {
+        qout = Q;
+        out_rows = m;
+      } else {
+        out_rows = (long long)lv.back().nblk * k;
+        top_q = DBuf(c, (size_t)out_rows * k * sizeof(double));
+        qout = top_q.d();
+      }
+    }
     {
-      ProfScope ps(c, PROF_QR, 2.0 * L.nblk * (double)L.mb * k * k);
-      k_qr_panel<<<L.nblk, 256, use ? sm : 0, c->stream>>>(L.W.d(), L.mb, k, L.tau.d(), L.Rs.d(), use, src, ld,
-                                                            rows);
+      ProfScope ps(c, PROF_QR, (fused ? 3.0 : 2.0) * L.nblk * (double)L.mb * k * k);
+      k_qr_panel<<<L.nblk, 256, fused ? 2 * sm : (use ? sm : 0), c->stream>>>(
+          L.W.d(), L.mb, k, L.tau.d(), L.Rs.d(), use, src, ld, rows, qout, out_rows);
       TTI_LAUNCH();
     }
     lv.push_back(std::move(L));
@@ -547,11 +642,10 @@ void qr(Ctx *c, int m, int k, const double *A, long long lda, double *Q, double 
   }
   TTI_CUDA(cudaMemcpyAsync(R, lv.back().Rs.d(), (size_t)k * k * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
   if (!Q) return;  // R only: the orthogonal factor is not formed
-  DBuf Cbuf;
-  const double *Cin = nullptr;
-  for (int L = (int)lv.size() - 1; L >= 0; --L) {
+  DBuf Cbuf = std::move(top_q);
+  const double *Cin = fused ? Cbuf.d() : nullptr;
+  for (int L = (int)lv.size() - (fused ? 2 : 1); L >= 0; --L) {
     Level &l = lv[L];
-    DBuf Y(c, (size_t)l.nblk * l.mb * k * sizeof(double));
     DBuf Out;
     double *outp;
     long long out_rows;
@@ -559,14 +653,15 @@ void qr(Ctx *c, int m, int k, const double *A, long long lda, double *Q, double 
       outp = Q;
       out_rows = m;
     } else {
-      out_rows = lv[L - 1].rows > 0 ? (long long)lv[L - 1].nblk * k : 0;
+      out_rows = (long long)lv[L - 1].nblk * k;
       Out = DBuf(c, (size_t)out_rows * k * sizeof(double));
       outp = Out.d();
     }
     const size_t sm = (size_t)l.mb * k * sizeof(double);
-    const int use = sm <= kQrSmemBytes;
-    k_qr_formq<<<l.nblk, 256, use ? sm : 0, c->stream>>>(l.W.d(), l.tau.d(), l.mb, k, Cin, Y.d(), outp, out_rows,
-                                                         use);
+    const int use = 2 * sm <= kQrSmemBytes ? 2 : (sm <= kQrSmemBytes ? 1 : 0);
+    DBuf Y;
+    if (!use) Y = DBuf(c, (size_t)l.nblk * l.mb * k * sizeof(double));
+    k_qr_formq<<<l.nblk, 256, use * sm, c->stream>>>(l.W.d(), l.tau.d(), l.mb, k, Cin, Y.d(), outp, out_rows, use);
     TTI_LAUNCH();
     Cbuf = std::move(Out);
     Cin = Cbuf.d();
@@ -594,6 +689,7 @@ __global__ void __launch_bounds__(1024) k_jacobi_svd(int k, const double *__rest
   extern __shared__ double smem[];
   __shared__ int perm[256];
   __shared__ double nrm[256];
+  __shared__ double cn[256];
   const int kp = k + (k & 1);
   double *W = use_smem ? smem : Wg;           // W[c * k + i]: column c, row i
   double *Vw = use_smem ? smem + (size_t)kp * k : Vg;
@@ -627,6 +723,19 @@ __global__ void __launch_bounds__(1024) k_jacobi_svd(int k, const double *__rest
   int sweep = 0;
   for (; sweep < 60; ++sweep) {
     int rotated = 0;
+    // squared column norms, exact at the start of each sweep and updated by every rotation
+    // (a' = a - t g, b' = b + t g for the pair's squared norms a, b and product g), so a
+    // round reduces only the product: one shuffle tree instead of three
+    for (int base = 0; base < kp; base += ngrp) {
+      const int cc = base + grp;
+      double a = 0.0;
+      if (cc < kp)
+        for (int i = li; i < k; i += G) a += W[(size_t)cc * k + i] * W[(size_t)cc * k + i];
+#pragma unroll
+      for (int o = G / 2; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+      if (cc < kp && li == 0) cn[cc] = a;
+    }
+    sync();
     for (int rd = 0; rd < kp - 1; ++rd) {
       // every lane runs the same number of passes (the shuffles below need the whole
       // warp); a group without a pair in this pass contributes zeros and rotates nothing
@@ -640,20 +749,13 @@ __global__ void __launch_bounds__(1024) k_jacobi_svd(int k, const double *__rest
           if (p > q) { int t = p; p = q; q = t; }
         }
         double *wp = W + (size_t)p * k, *wq = W + (size_t)q * k;
-        double a = 0.0, b = 0.0, g = 0.0;
+        double g = 0.0;
         if (act)
-          for (int i = li; i < k; i += G) {
-            const double x = wp[i], y = wq[i];
-            a += x * x;
-            b += y * y;
-            g += x * y;
-          }
+          for (int i = li; i < k; i += G) g += wp[i] * wq[i];
 #pragma unroll
-        for (int o = G / 2; o > 0; o >>= 1) {
-          a += __shfl_xor_sync(0xffffffffu, a, o);
-          b += __shfl_xor_sync(0xffffffffu, b, o);
-          g += __shfl_xor_sync(0xffffffffu, g, o);
-        }
+        for (int o = G / 2; o > 0; o >>= 1) g += __shfl_xor_sync(0xffffffffu, g, o);
+        const double a = act ? cn[p] : 0.0, b = act ? cn[q] : 0.0;
+        bool renorm = false;
         if (act && g != 0.0 && a > tiny && b > tiny && g * g > tol2 * a * b) {
           const double num = b - a, den = 2.0 * g;
           const float zf = (float)num / (float)den;
@@ -676,7 +778,32 @@ __global__ void __launch_bounds__(1024) k_jacobi_svd(int k, const double *__rest
             vp[i] = cs * x - sn * y;
             vq[i] = sn * x + cs * y;
           }
+          const double an = a - t * g, bn = b + t * g;
+          // a norm that drops by two orders has lost its relative accuracy to cancellation:
+          // recompute both from the rotated columns instead (the group agrees on the test)
+          renorm = an < 0.01 * a || bn < 0.01 * b;
+          if (li == 0) {
+            cn[p] = an;
+            cn[q] = bn;
+          }
           rotated = 1;
+        }
+        if (__any_sync(0xffffffffu, renorm)) {
+          double a2 = 0.0, b2 = 0.0;
+          if (renorm)
+            for (int i = li; i < k; i += G) {
+              a2 += wp[i] * wp[i];
+              b2 += wq[i] * wq[i];
+            }
+#pragma unroll
+          for (int o = G / 2; o > 0; o >>= 1) {
+            a2 += __shfl_xor_sync(0xffffffffu, a2, o);
+            b2 += __shfl_xor_sync(0xffffffffu, b2, o);
+          }
+          if (renorm && li == 0) {
+            cn[p] = a2;
+            cn[q] = b2;
+          }
         }
       }
       sync();

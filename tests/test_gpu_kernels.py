@@ -132,8 +132,10 @@ def test_gemm_matches_numpy(tt, ctx, m, n, k, ta, tb):
     assert np.max(np.abs(C.cpu().numpy() - ref)) <= 1e-13 * max(1.0, np.sqrt(k)) * max(1.0, np.max(np.abs(ref)))
 
 
-@pytest.mark.parametrize("m,k", [(1000, 37), (100000, 16), (5000, 128), (7, 20), (300, 1), (2048, 256)])
+@pytest.mark.parametrize("m,k", [(1000, 37), (100000, 16), (5000, 128), (7, 20), (300, 1), (2048, 256),
+                                 (14280, 4), (50000, 3)])
 def test_qr(tt, ctx, m, k):
+    """Tall panels, wide panels, m < k, and narrow panels whose upper tree level is one whole block."""
     import torch
     rng = np.random.default_rng(m + k)
     A = rng.standard_normal((m, k))
