@@ -533,7 +533,10 @@ int tt_iga_gemm_f64(tt_iga_ctx *ctx, int ta, int tb, int m, int n, int k, double
  * upper triangular).  k <= 256.  Q may alias A only if lda == k. */
 int tt_iga_qr(tt_iga_ctx *ctx, int m, int k, const double *A, int lda, double *Q, double *R);
 /* SVD of a small square matrix A (device, k x k): A = U diag(s) V^T by
- * one-sided Jacobi, FP64, singular values descending.  k <= 256. */
+ * one-sided Jacobi on the rows of A, FP64, singular values descending.
+ * U, s, V row-major device buffers (k x k, k, k x k).  U has orthonormal
+ * columns to FP64 precision; column j of V has unit norm (zero when s_j = 0)
+ * and is orthogonal to the others to about eps s_0 / s_j.  k <= 256. */
 int tt_iga_svd_small(tt_iga_ctx *ctx, int k, const double *A, double *U, double *s, double *V);
 /* Allocation-free SVD.  The paper has no counterpart: this is a library
  * service for callers that cannot allocate device memory.  Such callers are,

@@ -389,23 +389,6 @@ __global__ void k_qr_load(const double *__restrict__ A, long long lda, long long
   }
 }
 
-// Sum over the CTA, result broadcast: warps reduce by shuffles, warp 0 combines
-// the warp partials in a tree (log2 of the warp count dependent adds instead of
-// one per warp, each FP64 add costing tens of cycles here).
-__device__ __forceinline__ double cta_sum_tree(double v, double *red, double *out) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
-  v = warp_sum(v);
-  if (lane == 0) red[warp] = v;
-  __syncthreads();
-  if (warp == 0) {
-    double t = (lane < nw) ? red[lane] : 0.0;
-    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
-    if (lane == 0) *out = t;
-  }
-  __syncthreads();
-  return *out;
-}
-
 // Y <- H_0 H_1 ... H_{k-1} Y for the reflectors of one block (Wb: column j holds v_j below
 // the diagonal, the unit entry implied; tb: the k tau), applied backwards, one warp per
 // column of Y.  With `ident` Y starts as the first k columns of the identity: H_j then leaves
@@ -468,8 +451,6 @@ __global__ void __launch_bounds__(256) k_qr_panel(double *__restrict__ W, int mb
                                                   const double *__restrict__ src, long long ld, long long rows,
                                                   double *__restrict__ Qout, long long out_rows) {
   extern __shared__ double qsm[];
-  __shared__ double red[32];
-  __shared__ double sh[4];
   __shared__ double tsh[256];
   const long long blk = blockIdx.x;
   double *Wg = W + blk * (long long)mb * k;
@@ -485,45 +466,82 @@ __global__ void __launch_bounds__(256) k_qr_panel(double *__restrict__ W, int mb
   }
   double *tb = tau + blk * k;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
-  for (int j = 0; j < k; ++j) {
-    double *col = Wb + (long long)j * mb;
-    double s = 0.0;
-    for (int i = j + 1 + tid; i < mb; i += blockDim.x) s += col[i] * col[i];
-    s = cta_sum_tree(s, red, &sh[3]);
-    if (tid == 0) {
-      const double x0 = (j < mb) ? col[j] : 0.0;
-      if (s == 0.0) {
-        sh[0] = 0.0; sh[1] = x0; sh[2] = 0.0;
-      } else {
-        // beta = -sign(x0) sqrt(h), h = x0^2 + s; with y = 1/sqrt(h): |beta| = h y,
-        // tau = (beta - x0) / beta = 1 + |x0| y, and 1/(x0 - beta) = sign(x0) / (|x0| + h y)
-        const double h = x0 * x0 + s, y = rsqrt(h), ab = h * y;
-        sh[0] = 1.0 + fabs(x0) * y;
-        sh[1] = -copysign(ab, x0);
-        sh[2] = copysign(1.0, x0) / (fabs(x0) + ab);
-      }
-      tb[j] = sh[0];
-      tsh[j] = sh[0];
+  // Reflector of column c, run by one warp from s (its sum of squares below the diagonal,
+  // the same value in every lane) and its diagonal entry: every lane forms the same
+  // scalars, the warp scales the column below the diagonal, lane 0 stores tau and R's
+  // diagonal.  beta = -sign(x0) sqrt(h), h = x0^2 + s; with y = 1/sqrt(h): |beta| = h y,
+  // tau = (beta - x0) / beta = 1 + |x0| y, and 1/(x0 - beta) = sign(x0) / (|x0| + h y).
+  auto make_reflector = [&](int c, double s) {
+    double *col = Wb + (long long)c * mb;
+    const double x0 = col[c];
+    double t = 0.0, beta = x0, sc = 0.0;
+    if (s != 0.0) {
+      const double h = x0 * x0 + s, y = rsqrt(h), ab = h * y;
+      t = 1.0 + fabs(x0) * y;
+      beta = -copysign(ab, x0);
+      sc = copysign(1.0, x0) / (fabs(x0) + ab);
+      for (int i = c + 1 + lane; i < mb; i += 32) col[i] *= sc;
     }
-    __syncthreads();
-    const double tj = sh[0], sc = sh[2];
-    if (tj != 0.0)
-      for (int i = j + 1 + tid; i < mb; i += blockDim.x) col[i] *= sc;
-    __syncthreads();
-    if (tid == 0 && j < mb) col[j] = sh[1];
-    if (tj != 0.0) {
-      for (int cc = j + 1 + warp; cc < k; cc += nw) {
+    if (lane == 0) {
+      col[c] = beta;
+      tb[c] = t;
+      tsh[c] = t;
+    }
+  };
+  // Look-ahead: warp 0 applies reflector j to column j + 1 only, summing the squares of the
+  // updated entries as it goes, and forms reflector j + 1 at once; warps 1.. update the
+  // other trailing columns meanwhile.  One barrier per column, no CTA-wide reduction.
+  // (Launched with 256 threads: warps 1..7 exist.)
+  if (warp == 0) {
+    double sq = 0.0;
+    for (int i = 1 + lane; i < mb; i += 32) sq += Wb[i] * Wb[i];
+    sq = warp_sum(sq);
+    __syncwarp();
+    make_reflector(0, sq);
+  }
+  __syncthreads();
+  for (int j = 0; j < k; ++j) {
+    const double tj = tsh[j];
+    const double *v = Wb + (long long)j * mb;
+    if (warp == 0) {
+      if (j + 1 < k) {
+        double *cn = Wb + (long long)(j + 1) * mb;
+        double sq = 0.0;
+        if (tj != 0.0) {
+          double w = (lane == 0) ? cn[j] : 0.0, w2 = 0.0;
+          int i = j + 1 + lane;
+          for (; i + 32 < mb; i += 64) {
+            w += v[i] * cn[i];
+            w2 += v[i + 32] * cn[i + 32];
+          }
+          if (i < mb) w += v[i] * cn[i];
+          w = warp_sum(w + w2) * tj;
+          if (lane == 0) cn[j] -= w;
+          for (int i2 = j + 1 + lane; i2 < mb; i2 += 32) {
+            const double y = cn[i2] - w * v[i2];
+            cn[i2] = y;
+            if (i2 > j + 1) sq += y * y;
+          }
+        } else {
+          for (int i2 = j + 2 + lane; i2 < mb; i2 += 32) sq += cn[i2] * cn[i2];
+        }
+        sq = warp_sum(sq);
+        __syncwarp();
+        make_reflector(j + 1, sq);
+      }
+    } else if (tj != 0.0) {
+      for (int cc = j + 1 + warp; cc < k; cc += nw - 1) {
         double *ccol = Wb + (long long)cc * mb;
         double w = (lane == 0) ? ccol[j] : 0.0, w2 = 0.0;
         int i = j + 1 + lane;
         for (; i + 32 < mb; i += 64) {
-          w += col[i] * ccol[i];
-          w2 += col[i + 32] * ccol[i + 32];
+          w += v[i] * ccol[i];
+          w2 += v[i + 32] * ccol[i + 32];
         }
-        if (i < mb) w += col[i] * ccol[i];
+        if (i < mb) w += v[i] * ccol[i];
         w = warp_sum(w + w2) * tj;
         if (lane == 0) ccol[j] -= w;
-        for (int i = j + 1 + lane; i < mb; i += 32) ccol[i] -= w * col[i];
+        for (int i2 = j + 1 + lane; i2 < mb; i2 += 32) ccol[i2] -= w * v[i2];
       }
     }
     __syncthreads();
@@ -670,9 +688,16 @@ void qr(Ctx *c, int m, int k, const double *A, long long lda, double *Q, double 
 
 // ------------------------------------------------------- one-sided Jacobi SVD
 
-// One-sided Jacobi SVD of a k x k matrix (k <= 256), one CTA.  Each pair of
-// columns is handled by a group of G lanes (G = 4, 8, 16 or 32, the smallest
-// power of two >= k, 32 beyond): the three dot products reduce in log2(G)
+// One-sided Jacobi SVD of a k x k matrix (k <= 256), one CTA, run on the
+// columns of A^T (the rows of A): with A^T J = W converged to orthogonal
+// columns, A = J diag(|w_j|) (w_j / |w_j|)^T, so U is the accumulated rotation
+// J, exactly orthonormal, and V the normalised columns of W.  The inputs of the
+// TT algorithms are triangular factors of tall QRs with graded singular
+// values, for which the rows converge in about half the sweeps of the columns,
+// and the left factor they need comes out orthonormal to FP64 precision (a
+// column of V is orthogonal to the others to about eps s_0 / s_j).  Each pair
+// of columns is handled by a group of G lanes (G = 4, 8, 16 or 32, the
+// smallest power of two >= k, 32 beyond): the product reduces in log2(G)
 // shuffle levels, and all kp/2 pairs of a round run at once when the CTA is
 // large enough (for k <= 8 a single warp, synchronised with __syncwarp).  The
 // rotation angle is computed in FP32 from the FP64 dot products and cos/sin are
@@ -703,7 +728,7 @@ __global__ void __launch_bounds__(1024) k_jacobi_svd(int k, const double *__rest
   double fro = 0.0;
   for (int e = tid; e < kp * k; e += blockDim.x) {
     const int cc = e / k, i = e % k;
-    const double v = (cc < k) ? A[(long long)i * k + cc] : 0.0;
+    const double v = (cc < k) ? A[(long long)cc * k + i] : 0.0;  // column cc of A^T
     W[e] = v;
     fro += v * v;
     Vw[e] = (cc == i) ? 1.0 : 0.0;
@@ -833,8 +858,8 @@ __global__ void __launch_bounds__(1024) k_jacobi_svd(int k, const double *__rest
     const int i = e / k, j = e % k;
     const int src = perm[j];
     const double sv = nrm[src];
-    U[e] = (sv > 0.0) ? W[(size_t)src * k + i] / sv : 0.0;
-    V[e] = Vw[(size_t)src * k + i];
+    U[e] = Vw[(size_t)src * k + i];
+    V[e] = (sv > 0.0) ? W[(size_t)src * k + i] / sv : 0.0;
   }
   for (int j = tid; j < k; j += blockDim.x) S[j] = nrm[perm[j]];
 }

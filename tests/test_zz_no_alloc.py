@@ -56,10 +56,10 @@ def test_noalloc_svd_matches_allocating_svd_and_numpy():
                 assert np.all(np.diff(sh) <= 0.0), (k, rep)
                 assert np.max(np.abs(sh - s_np)) <= tol, (k, rep)
                 assert np.max(np.abs((Uh * sh) @ Vh.T - A)) <= tol, (k, rep)
-                assert np.max(np.abs(Vh.T @ Vh - np.eye(k))) <= 1e-12, (k, rep)
-                # columns of U belong to nonzero singular values; each has unit norm and they are
+                assert np.max(np.abs(Uh.T @ Uh - np.eye(k))) <= 1e-12, (k, rep)
+                # columns of V belong to nonzero singular values; each has unit norm and they are
                 # orthogonal to the accuracy their singular value allows
-                G = Uh.T @ Uh
+                G = Vh.T @ Vh
                 assert np.max(np.abs(np.diag(G) - 1.0)) <= 1e-12, (k, rep)
                 big = sh >= 1e-6 * sh[0]
                 assert np.max(np.abs(G[np.ix_(big, big)] - np.eye(int(big.sum())))) <= 1e-10, (k, rep)
