@@ -287,8 +287,9 @@ struct Amen {
     a.PhiL = PhiLk; a.PhiR = PhiRk; a.A = Ak; a.Lf = L; a.b = b; a.x = x;
     if (bb) {
       a.edge = 1;
-      a.bbLinv = bb->Linv.as<float>(); a.bbG = bb->G.as<float>(); a.bbH = bb->H.as<float>();
+      a.bbLinv = bb->Linv.as<float>(); a.bbUl = bb->Ul.as<float>(); a.bbUr = bb->Ur.as<float>();
       a.bbM = bb->M;
+      a.bbS = bb->S;
     }
     a.rl = rl(k); a.rr = rr(k); a.Rl = R[k]; a.Rr = R[k + 1]; a.n = n(k); a.p = S->p;
     a.tol2 = tol * tol;
@@ -330,17 +331,16 @@ struct Amen {
               (tr[1] - tr[0]) * 1e-3, iters ? ph[0] / iters * 1e-3 : 0.0, iters ? ph[1] / iters * 1e-3 : 0.0);
       if (a.edge) {
         const unsigned long long *sb = tr.data() + 2 + 2 * 128;
-        fprintf(stderr, "[tt_iga pcg]   block-band apply: update %.1f, L^-1 r %.1f, forward %.1f, L^-T y %.1f, "
-                        "backward %.1f, scatter %.1f us\n",
+        fprintf(stderr, "[tt_iga pcg]   block-band apply: update %.1f, forward %.1f, top %.1f, backward %.1f, "
+                        "scatter %.1f us\n",
                 (sb[1] - sb[0]) * 1e-3, (sb[2] - sb[1]) * 1e-3, (sb[3] - sb[2]) * 1e-3, (sb[4] - sb[3]) * 1e-3,
-                (sb[5] - sb[4]) * 1e-3, (sb[6] - sb[5]) * 1e-3);
+                (sb[6] - sb[5]) * 1e-3);
       }
     }
     int err = 0;
     memcpy(&err, &hout[3], sizeof(int));
     if (err)
-      fail(TT_IGA_ERR_TIMEOUT, "pcg: a %s wait ran out",
-           err == 2 ? "staging copy" : (err == 3 ? "tensor-core completion" : "grid barrier"));
+      fail(TT_IGA_ERR_TIMEOUT, "pcg: a %s wait ran out", err == 3 ? "tensor-core completion" : "grid barrier");
     const int it = (int)hout[0];
     last_pcg_converged = (it < maxit) && hout[1] <= a.tol2;
     {
@@ -408,24 +408,20 @@ struct Amen {
     }
     if (edge) {
       cudaEvent_t ev[2] = {nullptr, nullptr};
-      DBuf clk;
       if (o.verbose >= 2) {
-        clk = DBuf(c, 4 * sizeof(unsigned long long));
         TTI_CUDA(cudaEventCreate(&ev[0]));
         TTI_CUDA(cudaEventCreate(&ev[1]));
         TTI_CUDA(cudaEventRecord(ev[0], c->stream));
       }
-      bb_prec_build(hb, PhiL[k].d(), rl(k), A[k], PhiR[k].d(), rr(k), bb, clk.as<unsigned long long>());
+      bb_prec_build(hb, PhiL[k].d(), rl(k), A[k], PhiR[k].d(), rr(k), bb);
       if (o.verbose >= 2) {
         float ms = 0.f;
-        unsigned long long ck[3];
         TTI_CUDA(cudaEventRecord(ev[1], c->stream));
         TTI_CUDA(cudaEventSynchronize(ev[1]));
         TTI_CUDA(cudaEventElapsedTime(&ms, ev[0], ev[1]));
-        c->d2h(ck, clk.get(), sizeof(ck));
-        fprintf(stderr, "[tt_iga pcg] core %d block-band preconditioner (m %d n %d): build+factor+post %.1f us; "
-                        "factor cycles/step: diagonal %.0f panel %.0f update %.0f\n", k, rl(k) * rr(k), n(k),
-                ms * 1e3, (double)ck[0] / n(k), (double)ck[1] / n(k), (double)ck[2] / n(k));
+        fprintf(stderr, "[tt_iga pcg] core %d block-band preconditioner (m %d n %d): %d super-rows of %d, %d "
+                        "reduction levels, build and factor %.1f us\n", k, rl(k) * rr(k), n(k), bb.S, bb.q, bb.levels,
+                ms * 1e3);
         cudaEventDestroy(ev[0]);
         cudaEventDestroy(ev[1]);
       }
@@ -437,8 +433,8 @@ struct Amen {
       TTI_CUDA(cudaEventRecord(ev_out, hb->stream));
       L.rehome(parent);
       bb.Linv.rehome(parent);
-      bb.G.rehome(parent);
-      bb.H.rehome(parent);
+      bb.Ul.rehome(parent);
+      bb.Ur.rehome(parent);
     }
     if (res0 < 0.0) {
       try {

@@ -1,9 +1,8 @@
 // Exact block-band preconditioner of small-interface AMEn local systems:
-// assembly of the symmetric block band (FP64 contractions, FP32 result), the
-// sequential right-looking block Cholesky in one CTA, and the parallel
-// post-pass that turns the factor into the blocks the substitutions use.
-// Block size M (4 or 8) is m = rl * rr rounded up; padding rows and columns
-// carry the identity.
+// assembly of the symmetric block band (FP64 contractions, FP32 result), then
+// the odd-even (cyclic) reduction of its block-tridiagonal super-row form, one
+// launch pair per level (eliminations, then the Schur updates of the rows
+// left), so the factorisation is log2 of the super-row count deep.
 #include "bbprec.cuh"
 
 namespace ttiga {
@@ -46,270 +45,154 @@ __global__ void k_bb_build(const double *__restrict__ PhiL, int rl, int Rl, cons
   }
 }
 
-// Right-looking block Cholesky of the block band by one warp.
-// The live blocks (i+k, i+l), 0 <= l <= k <= p, sit in a ring of (p+1)^2 block
-// slots indexed by absolute block row and column modulo p+1, so nothing moves
-// between steps.  Step i: (a) every lane factors the M x M diagonal block
-// redundantly in its own registers (no shuffles on the dependent path; the
-// reciprocal pivots are the rsqrt results); (b) the panel X_k = W(i+k, i)
-// L_ii^{-T} by row-wise forward substitution against the register copy of
-// L_ii; (c) the trailing update W(i+k, i+l) -= X_k X_l^T in 4 x 4 register
-// tiles, and block row i+1+p (loaded into registers at the start of the step)
-// enters the slots of row i.  FP32 throughout: each step is a chain of
-// dependent operations, and this is a preconditioner.  A pivot that
-// cancellation drives below 1e-6 of the diagonal entry is replaced by that
-// entry (the factor stays SPD; PCG checks convergence).
-// Outputs: Ld[i] = L_ii (zero above), Lx[i][k-1] = L(i+k, i).
-template <int M>
-__global__ void __launch_bounds__(32) k_bb_factor(const float *__restrict__ Blow, int n, int p, int m,
-                                                   float *__restrict__ Ld, float *__restrict__ Lx,
-                                                   unsigned long long *phase_clk) {
-  constexpr int BS = M * M, T4 = M / 4, TB = T4 * T4, PE = (BS + 31) / 32;
-  // phase_clk (optional): SM clock cycles lane 0 spends in each phase of all steps
-  unsigned long long ck0 = 0, ck1 = 0, ck2 = 0, t0 = 0;
-  const bool prof = phase_clk != nullptr && threadIdx.x == 0;
-  auto stamp = [&](unsigned long long &acc) {
-    if (prof) {
-      const unsigned long long t1 = clock64();
-      acc += t1 - t0;
-      t0 = t1;
+// D[J] (q x q) and C[J] = B(super-row J, super-row J - 1) from the lower block band:
+// entry (a M + e, b M + f) of a super-row pair is B(i, j)[e][f] with i = p J + a and
+// j = p J + b (D) or p (J - 1) + b (C); B(i, j) = B(j, i)^T above the diagonal, and
+// block rows past n carry the identity with no coupling.
+__global__ void k_bcr_init(const float *__restrict__ Blow, int n, int p, int M, int S, int q, float *__restrict__ D,
+                           float *__restrict__ C) {
+  const long long per = (long long)q * q, tot = (long long)S * per;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < 2 * tot;
+       t += (long long)gridDim.x * blockDim.x) {
+    const bool coup = t >= tot;
+    const long long u = coup ? t - tot : t;
+    const int J = (int)(u / per), rc = (int)(u % per), r = rc / q, cc = rc % q;
+    const int a = r / M, e = r % M, bb = cc / M, f = cc % M;
+    const long long i = (long long)p * J + a, j = coup ? (long long)p * (J - 1) + bb : (long long)p * J + bb;
+    float v = 0.f;
+    if (coup && J == 0) {
+      v = 0.f;
+    } else if (i >= n || j >= n) {
+      v = (i == j && e == f) ? 1.f : 0.f;
+    } else if (j <= i && i - j <= p) {
+      v = Blow[(i * (p + 1) + (j - i + p)) * M * M + e * M + f];
+    } else if (j > i && j - i <= p) {
+      v = Blow[(j * (p + 1) + (i - j + p)) * M * M + f * M + e];
     }
-  };
-  extern __shared__ float4 fsm4[];
-  float *fsm = reinterpret_cast<float *>(fsm4);
-  const int nb = p + 1, P = p * M, npairs = p * (p + 1) / 2;
-  float *Wr = fsm;                // nb x nb ring of M x M blocks
-  float *Xs = Wr + nb * nb * BS;  // panel [p M][M]
-  int *pairs = reinterpret_cast<int *>(Xs + P * M);  // (kb, lb) of pair index, [28][2]
-  const int lane = threadIdx.x;
-  auto wrap = [nb](int v) { return v >= nb ? v - nb : v; };  // v < 2 nb
-  auto slot = [&](int sr, int sc) { return Wr + (sr * nb + sc) * BS; };
-  auto ident = [](int e) { return (e / M == e % M) ? 1.f : 0.f; };
-  if (lane == 0)
-    for (int kb = 1, q = 0; kb <= p; ++kb)
-      for (int lb = 1; lb <= kb; ++lb, ++q) {
-        pairs[2 * q] = kb;
-        pairs[2 * q + 1] = lb;
-      }
-  for (int k = 0; k < nb; ++k)
-    for (int l = 0; l <= k; ++l) {
-      float *dst = slot(k, l);
-      for (int e = lane; e < BS; e += 32)
-        dst[e] = (k < n) ? Blow[((long long)k * nb + (p - k + l)) * BS + e] : (l == k ? ident(e) : 0.f);
-    }
-  __syncwarp();
-  int s0 = 0;  // slot of block row / column i
-  for (int i = 0; i < n; ++i, s0 = wrap(s0 + 1)) {
-    if (prof) t0 = clock64();
-    const int inew = i + 1 + p;
-    float pre[8][PE];
-#pragma unroll
-    for (int l = 0; l < 8; ++l)
-#pragma unroll
-      for (int u = 0; u < PE; ++u) {
-        const int e = lane + u * 32;
-        pre[l][u] = 0.f;
-        if (l < nb && e < BS)
-          pre[l][u] = (inew < n) ? Blow[((long long)inew * nb + l) * BS + e] : (l == p ? ident(e) : 0.f);
-      }
-    // (a) diagonal block, factored by every lane
-    float Lr[M][M], ir[M];
-    {
-      const float4 *D4 = reinterpret_cast<const float4 *>(slot(s0, s0));
-#pragma unroll
-      for (int r = 0; r < M; ++r)
-#pragma unroll
-        for (int c4 = 0; c4 < T4; ++c4) {
-          const float4 v = D4[r * T4 + c4];
-          Lr[r][4 * c4 + 0] = v.x;
-          Lr[r][4 * c4 + 1] = v.y;
-          Lr[r][4 * c4 + 2] = v.z;
-          Lr[r][4 * c4 + 3] = v.w;
-        }
-#pragma unroll
-      for (int j = 0; j < M; ++j) {
-        ir[j] = 1.f;
-        if (j < m) {
-          float piv = Lr[j][j];
-          const float d0 = slot(s0, s0)[j * (M + 1)];
-          if (!(piv > 1e-6f * d0)) piv = (d0 > 0.f) ? d0 : 1.f;
-          const float inv = rsqrtf(piv);
-          ir[j] = inv;
-          Lr[j][j] = piv * inv;
-#pragma unroll
-          for (int r = j + 1; r < M; ++r) Lr[r][j] *= inv;
-#pragma unroll
-          for (int r = j + 1; r < M; ++r)
-#pragma unroll
-            for (int c = j + 1; c <= r; ++c) Lr[r][c] -= Lr[r][j] * Lr[c][j];
-        }
-      }
-      if (lane == 0) {
-        float4 *dst = reinterpret_cast<float4 *>(Ld + (long long)i * BS);
-#pragma unroll
-        for (int r = 0; r < M; ++r)
-#pragma unroll
-          for (int c4 = 0; c4 < T4; ++c4)
-            dst[r * T4 + c4] = make_float4(4 * c4 + 0 <= r ? Lr[r][4 * c4 + 0] : 0.f,
-                                           4 * c4 + 1 <= r ? Lr[r][4 * c4 + 1] : 0.f,
-                                           4 * c4 + 2 <= r ? Lr[r][4 * c4 + 2] : 0.f,
-                                           4 * c4 + 3 <= r ? Lr[r][4 * c4 + 3] : 0.f);
-      }
-    }
-    stamp(ck0);
-    // (b) panel rows: x (row e of X_k) solves L_ii x = w
-    for (int t = lane; t < P; t += 32) {
-      const int k = 1 + t / M, e = t % M;
-      const float4 *w4 = reinterpret_cast<const float4 *>(slot(wrap(s0 + k), s0) + e * M);
-      float x[M];
-#pragma unroll
-      for (int c4 = 0; c4 < T4; ++c4) {
-        const float4 v = w4[c4];
-        x[4 * c4 + 0] = v.x;
-        x[4 * c4 + 1] = v.y;
-        x[4 * c4 + 2] = v.z;
-        x[4 * c4 + 3] = v.w;
-      }
-#pragma unroll
-      for (int cc = 0; cc < M; ++cc) {
-        x[cc] *= ir[cc];
-#pragma unroll
-        for (int c = cc + 1; c < M; ++c) x[c] -= Lr[c][cc] * x[cc];
-      }
-      float4 *xs = reinterpret_cast<float4 *>(Xs + t * M);
-      float4 *xg = reinterpret_cast<float4 *>(Lx + (((long long)i * p + (k - 1)) * M + e) * M);
-#pragma unroll
-      for (int c4 = 0; c4 < T4; ++c4) {
-        const float4 v = make_float4(x[4 * c4], x[4 * c4 + 1], x[4 * c4 + 2], x[4 * c4 + 3]);
-        xs[c4] = v;
-        xg[c4] = v;
-      }
-    }
-    __syncwarp();
-    stamp(ck1);
-    // (c) trailing update in 4 x 4 tiles over block pairs (kb, lb), 1 <= lb <= kb <= p
-    for (int t = lane; t < npairs * TB; t += 32) {
-      const int pr = t / TB, tt = t % TB;
-      const int kb = pairs[2 * pr], lb = pairs[2 * pr + 1];
-      const int tr = tt / T4, tc = tt % T4;
-      float *dst = slot(wrap(s0 + kb), wrap(s0 + lb)) + (4 * tr) * M + 4 * tc;
-      const float *xa = Xs + ((kb - 1) * M + 4 * tr) * M;
-      const float *xb = Xs + ((lb - 1) * M + 4 * tc) * M;
-      float acc[4][4];
-#pragma unroll
-      for (int a = 0; a < 4; ++a) {
-        const float4 d = *reinterpret_cast<const float4 *>(dst + a * M);
-        acc[a][0] = d.x;
-        acc[a][1] = d.y;
-        acc[a][2] = d.z;
-        acc[a][3] = d.w;
-      }
-#pragma unroll
-      for (int s4 = 0; s4 < T4; ++s4) {
-        float4 va[4], vb[4];
-#pragma unroll
-        for (int a = 0; a < 4; ++a) {
-          va[a] = *reinterpret_cast<const float4 *>(xa + a * M + 4 * s4);
-          vb[a] = *reinterpret_cast<const float4 *>(xb + a * M + 4 * s4);
-        }
-#pragma unroll
-        for (int a = 0; a < 4; ++a)
-#pragma unroll
-          for (int bq = 0; bq < 4; ++bq)
-            acc[a][bq] -= va[a].x * vb[bq].x + va[a].y * vb[bq].y + va[a].z * vb[bq].z + va[a].w * vb[bq].w;
-      }
-#pragma unroll
-      for (int a = 0; a < 4; ++a)
-        *reinterpret_cast<float4 *>(dst + a * M) = make_float4(acc[a][0], acc[a][1], acc[a][2], acc[a][3]);
-    }
-    // block row i+1+p takes the slots of row i: slot row s0, slot columns s0+1+l
-#pragma unroll
-    for (int l = 0; l < 8; ++l)
-      if (l < nb) {
-        float *dst = slot(s0, wrap(s0 + 1 + l));
-#pragma unroll
-        for (int u = 0; u < PE; ++u) {
-          const int e = lane + u * 32;
-          if (e < BS) dst[e] = pre[l][u];
-        }
-      }
-    __syncwarp();
-    stamp(ck2);
-  }
-  if (prof) {
-    phase_clk[0] = ck0;
-    phase_clk[1] = ck1;
-    phase_clk[2] = ck2;
+    (coup ? C : D)[u] = v;
   }
 }
 
-// Per block row: Linv = L_ii^{-1}, G_k = L_ii^{-1} L(i, i-k), H_k = L_ii^{-T} L(i+k, i)^T
-// for k = 1..p, rows padded to the stride S with zeros.  256 / M^2 block rows per
-// CTA, one thread per (row, entry) of a block.
-template <int M>
-__global__ void __launch_bounds__(256) k_bb_post(const float *__restrict__ Ld, const float *__restrict__ Lx, int n,
-                                                  int p, float *__restrict__ Linv, float *__restrict__ G,
-                                                  float *__restrict__ H) {
-  constexpr int BS = M * M, RP = 256 / BS, S = bb_stride(M), M1 = M + 1;
-  __shared__ float Lsh[RP][BS], Li[RP][M * M1], X[RP][M * M1];
-  const int g = threadIdx.x / BS, lt = threadIdx.x % BS, e = lt / M, f = lt % M;
-  const int i = blockIdx.x * RP + g;
-  const bool live = i < n;
-  Lsh[g][lt] = live ? Ld[(long long)i * BS + lt] : (e == f ? 1.f : 0.f);
-  __syncthreads();
-  if (lt < M) {
-    // column col of L^{-1}: forward substitution against the unit vector
-    const int col = lt;
-    float v[M];
-#pragma unroll
-    for (int r = 0; r < M; ++r) {
-      float sv = (r == col) ? 1.f : 0.f;
-#pragma unroll
-      for (int q = 0; q < r; ++q) sv -= (q >= col) ? Lsh[g][r * M + q] * v[q] : 0.f;
-      v[r] = (r >= col) ? sv / Lsh[g][r * (M + 1)] : 0.f;
+// O = alpha op(A) op(B) for q x q shared-memory matrices (leading dimension ld); O has
+// leading dimension ldo and may be global.
+__device__ __forceinline__ void bcr_mm(const float *A, bool ta, const float *B, bool tb, float *O, int ldo, int q,
+                                       int ld, float alpha) {
+  for (int e = threadIdx.x; e < q * q; e += blockDim.x) {
+    const int r = e / q, c = e % q;
+    float s0 = 0.f, s1 = 0.f;
+    int k = 0;
+    for (; k + 1 < q; k += 2) {
+      s0 += (ta ? A[k * ld + r] : A[r * ld + k]) * (tb ? B[c * ld + k] : B[k * ld + c]);
+      s1 += (ta ? A[(k + 1) * ld + r] : A[r * ld + k + 1]) * (tb ? B[c * ld + k + 1] : B[(k + 1) * ld + c]);
     }
-#pragma unroll
-    for (int r = 0; r < M; ++r) Li[g][r * M1 + col] = v[r];
+    if (k < q) s0 += (ta ? A[k * ld + r] : A[r * ld + k]) * (tb ? B[c * ld + k] : B[k * ld + c]);
+    O[(long long)r * ldo + c] = alpha * (s0 + s1);
+  }
+}
+
+// Elimination of the super-rows that are odd multiples of h (j = h + 2 h blockIdx.x), one
+// CTA each, or of the top row 0 (root): Cholesky of D_j (a pivot that cancellation drives
+// below 1e-6 of the diagonal entry is replaced by that entry: the factor stays SPD and PCG
+// checks convergence), Linv_j = L_j^{-1}, Ul_j = Linv_j C_j, Ur_j = Linv_j C_{j+h}^T, and the
+// Schur terms SL_j = Ul_j^T Ul_j, SR_j = Ur_j^T Ur_j, CN_j = -Ur_j^T Ul_j for the update.
+__global__ void __launch_bounds__(256) k_bcr_elim(const float *__restrict__ D, const float *__restrict__ C, int S,
+                                                  int q, int h, int root, float *__restrict__ Linv,
+                                                  float *__restrict__ Ul, float *__restrict__ Ur, float *__restrict__ SL,
+                                                  float *__restrict__ SR, float *__restrict__ CN) {
+  extern __shared__ float bsm[];
+  const int ld = q + 1;
+  float *Lm = bsm;            // D_j, factored in place (lower triangle)
+  float *Li = Lm + q * ld;    // L_j^{-1}
+  float *Cl = Li + q * ld;    // C_j: rows of j, columns of j - h
+  float *Cr = Cl + q * ld;    // C_{j+h}^T: rows of j, columns of j + h
+  float *Wl = Cr + q * ld;    // Ul_j
+  float *Wr = Wl + q * ld;    // Ur_j
+  float *diag0 = Wr + q * ld;
+  __shared__ float inv_s;
+  const int j = root ? 0 : h + 2 * h * (int)blockIdx.x;
+  const bool hasl = !root, hasr = !root && j + h < S;
+  const long long per = (long long)q * q;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  for (int e = tid; e < q * q; e += nt) {
+    const int r = e / q, c = e % q;
+    Lm[r * ld + c] = D[j * per + e];
+    Cl[r * ld + c] = hasl ? C[j * per + e] : 0.f;
+    Cr[c * ld + r] = hasr ? C[(j + h) * per + e] : 0.f;
   }
   __syncthreads();
-  if (live) Linv[(long long)i * BS + lt] = Li[g][e * M1 + f];
-  for (int k = 1; k <= p; ++k) {
-    const long long orow = (((long long)i * p + (k - 1)) * M + e) * S;
-    X[g][e * M1 + f] = (live && i - k >= 0) ? Lx[((long long)(i - k) * p + (k - 1)) * BS + e * M + f] : 0.f;
-    __syncthreads();
-    float acc = 0.f;
-#pragma unroll
-    for (int s = 0; s < M; ++s) acc += Li[g][e * M1 + s] * X[g][s * M1 + f];
-    if (live) {
-      G[orow + f] = acc;
-      if (f < S - M) G[orow + M + f] = 0.f;
+  for (int r = tid; r < q; r += nt) diag0[r] = Lm[r * ld + r];
+  __syncthreads();
+  for (int c = 0; c < q; ++c) {
+    if (tid == 0) {
+      float piv = Lm[c * ld + c];
+      const float d0 = diag0[c];
+      if (!(piv > 1e-6f * d0)) piv = (d0 > 0.f) ? d0 : 1.f;
+      const float l = sqrtf(piv);
+      Lm[c * ld + c] = l;
+      inv_s = 1.f / l;
     }
     __syncthreads();
-    X[g][e * M1 + f] = (live && i + k < n) ? Lx[((long long)i * p + (k - 1)) * BS + e * M + f] : 0.f;
+    const float inv = inv_s;
+    for (int r = c + 1 + tid; r < q; r += nt) Lm[r * ld + c] *= inv;
     __syncthreads();
-    acc = 0.f;
-#pragma unroll
-    for (int s = 0; s < M; ++s) acc += Li[g][s * M1 + e] * X[g][f * M1 + s];
-    if (live) {
-      H[orow + f] = acc;
-      if (f < S - M) H[orow + M + f] = 0.f;
+    const int w = q - c - 1;
+    for (int e = tid; e < w * w; e += nt) {
+      const int r = c + 1 + e / w, cc = c + 1 + e % w;
+      if (cc <= r) Lm[r * ld + cc] -= Lm[r * ld + c] * Lm[cc * ld + c];
     }
     __syncthreads();
   }
+  // L^{-1}: forward substitution against each unit vector, a thread per column
+  for (int col = tid; col < q; col += nt)
+    for (int r = 0; r < q; ++r) {
+      float v = 0.f;
+      if (r >= col) {
+        float sv = (r == col) ? 1.f : 0.f;
+        for (int k = col; k < r; ++k) sv -= Lm[r * ld + k] * Li[k * ld + col];
+        v = sv / Lm[r * ld + r];
+      }
+      Li[r * ld + col] = v;
+    }
+  __syncthreads();
+  for (int e = tid; e < q * q; e += nt) Linv[j * per + e] = Li[(e / q) * ld + e % q];
+  if (root) return;
+  bcr_mm(Li, false, Cl, false, Wl, ld, q, ld, 1.f);
+  bcr_mm(Li, false, Cr, false, Wr, ld, q, ld, 1.f);
+  __syncthreads();
+  for (int e = tid; e < q * q; e += nt) {
+    Ul[j * per + e] = Wl[(e / q) * ld + e % q];
+    Ur[j * per + e] = Wr[(e / q) * ld + e % q];
+  }
+  bcr_mm(Wl, true, Wl, false, SL + j * per, q, q, ld, 1.f);
+  bcr_mm(Wr, true, Wr, false, SR + j * per, q, q, ld, 1.f);
+  bcr_mm(Wr, true, Wl, false, CN + j * per, q, q, ld, -1.f);
 }
 
-constexpr size_t kFactorSmemMax = 200 * 1024;
-
-size_t factor_smem(int M, int p) {
-  const size_t nb = (size_t)p + 1, BS = (size_t)M * M;
-  return (nb * nb * BS + (size_t)p * M * M) * sizeof(float) + 2 * 28 * sizeof(int);
+// Rows active at the next level (J = 2 h t): D_J -= SR_{J-h} + SL_{J+h}, and C_J becomes
+// CN_{J-h}, the coupling of J with J - 2 h through the eliminated row between them.
+__global__ void k_bcr_update(float *__restrict__ D, float *__restrict__ C, const float *__restrict__ SL,
+                             const float *__restrict__ SR, const float *__restrict__ CN, int S, int q, int h) {
+  const long long per = (long long)q * q;
+  const long long na = (S + 2LL * h - 1) / (2LL * h);
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < na * per;
+       t += (long long)gridDim.x * blockDim.x) {
+    const long long J = 2LL * h * (t / per), e = t % per;
+    float d = D[J * per + e];
+    if (J >= h) d -= SR[(J - h) * per + e];
+    if (J + h < S) d -= SL[(J + h) * per + e];
+    D[J * per + e] = d;
+    if (J >= 2LL * h) C[J * per + e] = CN[(J - h) * per + e];
+  }
 }
+
+constexpr size_t kBcrSmemMax = 100 * 1024;
+
+size_t bcr_smem(int q) { return ((size_t)6 * q * (q + 1) + q) * sizeof(float); }
 
 template <int M>
-void build_m(Ctx *c, const double *PhiL, int rl, const BandCore &A, const double *PhiR, int rr, BBPrec &P,
-             unsigned long long *phase_clk) {
-  const int n = A.n, p = A.p, m = rl * rr;
-  constexpr int BS = M * M, S = bb_stride(M), RP = 256 / BS;
+void build_m(Ctx *c, const double *PhiL, int rl, const BandCore &A, const double *PhiR, int rr, BBPrec &P) {
+  const int n = A.n, p = A.p;
+  constexpr int BS = M * M;
   DBuf Blow(c, (size_t)n * (p + 1) * BS * sizeof(float));
   {
     const long long tot = (long long)n * (p + 1) * BS;
@@ -317,19 +200,33 @@ void build_m(Ctx *c, const double *PhiL, int rl, const BandCore &A, const double
                                                            Blow.as<float>());
     TTI_LAUNCH();
   }
-  DBuf Ld(c, (size_t)n * BS * sizeof(float)), Lx(c, (size_t)n * p * BS * sizeof(float));
-  {
-    const size_t smem = factor_smem(M, p);
-    TTI_CUDA(cudaFuncSetAttribute(k_bb_factor<M>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFactorSmemMax));
-    ProfScope ps(c, PROF_PRECOND, 0.0);
-    k_bb_factor<M><<<1, 32, smem, c->stream>>>(Blow.as<float>(), n, p, m, Ld.as<float>(), Lx.as<float>(), phase_clk);
+  const int q = P.q, S = P.S;
+  const size_t mat = (size_t)S * q * q * sizeof(float);
+  DBuf D(c, mat), C(c, mat), SL(c, mat), SR(c, mat), CN(c, mat);
+  P.Linv = DBuf(c, mat);
+  P.Ul = DBuf(c, mat);
+  P.Ur = DBuf(c, mat);
+  k_bcr_init<<<grid1d(2LL * S * q * q, 256), 256, 0, c->stream>>>(Blow.as<float>(), n, p, M, S, q, D.as<float>(),
+                                                                  C.as<float>());
+  TTI_LAUNCH();
+  set_smem_limit_once((const void *)k_bcr_elim, (int)kBcrSmemMax);
+  const size_t smem = bcr_smem(q);
+  ProfScope ps(c, PROF_PRECOND, 0.0);
+  P.levels = 0;
+  for (int h = 1; h < S; h <<= 1, ++P.levels) {
+    const int ne = (S - h + 2 * h - 1) / (2 * h);
+    k_bcr_elim<<<ne, 256, smem, c->stream>>>(D.as<float>(), C.as<float>(), S, q, h, 0, P.Linv.as<float>(),
+                                             P.Ul.as<float>(), P.Ur.as<float>(), SL.as<float>(), SR.as<float>(),
+                                             CN.as<float>());
+    TTI_LAUNCH();
+    const long long na = (S + 2LL * h - 1) / (2LL * h);
+    k_bcr_update<<<grid1d(na * q * q, 256), 256, 0, c->stream>>>(D.as<float>(), C.as<float>(), SL.as<float>(),
+                                                                 SR.as<float>(), CN.as<float>(), S, q, h);
     TTI_LAUNCH();
   }
-  P.Linv = DBuf(c, (size_t)n * BS * sizeof(float));
-  P.G = DBuf(c, (size_t)n * p * M * S * sizeof(float));
-  P.H = DBuf(c, (size_t)n * p * M * S * sizeof(float));
-  k_bb_post<M><<<(n + RP - 1) / RP, 256, 0, c->stream>>>(Ld.as<float>(), Lx.as<float>(), n, p, P.Linv.as<float>(),
-                                                         P.G.as<float>(), P.H.as<float>());
+  k_bcr_elim<<<1, 256, smem, c->stream>>>(D.as<float>(), C.as<float>(), S, q, 0, 1, P.Linv.as<float>(),
+                                          P.Ul.as<float>(), P.Ur.as<float>(), SL.as<float>(), SR.as<float>(),
+                                          CN.as<float>());
   TTI_LAUNCH();
 }
 
@@ -337,19 +234,20 @@ void build_m(Ctx *c, const double *PhiL, int rl, const BandCore &A, const double
 
 bool bb_eligible(int m, int n, int p) {
   return m >= 1 && m <= kBBMaxM && n >= 1 && n <= 1024 && p >= 1 && p <= 7 &&
-         factor_smem(bb_pad(m), p) <= kFactorSmemMax;
+         bcr_smem(p * bb_pad(m)) <= kBcrSmemMax;
 }
 
-void bb_prec_build(Ctx *c, const double *PhiL, int rl, const BandCore &A, const double *PhiR, int rr, BBPrec &P,
-                   unsigned long long *phase_clk) {
+void bb_prec_build(Ctx *c, const double *PhiL, int rl, const BandCore &A, const double *PhiR, int rr, BBPrec &P) {
   const int m = rl * rr;
   TTI_CHECK_ARG(bb_eligible(m, A.n, A.p), "block-band preconditioner: m=%d n=%d p=%d out of range", m, A.n, A.p);
   P.n = A.n;
   P.p = A.p;
   P.m = m;
   P.M = bb_pad(m);
-  if (P.M == 4) build_m<4>(c, PhiL, rl, A, PhiR, rr, P, phase_clk);
-  else build_m<8>(c, PhiL, rl, A, PhiR, rr, P, phase_clk);
+  P.q = A.p * P.M;
+  P.S = (A.n + A.p - 1) / A.p;
+  if (P.M == 4) build_m<4>(c, PhiL, rl, A, PhiR, rr, P);
+  else build_m<8>(c, PhiL, rl, A, PhiR, rr, P);
 }
 
 }  // namespace ttiga

@@ -337,40 +337,6 @@ __device__ __forceinline__ void band_systems(const PcgArgs<T> &a, const T *__res
 
 // ---- block-band preconditioner (small interface blocks, CTA 0 only)
 
-__device__ __forceinline__ unsigned smem_u32(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ void mbar_init(unsigned long long *bar) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(bar)) : "memory");
-}
-__device__ __forceinline__ void mbar_inval(unsigned long long *bar) {
-  asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(smem_u32(bar)) : "memory");
-}
-// One bulk copy global -> shared of `bytes` (multiple of 16, both addresses
-// 16-byte aligned) completing on `bar`, after the arrival that expects it.
-__device__ __forceinline__ void bulk_load(void *dst, const void *src, unsigned bytes, unsigned long long *bar) {
-  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
-  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                   smem_u32(dst)),
-               "l"(src), "r"(bytes), "r"(smem_u32(bar))
-               : "memory");
-}
-// Wait for the phase of `bar` with the given parity to complete; false when the
-// poll limit runs out.
-__device__ __forceinline__ bool mbar_wait(unsigned long long *bar, unsigned parity) {
-  const unsigned addr = smem_u32(bar);
-  for (long long spin = 0; spin < kSpinLimit; ++spin) {
-    unsigned done;
-    asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
-        : "=r"(done)
-        : "r"(addr), "r"(parity)
-        : "memory");
-    if (done) return true;
-  }
-  return false;
-}
-
 // Sub-phase timestamp of the block-band apply (init call only, verbose trace).
 __device__ __forceinline__ void bb_mark(unsigned long long *trace, int cap, bool on, int k) {
   if (on && trace && threadIdx.x == 0 && cap >= 2 + 2 * 128 + 8) {
@@ -380,156 +346,83 @@ __device__ __forceinline__ void bb_mark(unsigned long long *trace, int cap, bool
   }
 }
 
-// Chunk sequence of one block-band apply: chunks 0..nch-1 hold the forward
-// blocks G (block rows ascending), chunks nch..2nch-1 the backward blocks H
-// (block rows descending), each `ch` block rows of PB blocks [M][S].  Chunk q
-// goes to staging buffer q & 1 and completes on barrier q & 1; ph carries the
-// two barriers' phase parities across applies.
-struct BBStream {
-  const float *G, *H;
-  int n, ch, nch;
-  float *st0, *st1;
-  unsigned long long *bars;
-  unsigned ph;
+// Products of one warp with the Q x Q matrices of the odd-even reduction (row-major,
+// global memory, written by the preconditioner build) and vectors in shared memory:
+// lane t owns output entries t and t + 32.
+template <int Q> struct BcrOut {
+  float v[(Q + 31) / 32];
 };
 
-__device__ __forceinline__ void bb_rows(const BBStream &s, int q, int &lo, int &hi) {
-  if (q < s.nch) {
-    lo = q * s.ch;
-    hi = min(s.n, lo + s.ch);
-  } else {
-    hi = s.n - (q - s.nch) * s.ch;
-    lo = max(0, hi - s.ch);
+// o_t += sum_c A[t][c] x[c]
+template <int Q> __device__ __forceinline__ void bcr_mv(const float *__restrict__ A, const float *x, BcrOut<Q> &o) {
+  const int lane = threadIdx.x & 31;
+  const float4 *x4 = reinterpret_cast<const float4 *>(x);
+#pragma unroll
+  for (int u = 0; u < (Q + 31) / 32; ++u) {
+    const int t = lane + 32 * u;
+    if (t >= Q) continue;
+    const float4 *a4 = reinterpret_cast<const float4 *>(A + t * Q);
+    float s0 = 0.f, s1 = 0.f;
+#pragma unroll
+    for (int c4 = 0; c4 < Q / 4; ++c4) {
+      const float4 av = __ldg(a4 + c4), w = x4[c4];
+      s0 += av.x * w.x + av.z * w.z;
+      s1 += av.y * w.y + av.w * w.w;
+    }
+    o.v[u] += s0 + s1;
   }
 }
 
-// Issue chunk q (one thread).  Its buffer was last read two chunks earlier.
-template <int PB, int M> __device__ __forceinline__ void bb_issue(const BBStream &s, int q) {
-  constexpr int RF = PB * M * bb_stride(M);  // floats per block row
-  int lo, hi;
-  bb_rows(s, q, lo, hi);
-  const float *base = (q < s.nch) ? s.G : s.H;
-  bulk_load((q & 1) ? s.st1 : s.st0, base + (long long)lo * RF, (unsigned)(hi - lo) * RF * sizeof(float),
-            s.bars + (q & 1));
+// o_t += sum_c A[c][t] x[c]
+template <int Q> __device__ __forceinline__ void bcr_mvt(const float *__restrict__ A, const float *x, BcrOut<Q> &o) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int u = 0; u < (Q + 31) / 32; ++u) {
+    const int t = lane + 32 * u;
+    if (t >= Q) continue;
+    float s0 = 0.f, s1 = 0.f;
+#pragma unroll 8
+    for (int c = 0; c < Q; c += 2) {
+      s0 += __ldg(A + c * Q + t) * x[c];
+      s1 += __ldg(A + (c + 1) * Q + t) * x[c + 1];
+    }
+    o.v[u] += s0 + s1;
+  }
 }
 
-// k >= 2 terms of row i: sum_{k=2..PB} M_ik v_{i-+k} for lane e's row.  Mi is
-// that row in block 1 of row i.  Rows outside 0..n-1 are clamped: their blocks
-// are zero, so the loads need no branch.
-template <int PB, int M>
-__device__ __forceinline__ float bb_far(const float *Mi, const float *v, int i, int n, bool fwd) {
-  constexpr int S = bb_stride(M);
-  float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
+template <int Q> __device__ __forceinline__ void bcr_store(float *dst, const BcrOut<Q> &o) {
+  const int lane = threadIdx.x & 31;
 #pragma unroll
-  for (int k = 2; k <= PB; ++k) {
-    const int j = min(max(fwd ? i - k : i + k, 0), n - 1);
-    const float4 *mk = reinterpret_cast<const float4 *>(Mi + (k - 1) * M * S);
-    const float4 *vj = reinterpret_cast<const float4 *>(v + j * M);
-#pragma unroll
-    for (int f4 = 0; f4 < M / 4; ++f4) {
-      const float4 g = mk[f4], w = vj[f4];
-      a0 += g.x * w.x;
-      a1 += g.y * w.y;
-      a2 += g.z * w.z;
-      a3 += g.w * w.w;
-    }
-  }
-  return (a0 + a1) + (a2 + a3);
-}
-
-// Block substitution run by warp 0 over the chunks of one pass: for each block
-// row i (ascending when fwd, else descending), v_i -= sum_{k=1..PB} M_ik v_{i-+k}.
-// Lane e (< M) owns entry e of the row (the other lanes mirror them and do not
-// store).  Only the k = 1 term depends on the row finished in the previous
-// step: the k >= 2 terms and the next row's k = 1 block row are loaded and
-// summed before the warp synchronises, so the dependent path of a step is one
-// read of the previous row, M FMAs in four chains and a store.
-template <int PB, int M> __device__ bool bb_chain(float *v, BBStream &s, bool fwd) {
-  constexpr int S = bb_stride(M), RF = PB * M * S;
-  const int lane = threadIdx.x & 31, e = lane % M;
-  const int q0 = fwd ? 0 : s.nch;
-  const int n = s.n;
-  for (int c = 0; c < s.nch; ++c) {
-    const int q = q0 + c;
-    if (lane == 0 && q + 1 < 2 * s.nch) bb_issue<PB, M>(s, q + 1);
-    const int bsel = q & 1;
-    // warp-uniform outcome: every lane polls, all lanes take the same branch
-    if (!__all_sync(0xffffffffu, mbar_wait(s.bars + bsel, (s.ph >> bsel) & 1u))) {
-      // give the copies in flight one more bounded wait before giving up
-      mbar_wait(s.bars + bsel, (s.ph >> bsel) & 1u);
-      if (q + 1 < 2 * s.nch) mbar_wait(s.bars + (bsel ^ 1), (s.ph >> (bsel ^ 1)) & 1u);
-      return false;
-    }
-    s.ph ^= 1u << bsel;
-    const float *Ms = bsel ? s.st1 : s.st0;
-    int lo, hi;
-    bb_rows(s, q, lo, hi);
-    const int rows = hi - lo;
-    auto row_i = [&](int t) { return fwd ? lo + t : hi - 1 - t; };
-    int i = row_i(0);
-    const float *Mi = Ms + (i - lo) * RF + e * S;
-    float far = bb_far<PB, M>(Mi, v, i, n, fwd);
-    float4 g1[M / 4];
-#pragma unroll
-    for (int f4 = 0; f4 < M / 4; ++f4) g1[f4] = reinterpret_cast<const float4 *>(Mi)[f4];
-    float self = v[i * M + e];
-    for (int t = 0; t < rows; ++t) {
-      const int j1 = min(max(fwd ? i - 1 : i + 1, 0), n - 1);
-      const float4 *vj = reinterpret_cast<const float4 *>(v + j1 * M);
-      float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
-#pragma unroll
-      for (int f4 = 0; f4 < M / 4; ++f4) {
-        const float4 w = vj[f4];
-        a0 += g1[f4].x * w.x;
-        a1 += g1[f4].y * w.y;
-        a2 += g1[f4].z * w.z;
-        a3 += g1[f4].w * w.w;
-      }
-      const float y = self - (far + ((a0 + a1) + (a2 + a3)));
-      if (lane < M) v[i * M + e] = y;
-      if (t + 1 < rows) {
-        // next row: its k >= 2 rows and its own entry are final already
-        i = row_i(t + 1);
-        Mi = Ms + (i - lo) * RF + e * S;
-        far = bb_far<PB, M>(Mi, v, i, n, fwd);
-#pragma unroll
-        for (int f4 = 0; f4 < M / 4; ++f4) g1[f4] = reinterpret_cast<const float4 *>(Mi)[f4];
-        self = v[i * M + e];
-      }
-      __syncwarp();
-    }
-  }
-  return true;
+  for (int u = 0; u < (Q + 31) / 32; ++u)
+    if (lane + 32 * u < Q) dst[lane + 32 * u] = o.v[u];
 }
 
 // E phase with the block-band preconditioner, run by CTA 0 alone (the other
 // CTAs contribute zero partials): x += alpha p, r -= alpha q (or x = 0, r = b),
-// then z = L^{-T} L^{-1} r by the two block substitutions; <r, r>, <r, z>.
-// Shared layout: rs[n][M], ys[n][M], two staging buffers of bb_ch block rows.
+// then z = B^{-1} r by the forward and backward passes of the odd-even reduction
+// (levels of independent super-rows, one warp per super-row, a CTA barrier per
+// phase); <r, r>, <r, z>.  When <r, r> already meets the tolerance the solve is
+// skipped: the iteration stops after the barrier and never reads z (the exact
+// block-band preconditioner of an edge core often converges in one iteration,
+// whose second application would otherwise be half the launch).
+// Shared layout: rs[S][Q] (b, then z), ys[S][Q] (y), a Q-entry scratch per warp;
+// super-row J entry a M + e is block row p J + a, entry e, so rs is the [n][M]
+// vector padded with zeros to S p block rows.
 // The element loops load a batch of kU entries per thread before computing, so
 // a thread waits for one memory latency per batch rather than per entry.
 constexpr int kU = 4;
 
 template <typename T, int PB, int M>
-__device__ bool bb_apply(const PcgArgs<T> &a, const T *__restrict__ pcur, double alpha, bool init, double &rr_out,
-                         double &rz_out, unsigned long long *bars, unsigned &ph) {
-  constexpr int S = bb_stride(M);
+__device__ void bb_apply(const PcgArgs<T> &a, const T *__restrict__ pcur, double alpha, bool init, double &rr_out,
+                         double &rz_out) {
+  constexpr int Q = PB * M;
+  constexpr long long QQ = (long long)Q * Q;
   bb_mark(a.trace, a.trace_cap, init, 0);
   extern __shared__ float4 esm4[];
-  const int n = a.n, rr = a.rr, m = a.rl * a.rr, tot = n * M, B = blockDim.x;
+  const int n = a.n, rr = a.rr, m = a.rl * a.rr, S = a.bbS, tot = n * M, totp = S * Q, B = blockDim.x;
   float *rs = reinterpret_cast<float *>(esm4);
-  float *ys = rs + n * M;
-  BBStream s;
-  s.G = a.bbG;
-  s.H = a.bbH;
-  s.n = n;
-  s.ch = a.bb_ch;
-  s.nch = (n + a.bb_ch - 1) / a.bb_ch;
-  s.st0 = ys + n * M;
-  s.st1 = s.st0 + a.bb_ch * PB * M * S;
-  s.bars = bars;
-  s.ph = ph;
-  if (threadIdx.x == 0) bb_issue<PB, M>(s, 0);  // lands while the element loops run
+  float *ys = rs + totp;
+  float *ws = ys + totp;
   auto index_of = [&](int e) { return ((long long)((e % M) / rr) * n + e / M) * rr + ((e % M) % rr); };
   double rr_th = 0.0;
   for (int e0 = threadIdx.x; e0 < tot; e0 += kU * B) {
@@ -572,75 +465,91 @@ __device__ bool bb_apply(const PcgArgs<T> &a, const T *__restrict__ pcur, double
       rs[e] = rv;
     }
   }
+  for (int e = tot + threadIdx.x; e < totp; e += B) rs[e] = 0.f;
   rr_out += rr_th;
-  __syncthreads();
-  bb_mark(a.trace, a.trace_cap, init, 1);
-  // s_i = L_ii^{-1} r_i
-  for (int e0 = threadIdx.x; e0 < tot; e0 += kU * B) {
-    float4 l4[kU][M / 4];
-#pragma unroll
-    for (int u = 0; u < kU; ++u) {
-      const int e = min(e0 + u * B, tot - 1);
-      const float4 *Li = reinterpret_cast<const float4 *>(a.bbLinv + (long long)(e / M) * M * M + (e % M) * M);
-#pragma unroll
-      for (int f = 0; f < M / 4; ++f) l4[u][f] = Li[f];
+  // <r, r> over the CTA, formed exactly as the caller's partial (CTA 0 owns every entry and the
+  // other partials are zero, so this is the value of the stop test)
+  {
+    __shared__ double red[32];
+    __shared__ int done;
+    double v = rr_out;
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double t = 0.0;
+      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+      done = !(t > a.tol2);
     }
-#pragma unroll
-    for (int u = 0; u < kU; ++u) {
-      const int e = e0 + u * B;
-      if (e >= tot) continue;
-      const float4 *ri = reinterpret_cast<const float4 *>(rs + (e / M) * M);
-      float s0 = 0.f, s1 = 0.f;
-#pragma unroll
-      for (int f = 0; f < M / 4; ++f) {
-        const float4 r4 = ri[f];
-        s0 += l4[u][f].x * r4.x + l4[u][f].z * r4.z;
-        s1 += l4[u][f].y * r4.y + l4[u][f].w * r4.w;
-      }
-      ys[e] = s0 + s1;
+    __syncthreads();
+    if (done) {
+      bb_mark(a.trace, a.trace_cap, init, 6);
+      return;
     }
   }
-  __syncthreads();
-  __shared__ int chain_ok;
+  bb_mark(a.trace, a.trace_cap, init, 1);
+  const int warp = threadIdx.x >> 5, nw = B >> 5;
+  const float *Li = a.bbLinv, *Ul = a.bbUl, *Ur = a.bbUr;
+  // forward: y_j = Linv_j b_j for the rows eliminated at level h, then the rows left take
+  // b_J -= Ur_{J-h}^T y_{J-h} + Ul_{J+h}^T y_{J+h}
+  int hmax = 0;
+  for (int h = 1; h < S; h <<= 1) {
+    hmax = h;
+    const int ne = (S - h + 2 * h - 1) / (2 * h), na = (S + 2 * h - 1) / (2 * h);
+    for (int t = warp; t < ne; t += nw) {
+      const int j = h + 2 * h * t;
+      BcrOut<Q> o = {};
+      bcr_mv<Q>(Li + j * QQ, rs + j * Q, o);
+      bcr_store<Q>(ys + j * Q, o);
+    }
+    __syncthreads();
+    for (int t = warp; t < na; t += nw) {
+      const int J = 2 * h * t;
+      BcrOut<Q> o = {};
+      if (J >= h) bcr_mvt<Q>(Ur + (J - h) * QQ, ys + (J - h) * Q, o);
+      if (J + h < S) bcr_mvt<Q>(Ul + (J + h) * QQ, ys + (J + h) * Q, o);
+      const int lane = threadIdx.x & 31;
+#pragma unroll
+      for (int u = 0; u < (Q + 31) / 32; ++u)
+        if (lane + 32 * u < Q) rs[J * Q + lane + 32 * u] -= o.v[u];
+    }
+    __syncthreads();
+  }
   bb_mark(a.trace, a.trace_cap, init, 2);
-  if (threadIdx.x < 32) {
-    const bool ok = bb_chain<PB, M>(ys, s, true);
-    if (threadIdx.x == 0) chain_ok = ok;
+  // top row: y_0 = Linv_0 b_0, z_0 = Linv_0^T y_0
+  if (warp == 0) {
+    BcrOut<Q> o = {};
+    bcr_mv<Q>(Li, rs, o);
+    bcr_store<Q>(ys, o);
+    __syncwarp();
+    BcrOut<Q> z = {};
+    bcr_mvt<Q>(Li, ys, z);
+    bcr_store<Q>(rs, z);
   }
   __syncthreads();
   bb_mark(a.trace, a.trace_cap, init, 3);
-  // t_i = L_ii^{-T} y_i
-  for (int e0 = threadIdx.x; e0 < tot; e0 += kU * B) {
-    float lc[kU][M];
+  // backward: z_j = Linv_j^T (y_j - Ul_j z_{j-h} - Ur_j z_{j+h}), levels top down
+  for (int h = hmax; h >= 1; h >>= 1) {
+    const int ne = (S - h + 2 * h - 1) / (2 * h);
+    float *w = ws + warp * Q;
+    for (int t = warp; t < ne; t += nw) {
+      const int j = h + 2 * h * t;
+      BcrOut<Q> o = {};
+      bcr_mv<Q>(Ul + j * QQ, rs + (j - h) * Q, o);
+      if (j + h < S) bcr_mv<Q>(Ur + j * QQ, rs + (j + h) * Q, o);
+      const int lane = threadIdx.x & 31;
 #pragma unroll
-    for (int u = 0; u < kU; ++u) {
-      const int e = min(e0 + u * B, tot - 1);
-      const float *Li = a.bbLinv + (long long)(e / M) * M * M + (e % M);
-#pragma unroll
-      for (int f = 0; f < M; ++f) lc[u][f] = Li[f * M];
+      for (int u = 0; u < (Q + 31) / 32; ++u)
+        if (lane + 32 * u < Q) w[lane + 32 * u] = ys[j * Q + lane + 32 * u] - o.v[u];
+      __syncwarp();
+      BcrOut<Q> z = {};
+      bcr_mvt<Q>(Li + j * QQ, w, z);
+      bcr_store<Q>(rs + j * Q, z);
+      __syncwarp();
     }
-#pragma unroll
-    for (int u = 0; u < kU; ++u) {
-      const int e = e0 + u * B;
-      if (e >= tot) continue;
-      const float *yi = ys + (e / M) * M;
-      float s0 = 0.f, s1 = 0.f;
-#pragma unroll
-      for (int f = 0; f < M; f += 2) {
-        s0 += lc[u][f] * yi[f];
-        s1 += lc[u][f + 1] * yi[f + 1];
-      }
-      rs[e] = s0 + s1;
-    }
+    __syncthreads();
   }
-  __syncthreads();
   bb_mark(a.trace, a.trace_cap, init, 4);
-  if (threadIdx.x < 32 && chain_ok) {
-    const bool ok = bb_chain<PB, M>(rs, s, false);
-    if (threadIdx.x == 0) chain_ok = ok;
-  }
-  if (threadIdx.x < 32) ph = s.ph;  // every lane of warp 0 polls with these parities next time
-  __syncthreads();
   bb_mark(a.trace, a.trace_cap, init, 5);
   double rz_th = 0.0;
   for (int e0 = threadIdx.x; e0 < tot; e0 += kU * B) {
@@ -662,20 +571,17 @@ __device__ bool bb_apply(const PcgArgs<T> &a, const T *__restrict__ pcur, double
     }
   }
   rz_out += rz_th;
-  const bool ok = chain_ok != 0;
   __syncthreads();
   bb_mark(a.trace, a.trace_cap, init, 6);
-  if (!ok && threadIdx.x == 0) atomicExch(a.err, 2);
-  return ok;
 }
 
 // Block-band E phase for the block size of this system (CTA 0 only).
 template <typename T, int PB>
 __device__ __forceinline__ void bb_phase(const PcgArgs<T> &a, const T *pcur, double alpha, bool init, double &rr_out,
-                                         double &rz_out, unsigned long long *bars, unsigned &ph) {
+                                         double &rz_out) {
   if (blockIdx.x != 0) return;
-  if (a.bbM == 4) bb_apply<T, PB, 4>(a, pcur, alpha, init, rr_out, rz_out, bars, ph);
-  else bb_apply<T, PB, 8>(a, pcur, alpha, init, rr_out, rz_out, bars, ph);
+  if (a.bbM == 4) bb_apply<T, PB, 4>(a, pcur, alpha, init, rr_out, rz_out);
+  else bb_apply<T, PB, 8>(a, pcur, alpha, init, rr_out, rz_out);
 }
 
 template <typename T, int PB>
@@ -738,19 +644,9 @@ __global__ void __launch_bounds__(256, 1) k_pcg_fused(PcgArgs<T> a) {
     }
   }
   bool aborted = false;
-  __shared__ __align__(8) unsigned long long bb_bars[2];
-  unsigned bb_ph = 0;
-  if (a.edge && blockIdx.x == 0) {
-    if (threadIdx.x == 0) {
-      mbar_init(&bb_bars[0]);
-      mbar_init(&bb_bars[1]);
-      asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    }
-    __syncthreads();
-  }
   // r = b, x = 0, z = P^{-1} r;  <r, r>, <r, z>
   double rr_loc = 0.0, rz_loc = 0.0;
-  if (a.edge) bb_phase<T, PB>(a, nullptr, 0.0, true, rr_loc, rz_loc, bb_bars, bb_ph);
+  if (a.edge) bb_phase<T, PB>(a, nullptr, 0.0, true, rr_loc, rz_loc);
   else band_systems<T, PB>(a, nullptr, 0.0, true, rr_loc, rz_loc);
   cta_partial(rr_loc, p_rr);
   cta_partial(rz_loc, p_rz);
@@ -1043,7 +939,7 @@ __global__ void __launch_bounds__(256, 1) k_pcg_fused(PcgArgs<T> a) {
     const double alpha = rz / pq;
     rr_loc = 0.0;
     rz_loc = 0.0;
-    if (a.edge) bb_phase<T, PB>(a, pcur, alpha, false, rr_loc, rz_loc, bb_bars, bb_ph);
+    if (a.edge) bb_phase<T, PB>(a, pcur, alpha, false, rr_loc, rz_loc);
     else band_systems<T, PB>(a, pcur, alpha, false, rr_loc, rz_loc);
     cta_partial(rr_loc, p_rr);
     cta_partial(rz_loc, p_rz);
@@ -1060,10 +956,6 @@ __global__ void __launch_bounds__(256, 1) k_pcg_fused(PcgArgs<T> a) {
     if (!aborted) {
       a.out[0] = (double)it;
       a.out[1] = res2;
-    }
-    if (a.edge) {
-      mbar_inval(&bb_bars[0]);
-      mbar_inval(&bb_bars[1]);
     }
   }
   if constexpr (kTc) {
@@ -1104,14 +996,12 @@ template <typename T> int pcg_fused_grid(Ctx *c, PcgArgs<T> &a) {
   // Slabs of S mode rows for the dense phase (at least 256 band-stage outputs
   // each), enough CTAs for the slabs and for the band systems, all co-resident.
   const void *k = pick<T>(a.p);
+  // block-band preconditioner: rs, ys [S][q] and a q-entry scratch per warp (8 warps)
+  const size_t bb_vec = a.edge ? (2 * (size_t)a.bbS + 8) * a.p * a.bbM * sizeof(float) : 0;
   if (a.edge) {
-    // block-band preconditioner: rs, ys [n][16] and two staging buffers of bb_ch block rows
-    const size_t vec = 2 * (size_t)a.n * a.bbM * sizeof(float),
-                 row = (size_t)a.p * a.bbM * bb_stride(a.bbM) * sizeof(float);
-    TTI_CHECK_ARG(vec + 2 * row <= kPcgSmemBytes, "pcg: n=%d too large for the block-band preconditioner", a.n);
-    a.bb_ch = (int)std::min<size_t>(32, (kPcgSmemBytes - vec) / (2 * row));
+    TTI_CHECK_ARG(bb_vec <= kPcgSmemBytes, "pcg: n=%d too large for the block-band preconditioner", a.n);
     a.slots = 1;
-    a.smem = (int)(vec + 2 * (size_t)a.bb_ch * row);
+    a.smem = (int)bb_vec;
   } else {
     a.slots = band_slots(a);
     a.smem = (int)((size_t)a.slots * a.n * (a.p + 2) * sizeof(float));
@@ -1148,28 +1038,17 @@ template <typename T> int pcg_fused_grid(Ctx *c, PcgArgs<T> &a) {
   a.dense_stride = a.p_stride + a.t1_stride + a.t2_stride;
   a.phr_ld = a.rr | 1;
   // Shared memory after the preconditioner's area: the slab scratch of the dense phase
-  // (p, T1, T2), then the interfaces, each when it fits (the block-band staging gives
-  // up chunk rows for them, down to 8); otherwise the slab scratch is in global memory
+  // (p, T1, T2), then the interfaces, each when it fits; otherwise the slab scratch is in global memory
   // (one region per CTA) and the interfaces are read from global memory.  The grid
   // must stay co-resident.
   const size_t dense = (size_t)a.dense_stride * sizeof(T);
   const size_t iface = ((size_t)a.rr * a.Rr * a.phr_ld + (size_t)a.rl * a.Rl * a.rl) * sizeof(T);
   const size_t pre_smem = (size_t)a.smem;
-  const int pre_ch = a.bb_ch;
   auto place = [&](bool want_iface, size_t reserve) {  // reserve: bytes kept free after the slab scratch
     a.dense_off = -1;
     a.iface_off = -1;
     const size_t extra = dense + (want_iface ? iface : 0) + reserve;
-    if (a.edge) {
-      const size_t vec = 2 * (size_t)a.n * a.bbM * sizeof(float),
-                   row = (size_t)a.p * a.bbM * bb_stride(a.bbM) * sizeof(float);
-      const size_t base = (vec + 15) / 16 * 16;
-      if (base + extra + 16 + 2 * 8 * row > kPcgSmemBytes) return;
-      a.bb_ch = (int)std::min<size_t>(32, (kPcgSmemBytes - base - extra - 16) / (2 * row));
-      const size_t off = (vec + 2 * (size_t)a.bb_ch * row + 15) / 16 * 16;
-      a.dense_off = (int)off;
-      a.smem = (int)(off + dense);
-    } else {
+    {
       const size_t off = (pre_smem + 15) / 16 * 16;
       if (off + extra + 16 > kPcgSmemBytes) return;
       a.dense_off = (int)off;
@@ -1232,7 +1111,6 @@ template <typename T> int pcg_fused_grid(Ctx *c, PcgArgs<T> &a) {
     // the sizes chosen above, slab scratch in global memory, interfaces from global memory
     a.iface_off = -1;
     a.smem = (int)pre_smem;
-    a.bb_ch = pre_ch;
   }
   return (int)g;
 }

@@ -9,11 +9,10 @@ template <typename T> struct PcgArgs {
   const T *PhiR;  // [rr][Rr][rr]
   const T *A;     // [Rl][n][2p+1][Rr]
   const float *Lf;  // band Cholesky factors [n][p+1][rl*rr] (FP32; reciprocal diagonal in slot p)
-  // block-band preconditioner (edge != 0), block size bbM: L_ii^{-1} [n][M][M],
-  // G and H [n][p][M][bb_stride(M)] (FP32, see bbprec.cuh)
-  const float *bbLinv, *bbG, *bbH;
-  int edge, bbM;
-  int bb_ch;      // block rows per staged chunk of G / H (set by pcg_fused_grid)
+  // block-band preconditioner (edge != 0), block size bbM, bbS super-rows of q = p bbM:
+  // the odd-even reduction factors Linv, Ul, Ur [bbS][q][q] (FP32, see bbprec.cuh)
+  const float *bbLinv, *bbUl, *bbUr;
+  int edge, bbM, bbS;
   const T *b;     // right-hand side [rl][n][rr]
   T *x, *r, *z, *pv, *pv2, *q;  // solution and work vectors [rl][n][rr] (pv, pv2: p double buffer)
   // per-CTA slab scratch of the dense phase, grid x dense_stride, used when dense_off < 0:
