@@ -1,8 +1,7 @@
 // Exact block-band preconditioner of small-interface AMEn local systems:
 // assembly of the symmetric block band (FP64 contractions, FP32 result), then
 // the odd-even (cyclic) reduction of its block-tridiagonal super-row form, one
-// launch pair per level (eliminations, then the Schur updates of the rows
-// left), so the factorisation is log2 of the super-row count deep.
+// launch per level, so the factorisation is log2 of the super-row count deep.
 #include "bbprec.cuh"
 
 namespace ttiga {
@@ -73,121 +72,201 @@ __global__ void k_bcr_init(const float *__restrict__ Blow, int n, int p, int M, 
   }
 }
 
-// O = alpha op(A) op(B) for q x q shared-memory matrices (leading dimension ld); O has
+// O = alpha op(A) op(B) for Q x Q shared-memory matrices (leading dimension Q + 1); O has
 // leading dimension ldo and may be global.
-__device__ __forceinline__ void bcr_mm(const float *A, bool ta, const float *B, bool tb, float *O, int ldo, int q,
-                                       int ld, float alpha) {
-  for (int e = threadIdx.x; e < q * q; e += blockDim.x) {
-    const int r = e / q, c = e % q;
+template <int Q, bool TA, bool TB>
+__device__ __forceinline__ void bcr_mm(const float *A, const float *B, float *O, int ldo, float alpha) {
+  constexpr int LD = Q + 1;
+  for (int e = threadIdx.x; e < Q * Q; e += blockDim.x) {
+    const int r = e / Q, c = e % Q;
     float s0 = 0.f, s1 = 0.f;
-    int k = 0;
-    for (; k + 1 < q; k += 2) {
-      s0 += (ta ? A[k * ld + r] : A[r * ld + k]) * (tb ? B[c * ld + k] : B[k * ld + c]);
-      s1 += (ta ? A[(k + 1) * ld + r] : A[r * ld + k + 1]) * (tb ? B[c * ld + k + 1] : B[(k + 1) * ld + c]);
+#pragma unroll
+    for (int k = 0; k < Q; k += 2) {
+      s0 += (TA ? A[k * LD + r] : A[r * LD + k]) * (TB ? B[c * LD + k] : B[k * LD + c]);
+      s1 += (TA ? A[(k + 1) * LD + r] : A[r * LD + k + 1]) * (TB ? B[c * LD + k + 1] : B[(k + 1) * LD + c]);
     }
-    if (k < q) s0 += (ta ? A[k * ld + r] : A[r * ld + k]) * (tb ? B[c * ld + k] : B[k * ld + c]);
     O[(long long)r * ldo + c] = alpha * (s0 + s1);
   }
 }
 
 // Elimination of the super-rows that are odd multiples of h (j = h + 2 h blockIdx.x), one
-// CTA each, or of the top row 0 (root): Cholesky of D_j (a pivot that cancellation drives
-// below 1e-6 of the diagonal entry is replaced by that entry: the factor stays SPD and PCG
-// checks convergence), Linv_j = L_j^{-1}, Ul_j = Linv_j C_j, Ur_j = Linv_j C_{j+h}^T, and the
-// Schur terms SL_j = Ul_j^T Ul_j, SR_j = Ur_j^T Ur_j, CN_j = -Ur_j^T Ul_j for the update.
+// CTA each, or of the top row 0 (root, h = the first power of two >= S).  Row j first takes
+// the Schur terms of every lower level h2 < h, in level order: D_j -= SR_{j-h2} + SL_{j+h2},
+// and its couplings of this level, CN_{j-h/2} with j - h and CN_{j+h/2} with j + h (the
+// original C at level 0).  Then: Cholesky of D_j by one warp (a pivot that cancellation
+// drives below 1e-6 of the diagonal entry is replaced by that entry: the factor stays SPD
+// and PCG checks convergence), Linv_j = L_j^{-1} (a thread per column), Ul_j = Linv_j C_j,
+// Ur_j = Linv_j C_{j+h}^T, and the Schur terms SL_j = Ul_j^T Ul_j, SR_j = Ur_j^T Ur_j,
+// CN_j = -Ur_j^T Ul_j that the rows of later levels take.  Each row is eliminated once, so
+// the terms of all levels stay in SL, SR, CN.  Q = p M is a template parameter so that the
+// loops over a super-row unroll.
+template <int Q>
 __global__ void __launch_bounds__(256) k_bcr_elim(const float *__restrict__ D, const float *__restrict__ C, int S,
-                                                  int q, int h, int root, float *__restrict__ Linv,
-                                                  float *__restrict__ Ul, float *__restrict__ Ur, float *__restrict__ SL,
-                                                  float *__restrict__ SR, float *__restrict__ CN) {
+                                                  int h, int root, float *__restrict__ Linv, float *__restrict__ Ul,
+                                                  float *__restrict__ Ur, float *SL, float *SR, float *CN) {
+  constexpr int LD = Q + 1;
+  constexpr long long per = (long long)Q * Q;
   extern __shared__ float bsm[];
-  const int ld = q + 1;
   float *Lm = bsm;            // D_j, factored in place (lower triangle)
-  float *Li = Lm + q * ld;    // L_j^{-1}
-  float *Cl = Li + q * ld;    // C_j: rows of j, columns of j - h
-  float *Cr = Cl + q * ld;    // C_{j+h}^T: rows of j, columns of j + h
-  float *Wl = Cr + q * ld;    // Ul_j
-  float *Wr = Wl + q * ld;    // Ur_j
-  float *diag0 = Wr + q * ld;
-  __shared__ float inv_s;
+  float *Li = Lm + Q * LD;    // L_j^{-1}
+  float *Cl = Li + Q * LD;    // C_j: rows of j, columns of j - h
+  float *Cr = Cl + Q * LD;    // C_{j+h}^T: rows of j, columns of j + h
+  float *Wl = Cr + Q * LD;    // Ul_j
+  float *Wr = Wl + Q * LD;    // Ur_j
+  float *diag0 = Wr + Q * LD;
+  float *rdiag = diag0 + Q;   // 1 / L_rr
   const int j = root ? 0 : h + 2 * h * (int)blockIdx.x;
   const bool hasl = !root, hasr = !root && j + h < S;
-  const long long per = (long long)q * q;
   const int tid = threadIdx.x, nt = blockDim.x;
-  for (int e = tid; e < q * q; e += nt) {
-    const int r = e / q, c = e % q;
-    Lm[r * ld + c] = D[j * per + e];
-    Cl[r * ld + c] = hasl ? C[j * per + e] : 0.f;
-    Cr[c * ld + r] = hasr ? C[(j + h) * per + e] : 0.f;
+  for (int e = tid; e < Q * Q; e += nt) {
+    const int r = e / Q, c = e % Q;
+    float d = D[j * per + e];
+    for (int h2 = 1; h2 < h; h2 <<= 1) {
+      if (j >= h2) d -= SR[(j - h2) * per + e];
+      if (j + h2 < S) d -= SL[(j + h2) * per + e];
+    }
+    Lm[r * LD + c] = d;
+    if (r == c) diag0[r] = d;
+    Cl[r * LD + c] = hasl ? (h == 1 ? C[j * per + e] : CN[(j - h / 2) * per + e]) : 0.f;
+    Cr[c * LD + r] = hasr ? (h == 1 ? C[(j + h) * per + e] : CN[(j + h / 2) * per + e]) : 0.f;
   }
   __syncthreads();
-  for (int r = tid; r < q; r += nt) diag0[r] = Lm[r * ld + r];
-  __syncthreads();
-  for (int c = 0; c < q; ++c) {
-    if (tid == 0) {
-      float piv = Lm[c * ld + c];
+  if (Q <= 32 && tid < 32) {
+    // right-looking Cholesky in registers: lane r holds row r, the pivot and the entries of
+    // column c come from their owners by shuffles
+    constexpr int NR = (Q + 31) / 32;
+    const int lane = tid;
+    float R[NR][Q];
+#pragma unroll
+    for (int u = 0; u < NR; ++u) {
+      const int r = lane + 32 * u;
+#pragma unroll
+      for (int k = 0; k < Q; ++k) R[u][k] = (r < Q) ? Lm[r * LD + k] : 0.f;
+    }
+#pragma unroll
+    for (int c = 0; c < Q; ++c) {
+      float piv = __shfl_sync(0xffffffffu, R[c / 32][c], c % 32);
       const float d0 = diag0[c];
       if (!(piv > 1e-6f * d0)) piv = (d0 > 0.f) ? d0 : 1.f;
-      const float l = sqrtf(piv);
-      Lm[c * ld + c] = l;
-      inv_s = 1.f / l;
-    }
-    __syncthreads();
-    const float inv = inv_s;
-    for (int r = c + 1 + tid; r < q; r += nt) Lm[r * ld + c] *= inv;
-    __syncthreads();
-    const int w = q - c - 1;
-    for (int e = tid; e < w * w; e += nt) {
-      const int r = c + 1 + e / w, cc = c + 1 + e % w;
-      if (cc <= r) Lm[r * ld + cc] -= Lm[r * ld + c] * Lm[cc * ld + c];
-    }
-    __syncthreads();
-  }
-  // L^{-1}: forward substitution against each unit vector, a thread per column
-  for (int col = tid; col < q; col += nt)
-    for (int r = 0; r < q; ++r) {
-      float v = 0.f;
-      if (r >= col) {
-        float sv = (r == col) ? 1.f : 0.f;
-        for (int k = col; k < r; ++k) sv -= Lm[r * ld + k] * Li[k * ld + col];
-        v = sv / Lm[r * ld + r];
+      const float l = sqrtf(piv), inv = 1.f / l;
+#pragma unroll
+      for (int u = 0; u < NR; ++u) {
+        const int r = lane + 32 * u;
+        if (r == c) R[u][c] = l;
+        else if (r > c) R[u][c] *= inv;
       }
-      Li[r * ld + col] = v;
+      if (lane == 0) rdiag[c] = inv;
+#pragma unroll
+      for (int cc = c + 1; cc < Q; ++cc) {
+        const float v = __shfl_sync(0xffffffffu, R[cc / 32][c], cc % 32);  // L[cc][c]
+#pragma unroll
+        for (int u = 0; u < NR; ++u)
+          if (lane + 32 * u >= cc) R[u][cc] -= R[u][c] * v;
+      }
     }
+#pragma unroll
+    for (int u = 0; u < NR; ++u) {
+      const int r = lane + 32 * u;
+      if (r < Q)
+#pragma unroll
+        for (int k = 0; k < Q; ++k) Lm[r * LD + k] = R[u][k];
+    }
+  } else if (Q > 32 && tid < 32) {
+    // the same in shared memory (rows of up to 56 entries do not fit the registers): lane r
+    // owns rows r and r + 32; column c is read into registers before the row updates
+    const int lane = tid;
+    for (int c = 0; c < Q; ++c) {
+      float piv = Lm[c * LD + c];
+      const float d0 = diag0[c];
+      if (!(piv > 1e-6f * d0)) piv = (d0 > 0.f) ? d0 : 1.f;
+      const float l = sqrtf(piv), inv = 1.f / l;
+      __syncwarp();
+      for (int r = lane; r < Q; r += 32) {
+        if (r == c) {
+          Lm[c * LD + c] = l;
+          rdiag[c] = inv;
+        } else if (r > c) {
+          Lm[r * LD + c] *= inv;
+        }
+      }
+      __syncwarp();
+      for (int r = lane; r < Q; r += 32) {
+        if (r <= c) continue;
+        const float lrc = Lm[r * LD + c];
+        float col[Q];
+#pragma unroll
+        for (int cc = 0; cc < Q; ++cc) col[cc] = Lm[cc * LD + c];
+#pragma unroll
+        for (int cc = 1; cc < Q; ++cc)
+          if (cc > c && cc <= r) Lm[r * LD + cc] -= lrc * col[cc];
+      }
+      __syncwarp();
+    }
+  }
   __syncthreads();
-  for (int e = tid; e < q * q; e += nt) Linv[j * per + e] = Li[(e / q) * ld + e % q];
+  // L^{-1}: forward substitution against each unit vector, a thread per column
+  if (tid < Q) {
+    const int col = tid;
+    float x[Q];
+#pragma unroll
+    for (int r = 0; r < Q; ++r) {
+      float s0 = 0.f, s1 = 0.f;
+#pragma unroll
+      for (int k = 0; k < r; ++k) {
+        const float t = (k >= col) ? Lm[r * LD + k] * x[k] : 0.f;
+        if (k & 1) s1 += t;
+        else s0 += t;
+      }
+      x[r] = (r < col) ? 0.f : (((r == col) ? 1.f : 0.f) - (s0 + s1)) * rdiag[r];
+    }
+#pragma unroll
+    for (int r = 0; r < Q; ++r) Li[r * LD + col] = x[r];
+  }
+  __syncthreads();
+  for (int e = tid; e < Q * Q; e += nt) Linv[j * per + e] = Li[(e / Q) * LD + e % Q];
   if (root) return;
-  bcr_mm(Li, false, Cl, false, Wl, ld, q, ld, 1.f);
-  bcr_mm(Li, false, Cr, false, Wr, ld, q, ld, 1.f);
+  bcr_mm<Q, false, false>(Li, Cl, Wl, LD, 1.f);
+  bcr_mm<Q, false, false>(Li, Cr, Wr, LD, 1.f);
   __syncthreads();
-  for (int e = tid; e < q * q; e += nt) {
-    Ul[j * per + e] = Wl[(e / q) * ld + e % q];
-    Ur[j * per + e] = Wr[(e / q) * ld + e % q];
+  for (int e = tid; e < Q * Q; e += nt) {
+    Ul[j * per + e] = Wl[(e / Q) * LD + e % Q];
+    Ur[j * per + e] = Wr[(e / Q) * LD + e % Q];
   }
-  bcr_mm(Wl, true, Wl, false, SL + j * per, q, q, ld, 1.f);
-  bcr_mm(Wr, true, Wr, false, SR + j * per, q, q, ld, 1.f);
-  bcr_mm(Wr, true, Wl, false, CN + j * per, q, q, ld, -1.f);
-}
-
-// Rows active at the next level (J = 2 h t): D_J -= SR_{J-h} + SL_{J+h}, and C_J becomes
-// CN_{J-h}, the coupling of J with J - 2 h through the eliminated row between them.
-__global__ void k_bcr_update(float *__restrict__ D, float *__restrict__ C, const float *__restrict__ SL,
-                             const float *__restrict__ SR, const float *__restrict__ CN, int S, int q, int h) {
-  const long long per = (long long)q * q;
-  const long long na = (S + 2LL * h - 1) / (2LL * h);
-  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < na * per;
-       t += (long long)gridDim.x * blockDim.x) {
-    const long long J = 2LL * h * (t / per), e = t % per;
-    float d = D[J * per + e];
-    if (J >= h) d -= SR[(J - h) * per + e];
-    if (J + h < S) d -= SL[(J + h) * per + e];
-    D[J * per + e] = d;
-    if (J >= 2LL * h) C[J * per + e] = CN[(J - h) * per + e];
-  }
+  bcr_mm<Q, true, false>(Wl, Wl, SL + j * per, Q, 1.f);
+  bcr_mm<Q, true, false>(Wr, Wr, SR + j * per, Q, 1.f);
+  bcr_mm<Q, true, false>(Wr, Wl, CN + j * per, Q, -1.f);
 }
 
 constexpr size_t kBcrSmemMax = 100 * 1024;
 
-size_t bcr_smem(int q) { return ((size_t)6 * q * (q + 1) + q) * sizeof(float); }
+size_t bcr_smem(int q) { return ((size_t)6 * q * (q + 1) + 2 * q) * sizeof(float); }
+
+// Super-row sizes q = p M of the instantiated eliminations (p <= 7, M = 4 or 8).
+template <int Q> void bcr_launch(Ctx *c, int grid, size_t smem, const float *D, const float *C, int S, int h, int root,
+                                 BBPrec &P, float *SL, float *SR, float *CN) {
+  set_smem_limit_once((const void *)k_bcr_elim<Q>, (int)kBcrSmemMax);
+  k_bcr_elim<Q><<<grid, 256, smem, c->stream>>>(D, C, S, h, root, P.Linv.as<float>(), P.Ul.as<float>(),
+                                                P.Ur.as<float>(), SL, SR, CN);
+  TTI_LAUNCH();
+}
+
+void bcr_elim(Ctx *c, int q, int grid, size_t smem, const float *D, const float *C, int S, int h, int root,
+              BBPrec &P, float *SL, float *SR, float *CN) {
+  switch (q) {
+    case 4: bcr_launch<4>(c, grid, smem, D, C, S, h, root, P, SL, SR, CN); break;
+    case 8: bcr_launch<8>(c, grid, smem, D, C, S, h, root, P, SL, SR, CN); break;
+    case 12: bcr_launch<12>(c, grid, smem, D, C, S, h, root, P, SL, SR, CN); break;
+    case 16: bcr_launch<16>(c, grid, smem, D, C, S, h, root, P, SL, SR, CN); break;
+    case 20: bcr_launch<20>(c, grid, smem, D, C, S, h, root, P, SL, SR, CN); break;
+    case 24: bcr_launch<24>(c, grid, smem, D, C, S, h, root, P, SL, SR, CN); break;
+    case 28: bcr_launch<28>(c, grid, smem, D, C, S, h, root, P, SL, SR, CN); break;
+    case 32: bcr_launch<32>(c, grid, smem, D, C, S, h, root, P, SL, SR, CN); break;
+    case 40: bcr_launch<40>(c, grid, smem, D, C, S, h, root, P, SL, SR, CN); break;
+    case 48: bcr_launch<48>(c, grid, smem, D, C, S, h, root, P, SL, SR, CN); break;
+    case 56: bcr_launch<56>(c, grid, smem, D, C, S, h, root, P, SL, SR, CN); break;
+    default: fail(TT_IGA_ERR_ARG, "block-band preconditioner: super-row size %d not instantiated", q);
+  }
+}
 
 template <int M>
 void build_m(Ctx *c, const double *PhiL, int rl, const BandCore &A, const double *PhiR, int rr, BBPrec &P) {
@@ -209,25 +288,14 @@ void build_m(Ctx *c, const double *PhiL, int rl, const BandCore &A, const double
   k_bcr_init<<<grid1d(2LL * S * q * q, 256), 256, 0, c->stream>>>(Blow.as<float>(), n, p, M, S, q, D.as<float>(),
                                                                   C.as<float>());
   TTI_LAUNCH();
-  set_smem_limit_once((const void *)k_bcr_elim, (int)kBcrSmemMax);
   const size_t smem = bcr_smem(q);
   ProfScope ps(c, PROF_PRECOND, 0.0);
   P.levels = 0;
-  for (int h = 1; h < S; h <<= 1, ++P.levels) {
-    const int ne = (S - h + 2 * h - 1) / (2 * h);
-    k_bcr_elim<<<ne, 256, smem, c->stream>>>(D.as<float>(), C.as<float>(), S, q, h, 0, P.Linv.as<float>(),
-                                             P.Ul.as<float>(), P.Ur.as<float>(), SL.as<float>(), SR.as<float>(),
-                                             CN.as<float>());
-    TTI_LAUNCH();
-    const long long na = (S + 2LL * h - 1) / (2LL * h);
-    k_bcr_update<<<grid1d(na * q * q, 256), 256, 0, c->stream>>>(D.as<float>(), C.as<float>(), SL.as<float>(),
-                                                                 SR.as<float>(), CN.as<float>(), S, q, h);
-    TTI_LAUNCH();
-  }
-  k_bcr_elim<<<1, 256, smem, c->stream>>>(D.as<float>(), C.as<float>(), S, q, 0, 1, P.Linv.as<float>(),
-                                          P.Ul.as<float>(), P.Ur.as<float>(), SL.as<float>(), SR.as<float>(),
-                                          CN.as<float>());
-  TTI_LAUNCH();
+  int h = 1;
+  for (; h < S; h <<= 1, ++P.levels)
+    bcr_elim(c, q, (S - h + 2 * h - 1) / (2 * h), smem, D.as<float>(), C.as<float>(), S, h, 0, P, SL.as<float>(),
+             SR.as<float>(), CN.as<float>());
+  bcr_elim(c, q, 1, smem, D.as<float>(), C.as<float>(), S, h, 1, P, SL.as<float>(), SR.as<float>(), CN.as<float>());
 }
 
 }  // namespace
