@@ -59,9 +59,9 @@ FP32_ALU_PEAK_TFLOPS = 80.54  # 152 SMs x 128 FP32 FMA/clk x 2 FLOP x 2.07 GHz
 PCG_TRAFFIC_SOURCES = ("pcg_fused.cu", "pcg_fused.cuh", "bbprec.cu", "bbprec.cuh")
 PCG_TRAFFIC = {  # (workload, "fp64" | "mixed") -> (bytes per launch, sha256 of the sources)
     ("twisted_annulus_p3_n512", "fp64"):
-        (1417472, "bebcaadd0336a69925c8623c36570ebc1d940806410d2eed71676bee0a7fca66"),
+        (1360555, "157968b215895c1ddbd82edd2b3e6e78d2f003790004937f818b7bb9dc4b4b50"),
     ("twisted_annulus_p3_n512", "mixed"):
-        (1094208, "bebcaadd0336a69925c8623c36570ebc1d940806410d2eed71676bee0a7fca66"),
+        (1063125, "157968b215895c1ddbd82edd2b3e6e78d2f003790004937f818b7bb9dc4b4b50"),
 }
 
 
