@@ -56,12 +56,12 @@ FP32_ALU_PEAK_TFLOPS = 80.54  # 152 SMs x 128 FP32 FMA/clk x 2 FLOP x 2.07 GHz
 # step, from one ncu capture whose summary is committed with the profiles, keyed by
 # (workload, precision).  Valid only for the sources they were taken from: reported as null
 # once those change.
-PCG_TRAFFIC_SOURCES = ("pcg_fused.cu", "pcg_fused.cuh", "bbprec.cu", "bbprec.cuh")
+PCG_TRAFFIC_SOURCES = ("pcg_fused_impl.cuh", "pcg_fused.cuh", "bbprec.cu", "bbprec.cuh")
 PCG_TRAFFIC = {  # (workload, "fp64" | "mixed") -> (bytes per launch, sha256 of the sources)
     ("twisted_annulus_p3_n512", "fp64"):
-        (1360555, "157968b215895c1ddbd82edd2b3e6e78d2f003790004937f818b7bb9dc4b4b50"),
+        (1360555, "f8afa7f58a9d36150cd9db39fb23dfe0f238b13a9ad107f018715bc064f960e3"),
     ("twisted_annulus_p3_n512", "mixed"):
-        (1063125, "157968b215895c1ddbd82edd2b3e6e78d2f003790004937f818b7bb9dc4b4b50"),
+        (1063125, "f8afa7f58a9d36150cd9db39fb23dfe0f238b13a9ad107f018715bc064f960e3"),
 }
 
 

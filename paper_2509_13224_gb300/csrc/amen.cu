@@ -454,7 +454,7 @@ struct Amen {
     const int maxit = o.local_maxit;
     const BBPrec *bbp = edge ? &bb : nullptr;
     if (o.precision == TT_IGA_FP64) {
-      // preconditioner factors in FP32 (see pcg_fused.cu, bbprec.cu)
+      // preconditioner factors in FP32 (see pcg_fused_impl.cuh, bbprec.cu)
       DBuf d(c, N * sizeof(double));
       // correction form: B d = r, x += d, checked in FP64
       // correction form B d = r; in FP64 the PCG recurrence residual is the residual of

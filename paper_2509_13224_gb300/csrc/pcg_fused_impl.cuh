@@ -12,6 +12,7 @@
 // Reductions are deterministic: every CTA writes one partial per phase and
 // all CTAs sum the partials in the same order.  The grid barrier spins with an
 // iteration limit; on expiry it raises an error flag and the kernel returns.
+#pragma once
 #include <algorithm>
 
 #include <type_traits>
@@ -1125,10 +1126,5 @@ template <typename T> void pcg_fused(Ctx *c, PcgArgs<T> a, int grid) {
   }
   g_launches.fetch_add(1, std::memory_order_relaxed);
 }
-
-template int pcg_fused_grid<double>(Ctx *, PcgArgs<double> &);
-template int pcg_fused_grid<float>(Ctx *, PcgArgs<float> &);
-template void pcg_fused<double>(Ctx *, PcgArgs<double>, int);
-template void pcg_fused<float>(Ctx *, PcgArgs<float>, int);
 
 }  // namespace ttiga
