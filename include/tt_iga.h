@@ -532,6 +532,19 @@ int tt_iga_gemm_f64(tt_iga_ctx *ctx, int ta, int tb, int m, int n, int k, double
  * = Q R with Q (device, m x k, ld k) orthonormal columns and R (device, k x k
  * upper triangular).  k <= 256.  Q may alias A only if lda == k. */
 int tt_iga_qr(tt_iga_ctx *ctx, int m, int k, const double *A, int lda, double *Q, double *R);
+/* Block-band preconditioner of an AMEn local system (Section 4.1.2, local
+ * solves): solves B z = r once, where B is the symmetric part of
+ * sum_{g,d} PhiL[:, g, :] (x) A[g, :, :, d] (x) PhiR[:, d, :] over the unknowns
+ * x[a][i][c] (index (a n + i) rr + c), with the FP32 factor the AMEn local PCG
+ * uses for interface blocks m = rl rr <= 8 (odd-even reduction of the
+ * block-tridiagonal super-row form).  PhiL (device, rl x Rl x rl), A (device,
+ * band-stored operator core [Rl][n][2p+1][Rr], slot o = j - i + p), PhiR
+ * (device, rr x Rr x rr), r and z (device, rl n rr).  B must be symmetric
+ * positive definite; the result is B^{-1} r to FP32 accuracy.  Returns
+ * TT_IGA_ERR_TOO_LARGE when m > 8, n > 1024 or p > 7.  A test entry point: the
+ * solver applies the same factor inside its PCG. */
+int tt_iga_blockband_solve(tt_iga_ctx *ctx, int rl, int rr, int Rl, int Rr, int n, int p, const double *PhiL,
+                           const double *A, const double *PhiR, const double *r, double *z);
 /* SVD of a small square matrix A (device, k x k): A = U diag(s) V^T by
  * one-sided Jacobi on the rows of A, FP64, singular values descending.
  * U, s, V row-major device buffers (k x k, k, k x k).  U has orthonormal

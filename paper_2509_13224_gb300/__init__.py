@@ -166,6 +166,8 @@ _SIGS = {
                                        ctypes.c_int]),
     "tt_iga_qr": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, _vp, ctypes.c_int, _vp, _vp]),
     "tt_iga_svd_small": (ctypes.c_int, [_vp, ctypes.c_int, _vp, _vp, _vp, _vp]),
+    "tt_iga_blockband_solve": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                              ctypes.c_int, ctypes.c_int, _vp, _vp, _vp, _vp, _vp]),
     "tt_iga_svd_small_noalloc": (ctypes.c_int, [_vp, ctypes.c_int, _vp, _vp, _vp, _vp, _vp]),
     "tt_iga_maxvol": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, _vp, ctypes.c_double, ctypes.c_int, _vp, _vp]),
 }
@@ -696,6 +698,16 @@ def tt_iga_qr(ctx, A, Q, R):
 
 def tt_iga_svd_small(ctx, A, U, s, V):
     _check(ctx, _lib.tt_iga_svd_small(ctx, int(A.shape[0]), _ptr(A), _ptr(U), _ptr(s), _ptr(V)))
+
+
+def tt_iga_blockband_solve(ctx, PhiL, A, PhiR, r, z):
+    """z = B^{-1} r with the block-band preconditioner of the local system B = sym(PhiL (x) A (x) PhiR)
+    (device tensors: PhiL [rl][Rl][rl], A [Rl][n][2p+1][Rr] band-stored, PhiR [rr][Rr][rr], r and z [rl*n*rr])."""
+    rl, Rl = int(PhiL.shape[0]), int(PhiL.shape[1])
+    rr, Rr = int(PhiR.shape[0]), int(PhiR.shape[1])
+    n, p = int(A.shape[1]), (int(A.shape[2]) - 1) // 2
+    _check(ctx, _lib.tt_iga_blockband_solve(ctx, rl, rr, Rl, Rr, n, p, _ptr(PhiL), _ptr(A), _ptr(PhiR), _ptr(r),
+                                            _ptr(z)))
 
 
 def tt_iga_svd_small_noalloc(stream, A, U, s, V, info=None):

@@ -8,7 +8,9 @@
 #include "block.cuh"
 #include "eval.cuh"
 #include "handles.cuh"
+#include "bbprec.cuh"
 #include "linalg.cuh"
+#include "pcg_fused.cuh"
 #include "tt.cuh"
 
 namespace ttiga {
@@ -827,6 +829,20 @@ int tt_iga_qr(tt_iga_ctx *c, int m, int k, const double *A, int lda, double *Q, 
   if (!c || !A || !Q || !R || lda < k) return TT_IGA_ERR_ARG;
   API_TRY
   qr(c, m, k, A, lda, Q, R);
+  c->sync();
+  return TT_IGA_OK;
+  API_CATCH(c)
+}
+
+int tt_iga_blockband_solve(tt_iga_ctx *c, int rl, int rr, int Rl, int Rr, int n, int p, const double *PhiL,
+                           const double *A, const double *PhiR, const double *r, double *z) {
+  if (!c || !PhiL || !A || !PhiR || !r || !z || rl < 1 || rr < 1 || Rl < 1 || Rr < 1) return TT_IGA_ERR_ARG;
+  if (!ttiga::bb_eligible(rl * rr, n, p)) return TT_IGA_ERR_TOO_LARGE;
+  API_TRY
+  ttiga::BandCore core{A, nullptr, Rl, n, 2 * p + 1, p, Rr};
+  ttiga::BBPrec P;
+  ttiga::bb_prec_build(c, PhiL, rl, core, PhiR, rr, P);
+  ttiga::bb_solve_once<double>(c, P, rl, rr, n, p, r, z);
   c->sync();
   return TT_IGA_OK;
   API_CATCH(c)

@@ -50,5 +50,9 @@ template <typename T> struct PcgArgs {
 template <typename T> int pcg_fused_grid(Ctx *c, PcgArgs<T> &a);
 // Launch on the context stream; bar must hold 8 zeroed-or-stale bytes (reset here).
 template <typename T> void pcg_fused(Ctx *c, PcgArgs<T> a, int grid);
+// z = B^{-1} b with a built block-band preconditioner (one CTA, the E phase of PCG).
+struct BBPrec;
+template <typename T>
+void bb_solve_once(Ctx *c, const BBPrec &P, int rl, int rr, int n, int p, const T *b, T *z);
 
 }  // namespace ttiga

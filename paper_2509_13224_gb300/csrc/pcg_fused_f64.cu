@@ -6,5 +6,6 @@ namespace ttiga {
 
 template int pcg_fused_grid<double>(Ctx *, PcgArgs<double> &);
 template void pcg_fused<double>(Ctx *, PcgArgs<double>, int);
+template void bb_solve_once<double>(Ctx *, const BBPrec &, int, int, int, int, const double *, double *);
 
 }  // namespace ttiga

@@ -984,6 +984,18 @@ template <typename T> const void *pick(int p) {
   }
 }
 
+// One application of the block-band preconditioner outside PCG (a test entry point):
+// z = B^{-1} b with the stored factors, by the E phase of the first iteration (x = 0,
+// r = b; tol2 < 0, so the substitutions always run).  One CTA.
+template <typename T, int PB, int M> __global__ void __launch_bounds__(256) k_bb_apply_once(PcgArgs<T> a) {
+  double rr = 0.0, rz = 0.0;
+  bb_apply<T, PB, M>(a, nullptr, 0.0, true, rr, rz);
+}
+
+template <typename T, int PB> const void *bb_once_ptr(int M) {
+  return M == 4 ? (const void *)k_bb_apply_once<T, PB, 4> : (const void *)k_bb_apply_once<T, PB, 8>;
+}
+
 }  // namespace
 
 // Band systems staged per CTA at a time (one warp each) and the shared memory they need.
@@ -1114,6 +1126,45 @@ template <typename T> int pcg_fused_grid(Ctx *c, PcgArgs<T> &a) {
     a.smem = (int)pre_smem;
   }
   return (int)g;
+}
+
+template <typename T>
+void bb_solve_once(Ctx *c, const BBPrec &P, int rl, int rr, int n, int p, const T *b, T *z) {
+  const long long N = (long long)rl * n * rr;
+  DBuf xr(c, 2 * N * sizeof(T));
+  PcgArgs<T> a{};
+  a.b = b;
+  a.x = xr.as<T>();
+  a.r = a.x + N;
+  a.z = z;
+  a.rl = rl;
+  a.rr = rr;
+  a.n = n;
+  a.p = p;
+  a.tol2 = -1.0;
+  a.edge = 1;
+  a.bbLinv = P.Linv.as<float>();
+  a.bbUl = P.Ul.as<float>();
+  a.bbUr = P.Ur.as<float>();
+  a.bbM = P.M;
+  a.bbS = P.S;
+  const void *k = nullptr;
+  switch (p) {
+    case 1: k = bb_once_ptr<T, 1>(P.M); break;
+    case 2: k = bb_once_ptr<T, 2>(P.M); break;
+    case 3: k = bb_once_ptr<T, 3>(P.M); break;
+    case 4: k = bb_once_ptr<T, 4>(P.M); break;
+    case 5: k = bb_once_ptr<T, 5>(P.M); break;
+    case 6: k = bb_once_ptr<T, 6>(P.M); break;
+    case 7: k = bb_once_ptr<T, 7>(P.M); break;
+    default: fail(TT_IGA_ERR_ARG, "block-band solve: degree %d outside 1..7", p);
+  }
+  const size_t smem = (2 * (size_t)P.S + 8) * P.q * sizeof(float);
+  TTI_CHECK_ARG(smem <= kPcgSmemBytes, "block-band solve: n=%d too large", n);
+  TTI_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kPcgSmemBytes));
+  void *args[] = {&a};
+  TTI_CUDA(cudaLaunchKernel(k, dim3(1), dim3(256), args, smem, c->stream));
+  g_launches.fetch_add(1, std::memory_order_relaxed);
 }
 
 template <typename T> void pcg_fused(Ctx *c, PcgArgs<T> a, int grid) {

@@ -241,3 +241,53 @@ def test_fma_peaks_are_physical(tt):
     assert 0.3 < fp64 < 5.0, fp64      # nominal FP64 about 1.25 TFLOP/s
     assert 20.0 < fp32 < 200.0, fp32   # 152 SMs x 128 FP32 FMA/clk x 2 x ~2 GHz is about 80
     assert fp32 > 10.0 * fp64
+
+
+def _spd(rng, m):
+    G = rng.standard_normal((m, m))
+    return G @ G.T / m + np.eye(m)
+
+
+@pytest.mark.parametrize("rl,rr,Rl,Rr,n,p", [(1, 1, 1, 1, 7, 2), (1, 2, 2, 3, 64, 3), (2, 3, 3, 2, 510, 3),
+                                            (2, 2, 1, 2, 5, 3), (3, 2, 2, 2, 37, 2), (1, 4, 2, 2, 100, 4),
+                                            (8, 1, 2, 1, 33, 1), (1, 2, 1, 1, 1024, 3)])
+def test_blockband_solve_matches_dense(tt, ctx, rl, rr, Rl, Rr, n, p):
+    """The block-band preconditioner of the AMEn local solves (odd-even reduction of the block-tridiagonal
+    super-row form, FP32 factor) against a dense FP64 solve of the same SPD local matrix
+    B = sum_{g,d} PhiL_g (x) A_gd (x) PhiR_d: super-row counts 1 (n <= p) to 342, padded tails, blocks of 1 to 8."""
+    import torch
+    rng = np.random.default_rng(n * 31 + rl * 7 + rr)
+    PhiL = np.stack([_spd(rng, rl) for _ in range(Rl)], axis=1)  # [rl][Rl][rl]
+    PhiR = np.stack([_spd(rng, rr) for _ in range(Rr)], axis=1)  # [rr][Rr][rr]
+    A = np.zeros((Rl, n, 2 * p + 1, Rr))
+    B = np.zeros((rl * n * rr, rl * n * rr))
+    for g in range(Rl):
+        for d in range(Rr):
+            Mg = np.zeros((n, n))
+            for o in range(1, p + 1):
+                v = rng.uniform(-1.0, 1.0, n - o) if n > o else np.zeros(0)
+                Mg += np.diag(v, o) + np.diag(v, -o)
+            Mg += np.diag(np.abs(Mg).sum(axis=1) + rng.uniform(0.5, 1.5, n))  # diagonally dominant: SPD
+            for i in range(n):
+                for o in range(2 * p + 1):
+                    j = i + o - p
+                    if 0 <= j < n:
+                        A[g, i, o, d] = Mg[i, j]
+            B += np.kron(PhiL[:, g, :], np.kron(Mg, PhiR[:, d, :]))
+    r = rng.standard_normal(rl * n * rr)
+    ref = np.linalg.solve(B, r)
+    z = torch.zeros(rl * n * rr, dtype=torch.float64, device="cuda")
+    tt.tt_iga_blockband_solve(ctx, _t(PhiL), _t(A), _t(PhiR), _t(r), z)
+    torch.cuda.synchronize()
+    got = z.cpu().numpy()
+    assert np.linalg.norm(got - ref) <= 1e-4 * np.linalg.norm(ref), np.linalg.norm(got - ref) / np.linalg.norm(ref)
+
+
+def test_blockband_solve_rejects_large_blocks(tt, ctx):
+    import torch
+    z = torch.zeros(9 * 8, dtype=torch.float64, device="cuda")
+    PhiL = torch.eye(3, dtype=torch.float64, device="cuda").reshape(3, 1, 3)
+    A = torch.zeros(1, 8, 5, 1, dtype=torch.float64, device="cuda")
+    with pytest.raises(tt.TTIgaError) as e:
+        tt.tt_iga_blockband_solve(ctx, PhiL, A, PhiL, z, z)  # m = 3 x 3 = 9 > 8
+    assert e.value.code == tt.ERR_TOO_LARGE
