@@ -59,9 +59,9 @@ FP32_ALU_PEAK_TFLOPS = 80.54  # 152 SMs x 128 FP32 FMA/clk x 2 FLOP x 2.07 GHz
 PCG_TRAFFIC_SOURCES = ("pcg_fused_impl.cuh", "pcg_fused.cuh", "bbprec.cu", "bbprec.cuh")
 PCG_TRAFFIC = {  # (workload, "fp64" | "mixed") -> (bytes per launch, sha256 of the sources)
     ("twisted_annulus_p3_n512", "fp64"):
-        (1360555, "f8afa7f58a9d36150cd9db39fb23dfe0f238b13a9ad107f018715bc064f960e3"),
+        (1360555, "b161e4c9238ae2a7df6f34ce9cabe1ee24a5d5e8300fa07700314d9e71a0043b"),
     ("twisted_annulus_p3_n512", "mixed"):
-        (1063125, "f8afa7f58a9d36150cd9db39fb23dfe0f238b13a9ad107f018715bc064f960e3"),
+        (1063125, "b161e4c9238ae2a7df6f34ce9cabe1ee24a5d5e8300fa07700314d9e71a0043b"),
 }
 
 
