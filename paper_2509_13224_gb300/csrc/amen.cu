@@ -174,11 +174,16 @@ struct Amen {
   DBuf scal;
   // fork / join events of the preconditioner build on a helper stream (created on first use)
   cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+  // The enrichment chain (z) on a helper stream: its work area, fork / join events, and
+  // whether a join is pending.
+  Work<double> wz;
+  cudaEvent_t ev_zin = nullptr, ev_zout = nullptr;
+  bool z_pending = false;
 
   const TT3 *u0 = nullptr;  // initial iterate (warm start), or null for a random rank-2 TT
 
   Amen(Ctx *c_, const tt_iga_system *s, const tt_iga_solve_opts &opts, const TT3 *start)
-      : c(c_), S(s), F(s->F[opts.rhs_index]), Fnorm(s->F_norm[opts.rhs_index]), o(opts), u0(start), w64{c_}, w32{c_} {
+      : c(c_), S(s), F(s->F[opts.rhs_index]), Fnorm(s->F_norm[opts.rhs_index]), o(opts), u0(start), w64{c_}, w32{c_}, wz{c_} {
     for (int k = 0; k < 4; ++k) { R[k] = S->K.r[k]; f[k] = F.r[k]; }
     for (int k = 0; k < 3; ++k) {
       A[k].A = S->K.core[k].d();
@@ -198,8 +203,62 @@ struct Amen {
   }
 
   ~Amen() {
+    if (z_pending) cudaStreamWaitEvent(c->stream, ev_zout, 0);  // helper reads end before the frees
     if (ev_in) cudaEventDestroy(ev_in);
     if (ev_out) cudaEventDestroy(ev_out);
+    if (ev_zin) cudaEventDestroy(ev_zin);
+    if (ev_zout) cudaEventDestroy(ev_zout);
+  }
+
+  // Context of the enrichment chain: a helper stream under the same conditions as the
+  // preconditioner build (one live context, no caller allocator, no stage timers), else c.
+  // The z cores and their interfaces depend on u only through the truncated solution and
+  // u's interfaces, so the z chain of a step (projected residual and its QR; the backward
+  // orthogonalisation of z) overlaps the u chain and joins before its result is read.
+  Ctx *z_ctx() {
+    if (o.kickrank <= 0 || c->alloc_fn || o.verbose >= 2 || g_live_contexts.load(std::memory_order_relaxed) > 1)
+      return c;
+    return c->sub(0);
+  }
+  void z_fork(Ctx *h) {
+    if (!ev_zin) {
+      TTI_CUDA(cudaEventCreateWithFlags(&ev_zin, cudaEventDisableTiming));
+      TTI_CUDA(cudaEventCreateWithFlags(&ev_zout, cudaEventDisableTiming));
+    }
+    TTI_CUDA(cudaEventRecord(ev_zin, c->stream));
+    TTI_CUDA(cudaStreamWaitEvent(h->stream, ev_zin, 0));
+  }
+  void z_done(Ctx *h) {
+    TTI_CUDA(cudaEventRecord(ev_zout, h->stream));
+    z_pending = true;
+  }
+  void z_join() {
+    if (!z_pending) return;
+    TTI_CUDA(cudaStreamWaitEvent(c->stream, ev_zout, 0));
+    z_pending = false;
+  }
+  // Joins on scope exit, also when an exception unwinds the step: the buffers the helper
+  // reads are freed on c afterwards.
+  struct ZJoinGuard {
+    Amen *a;
+    ~ZJoinGuard() {
+      if (a->z_pending) cudaStreamWaitEvent(a->c->stream, a->ev_zout, 0);
+      a->z_pending = false;
+    }
+  };
+  // Backward orthogonalisation step of z at core k.  Its replaced core k-1 is handed to the
+  // helper first, so that the old buffer is freed in the helper's stream order.
+  void z_orth(int k) {
+    Ctx *h = z_ctx();
+    if (h == c) {
+      orth_right_step(c, z, k);
+      return;
+    }
+    z_fork(h);
+    z.core[k - 1].rehome(h);
+    orth_right_step(h, z, k);
+    z.core[k - 1].rehome(c);
+    z_done(h);
   }
   Amen(const Amen &) = delete;
   Amen &operator=(const Amen &) = delete;
@@ -215,6 +274,7 @@ struct Amen {
     PsiR[k - 1] = DBuf(c, (size_t)u.r[k] * f[k] * sizeof(double));
     rhs_right_update(c, w64, u.core[k].d(), u.r[k], u.r[k + 1], F.core[k].d(), f[k], n(k), f[k + 1], PsiR[k].d(),
                      PsiR[k - 1].d());
+    z_join();  // z's core k from the helper
     PhiRz[k - 1] = DBuf(c, (size_t)z.r[k] * R[k] * u.r[k] * sizeof(double));
     right_update(c, w64, z.core[k].d(), z.r[k], z.r[k + 1], A[k], PhiRz[k].d(), u.core[k].d(), u.r[k], u.r[k + 1],
                  PhiRz[k - 1].d());
@@ -554,6 +614,31 @@ struct Amen {
     r = (int)std::min<long long>(r, right_cap);
     // truncated solution xt = QU[:, :r] SVt[:r]
     gemm<double>(c, false, false, rows, b, r, 1.0, QU.d(), b, 0, SVt.d(), b, 0, 0.0, xt.d(), b, 0, 1);
+    // z core k: residual of xt projected on z's interfaces, on the helper stream when one is
+    // free (it reads xt, z's interfaces and the operator, none of which the enrichment below
+    // changes); joined at the end of this step, before xt is freed and z's interfaces read it
+    if (o.kickrank > 0) {
+      Ctx *h = z_ctx();
+      Work<double> &w = (h == c) ? w64 : wz;
+      if (h != c) {
+        wz.c = h;
+        z_fork(h);
+      }
+      const int zl = z.r[k], zr = z.r[k + 1];
+      DBuf zk(h, (size_t)zl * nk * zr * sizeof(double)), bz(h, (size_t)zl * nk * zr * sizeof(double));
+      rhs_local(h, w, PsiLz[k].d(), zl, F.core[k].d(), f[k], nk, f[k + 1], PsiRz[k].d(), zr, zk.d());
+      apply_local<double>(h, w, PhiLz[k].d(), zl, a, A[k], A[k].A, PhiRz[k].d(), zr, b, xt.d(), bz.d());
+      k_sub<<<grid1d((long long)zl * nk * zr, 256), 256, 0, h->stream>>>(zk.d(), bz.d(), (long long)zl * nk * zr);
+      TTI_LAUNCH();
+      DBuf Zq(h, (size_t)zl * nk * zr * sizeof(double)), Zr(h, (size_t)zr * zr * sizeof(double));
+      qr(h, zl * nk, zr, bz.d(), zr, Zq.d(), Zr.d());
+      if (h != c) {
+        Zq.rehome(c);
+        z_done(h);
+      }
+      z.core[k] = std::move(Zq);
+    }
+    ZJoinGuard zguard{this};  // declared after xt: joins before xt is freed
     // enrichment from the residual projected on z's right interface
     int rho = (o.kickrank > 0) ? z.r[k + 1] : 0;
     rho = std::min(rho, std::max(0, rows - r));
@@ -591,21 +676,10 @@ struct Amen {
     DBuf next(c, (size_t)rn * cols * sizeof(double));
     gemm<double>(c, false, false, rn, (int)cols, b, 1.0, C.d(), b, 0, u.core[k + 1].d(), cols, 0, 0.0, next.d(), cols,
                  0, 1);
-    // z core k: residual of xt projected on z's interfaces
-    if (o.kickrank > 0) {
-      const int zl = z.r[k], zr = z.r[k + 1];
-      DBuf zk(c, (size_t)zl * nk * zr * sizeof(double)), bz(c, (size_t)zl * nk * zr * sizeof(double));
-      rhs_local(c, w64, PsiLz[k].d(), zl, F.core[k].d(), f[k], nk, f[k + 1], PsiRz[k].d(), zr, zk.d());
-      apply_local<double>(c, w64, PhiLz[k].d(), zl, a, A[k], A[k].A, PhiRz[k].d(), zr, b, xt.d(), bz.d());
-      k_sub<<<grid1d((long long)zl * nk * zr, 256), 256, 0, c->stream>>>(zk.d(), bz.d(), (long long)zl * nk * zr);
-      TTI_LAUNCH();
-      DBuf Zq(c, (size_t)zl * nk * zr * sizeof(double)), Zr(c, (size_t)zr * zr * sizeof(double));
-      qr(c, zl * nk, zr, bz.d(), zr, Zq.d(), Zr.d());
-      z.core[k] = std::move(Zq);
-    }
     u.core[k] = std::move(Qe);
     u.core[k + 1] = std::move(next);
     u.r[k + 1] = rn;
+    z_join();
   }
 
   void last_core_z(const double *x) {
@@ -698,8 +772,8 @@ struct Amen {
       // backward orthogonalisation of u and z, refresh right interfaces
       const double tb0 = now_ms();
       for (int k = 2; k >= 1; --k) {
+        if (o.kickrank > 0) z_orth(k);  // on the helper stream, overlapping u's step
         orth_right_step(c, u, k);
-        if (o.kickrank > 0) orth_right_step(c, z, k);
         right_interfaces(k);
       }
       const double tb1 = now_ms();
