@@ -218,7 +218,7 @@ struct Amen {
   Ctx *z_ctx() {
     if (o.kickrank <= 0 || c->alloc_fn || o.verbose >= 2 || g_live_contexts.load(std::memory_order_relaxed) > 1)
       return c;
-    return c->sub(0);
+    return c->sub(1);  // helper 0 builds preconditioners
   }
   void z_fork(Ctx *h) {
     if (!ev_zin) {
@@ -274,13 +274,26 @@ struct Amen {
     PsiR[k - 1] = DBuf(c, (size_t)u.r[k] * f[k] * sizeof(double));
     rhs_right_update(c, w64, u.core[k].d(), u.r[k], u.r[k + 1], F.core[k].d(), f[k], n(k), f[k + 1], PsiR[k].d(),
                      PsiR[k - 1].d());
-    z_join();  // z's core k from the helper
-    PhiRz[k - 1] = DBuf(c, (size_t)z.r[k] * R[k] * u.r[k] * sizeof(double));
-    right_update(c, w64, z.core[k].d(), z.r[k], z.r[k + 1], A[k], PhiRz[k].d(), u.core[k].d(), u.r[k], u.r[k + 1],
-                 PhiRz[k - 1].d());
-    PsiRz[k - 1] = DBuf(c, (size_t)z.r[k] * f[k] * sizeof(double));
-    rhs_right_update(c, w64, z.core[k].d(), z.r[k], z.r[k + 1], F.core[k].d(), f[k], n(k), f[k + 1], PsiRz[k].d(),
-                     PsiRz[k - 1].d());
+    // z's interfaces on the enrichment stream (after z's core k there, after u's core k here);
+    // read on c only by the enrichment of a truncation, which joins first
+    Ctx *h = z_ctx();
+    Work<double> &w = (h == c) ? w64 : wz;
+    if (h != c) {
+      wz.c = h;
+      z_fork(h);
+    }
+    DBuf phz(h, (size_t)z.r[k] * R[k] * u.r[k] * sizeof(double)), psz(h, (size_t)z.r[k] * f[k] * sizeof(double));
+    right_update(h, w, z.core[k].d(), z.r[k], z.r[k + 1], A[k], PhiRz[k].d(), u.core[k].d(), u.r[k], u.r[k + 1],
+                 phz.d());
+    rhs_right_update(h, w, z.core[k].d(), z.r[k], z.r[k + 1], F.core[k].d(), f[k], n(k), f[k + 1], PsiRz[k].d(),
+                     psz.d());
+    if (h != c) {
+      phz.rehome(c);
+      psz.rehome(c);
+      z_done(h);
+    }
+    PhiRz[k - 1] = std::move(phz);
+    PsiRz[k - 1] = std::move(psz);
   }
 
   void left_interfaces(int k) {  // from core k (0 or 1) into index k+1
@@ -290,12 +303,27 @@ struct Amen {
     PsiL[k + 1] = DBuf(c, (size_t)u.r[k + 1] * f[k + 1] * sizeof(double));
     rhs_left_update(c, w64, u.core[k].d(), u.r[k], u.r[k + 1], PsiL[k].d(), F.core[k].d(), f[k], n(k), f[k + 1],
                     PsiL[k + 1].d());
-    PhiLz[k + 1] = DBuf(c, (size_t)z.r[k + 1] * R[k + 1] * u.r[k + 1] * sizeof(double));
-    left_update(c, w64, z.core[k].d(), z.r[k], z.r[k + 1], PhiLz[k].d(), A[k], u.core[k].d(), u.r[k], u.r[k + 1],
-                PhiLz[k + 1].d());
-    PsiLz[k + 1] = DBuf(c, (size_t)z.r[k + 1] * f[k + 1] * sizeof(double));
-    rhs_left_update(c, w64, z.core[k].d(), z.r[k], z.r[k + 1], PsiLz[k].d(), F.core[k].d(), f[k], n(k), f[k + 1],
-                    PsiLz[k + 1].d());
+    // z's interfaces on the enrichment stream, overlapping the next local solve; read there by
+    // the next step's z chain, and on c by the last core's z update after a join
+    Ctx *h = z_ctx();
+    Work<double> &w = (h == c) ? w64 : wz;
+    if (h != c) {
+      wz.c = h;
+      z_fork(h);
+    }
+    DBuf phz(h, (size_t)z.r[k + 1] * R[k + 1] * u.r[k + 1] * sizeof(double)),
+        psz(h, (size_t)z.r[k + 1] * f[k + 1] * sizeof(double));
+    left_update(h, w, z.core[k].d(), z.r[k], z.r[k + 1], PhiLz[k].d(), A[k], u.core[k].d(), u.r[k], u.r[k + 1],
+                phz.d());
+    rhs_left_update(h, w, z.core[k].d(), z.r[k], z.r[k + 1], PsiLz[k].d(), F.core[k].d(), f[k], n(k), f[k + 1],
+                    psz.d());
+    if (h != c) {
+      phz.rehome(c);
+      psz.rehome(c);
+      z_done(h);
+    }
+    PhiLz[k + 1] = std::move(phz);
+    PsiLz[k + 1] = std::move(psz);
   }
 
   void init() {
@@ -549,6 +577,7 @@ struct Amen {
 
   // Truncate the solution x of core k (k < 2) and enrich; updates u cores k, k+1.
   void truncate_enrich(int k, const double *rhs, const double *x, double tol_trunc) {
+    z_join();  // z's interfaces from the enrichment stream
     const int a = rl(k), nk = n(k), b = rr(k);
     const int rows = a * nk;
     DBuf Q(c, (size_t)rows * b * sizeof(double)), Rm(c, (size_t)b * b * sizeof(double));
@@ -684,6 +713,7 @@ struct Amen {
 
   void last_core_z(const double *x) {
     if (o.kickrank <= 0) return;
+    z_join();  // z's left interfaces of core 2
     const int k = 2, zl = z.r[2], nk = n(2);
     DBuf zk(c, (size_t)zl * nk * sizeof(double)), bz(c, (size_t)zl * nk * sizeof(double));
     rhs_local(c, w64, PsiLz[k].d(), zl, F.core[k].d(), f[k], nk, 1, PsiRz[k].d(), 1, zk.d());
@@ -797,6 +827,7 @@ struct Amen {
         check_pending = true;
       }
     }
+    z_join();  // the solve ends when its helper work does
     st.ranks[0] = u.r[1];
     st.ranks[1] = u.r[2];
     st.converged = status == TT_IGA_OK;
