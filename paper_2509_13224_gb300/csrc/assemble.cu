@@ -8,6 +8,7 @@
 // One thread per band output, consecutive threads on consecutive beta so
 // reads of G and writes of M are coalesced along the rank.
 #include <algorithm>
+#include <utility>
 #include <cmath>
 
 #include "amen_ops.cuh"
@@ -202,9 +203,12 @@ void assemble_system(Ctx *c, const tt_iga_geom *g, const tt_iga_rhs_desc *rhs, i
   std::vector<TT3> F(n_rhs);
   std::vector<double> F_norm(n_rhs, 0.0);
 
-  // K = sum of the K_ab terms, rounded after every addition.  The additions form a
-  // pairwise tree whose levels run concurrently: the same number of roundings
-  // as a left-to-right sum, fewer of them one after another.
+  // K = sum of the K_ab terms, rounded after every summation step (Section 4.2.1), which
+  // keeps the ranks from inflating.  A step sums as many consecutive terms as keep the
+  // summed ranks within kSumRankCap (at least two), since rounding a sum of ranks up to
+  // that cap costs about what rounding a pair does, and the groups of a level run
+  // concurrently; with the low-rank coefficient fields of smooth geometries one step
+  // takes all terms, one rounding instead of a tree of them.
   auto build_operator = [&](Ctx *h) {
     std::vector<TT3> terms;
     static const int pairs[6][2] = {{0, 0}, {1, 1}, {2, 2}, {0, 1}, {0, 2}, {1, 2}};
@@ -226,15 +230,35 @@ void assemble_system(Ctx *c, const tt_iga_geom *g, const tt_iga_rhs_desc *rhs, i
       }
     }
     TTI_CHECK_ARG(!terms.empty(), "assemble: every coefficient field vanished");
+    constexpr int kSumRankCap = 32;
     while (terms.size() > 1) {
-      const int np = (int)terms.size() / 2;
-      std::vector<TT3> next(np);
-      run_concurrent(h, np, [&](int q, Ctx *hh) {
-        tt_sum(hh, terms[2 * q], 1.0, terms[2 * q + 1], 1.0, next[q]);
+      std::vector<std::pair<int, int>> groups;  // [begin, end) of consecutive terms
+      const int nt = (int)terms.size();
+      for (int i0 = 0; i0 < nt;) {
+        int r1 = terms[i0].r[1], r2 = terms[i0].r[2], i1 = i0 + 1;
+        while (i1 < nt && r1 + terms[i1].r[1] <= kSumRankCap && r2 + terms[i1].r[2] <= kSumRankCap) {
+          r1 += terms[i1].r[1];
+          r2 += terms[i1].r[2];
+          ++i1;
+        }
+        if (i1 == i0 + 1 && i1 < nt) ++i1;  // at least a pair: every level shrinks
+        groups.emplace_back(i0, i1);
+        i0 = i1;
+      }
+      std::vector<TT3> next(groups.size());
+      std::vector<int> sums;  // groups that are summed and rounded (a lone last term moves on)
+      for (int q = 0; q < (int)groups.size(); ++q) {
+        if (groups[q].second - groups[q].first == 1) next[q] = std::move(terms[groups[q].first]);
+        else sums.push_back(q);
+      }
+      run_concurrent(h, (int)sums.size(), [&](int t, Ctx *hh) {
+        const int q = sums[t];
+        std::vector<const TT3 *> xs;
+        for (int i = groups[q].first; i < groups[q].second; ++i) xs.push_back(&terms[i]);
+        tt_sum_many(hh, xs, next[q]);
         tt_round(hh, next[q], round_tol, 0);
         for (int d = 0; d < 3; ++d) next[q].core[d].rehome(h);
       });
-      if (terms.size() % 2) next.push_back(std::move(terms.back()));
       terms = std::move(next);  // the consumed terms are freed on h, after the helpers (ordered by the join)
     }
     K = std::move(terms[0]);

@@ -2,8 +2,10 @@
 // evaluation and densification.
 #include <algorithm>
 #include <cmath>
+#include <vector>
 
 #include "linalg.cuh"
+
 #include "tt.cuh"
 
 namespace ttiga {
@@ -72,6 +74,31 @@ void tt_sum(Ctx *c, const TT3 &x, double a, const TT3 &y, double b, TT3 &out) {
   embed(c, o.core[1].d(), o.r[1], o.m[1], o.r[2], y.core[1].d(), y.r[1], y.r[2], x.r[1], x.r[2], 1.0);
   embed(c, o.core[2].d(), o.r[2], o.m[2], 1, x.core[2].d(), x.r[2], 1, 0, 0, 1.0);
   embed(c, o.core[2].d(), o.r[2], o.m[2], 1, y.core[2].d(), y.r[2], 1, x.r[2], 0, 1.0);
+  out = std::move(o);
+}
+
+void tt_sum_many(Ctx *c, const std::vector<const TT3 *> &xs, TT3 &out) {
+  TTI_CHECK_ARG(!xs.empty(), "tt_sum_many: no terms");
+  TT3 o;
+  for (int k = 0; k < 3; ++k) o.m[k] = xs[0]->m[k];
+  o.r[0] = 1;
+  o.r[3] = 1;
+  o.r[1] = o.r[2] = 0;
+  for (const TT3 *x : xs) {
+    for (int k = 0; k < 3; ++k) TTI_CHECK_ARG(x->m[k] == o.m[k], "tt_sum_many: mode sizes differ");
+    o.r[1] += x->r[1];
+    o.r[2] += x->r[2];
+  }
+  o.alloc(c);
+  for (int k = 0; k < 3; ++k) c->zero(o.core[k].get(), o.core_elems(k) * sizeof(double));
+  int off1 = 0, off2 = 0;
+  for (const TT3 *x : xs) {
+    embed(c, o.core[0].d(), 1, o.m[0], o.r[1], x->core[0].d(), 1, x->r[1], 0, off1, 1.0);
+    embed(c, o.core[1].d(), o.r[1], o.m[1], o.r[2], x->core[1].d(), x->r[1], x->r[2], off1, off2, 1.0);
+    embed(c, o.core[2].d(), o.r[2], o.m[2], 1, x->core[2].d(), x->r[2], 1, off2, 0, 1.0);
+    off1 += x->r[1];
+    off2 += x->r[2];
+  }
   out = std::move(o);
 }
 

@@ -1,5 +1,6 @@
 // Order-3 tensor-train operations on the device (Section 4.1.1).
 #pragma once
+#include <vector>
 #include "common.cuh"
 
 namespace ttiga {
@@ -8,6 +9,8 @@ namespace ttiga {
 void tt_copy(Ctx *c, const TT3 &x, TT3 &y);
 // y = a x + b y as a TT of rank r_x + r_y (block cores); a is applied to core 1.
 void tt_sum(Ctx *c, const TT3 &x, double a, const TT3 &y, double b, TT3 &out);
+// out = sum of the terms, unrounded: ranks add up (block-diagonal inner cores).
+void tt_sum_many(Ctx *c, const std::vector<const TT3 *> &xs, TT3 &out);
 // In-place TT rounding to relative accuracy eps (Oseledets 2011): right-to-left
 // QR orthogonalisation, left-to-right truncated SVD with threshold
 // eps ||X|| / sqrt(2).  Ranks capped at max_rank (0: none).  Returns ||X||_F.
