@@ -231,6 +231,7 @@ void assemble_system(Ctx *c, const tt_iga_geom *g, const tt_iga_rhs_desc *rhs, i
     }
     TTI_CHECK_ARG(!terms.empty(), "assemble: every coefficient field vanished");
     constexpr int kSumRankCap = 32;
+    bool restricted = false;
     while (terms.size() > 1) {
       std::vector<std::pair<int, int>> groups;  // [begin, end) of consecutive terms
       const int nt = (int)terms.size();
@@ -245,6 +246,9 @@ void assemble_system(Ctx *c, const tt_iga_geom *g, const tt_iga_rhs_desc *rhs, i
         groups.emplace_back(i0, i1);
         i0 = i1;
       }
+      // the level that leaves one term makes the operator: without a lift its Dirichlet
+      // restriction (linear) goes before that rounding, which then serves both
+      const bool last = groups.size() == 1;
       std::vector<TT3> next(groups.size());
       std::vector<int> sums;  // groups that are summed and rounded (a lone last term moves on)
       for (int q = 0; q < (int)groups.size(); ++q) {
@@ -256,18 +260,22 @@ void assemble_system(Ctx *c, const tt_iga_geom *g, const tt_iga_rhs_desc *rhs, i
         std::vector<const TT3 *> xs;
         for (int i = groups[q].first; i < groups[q].second; ++i) xs.push_back(&terms[i]);
         tt_sum_many(hh, xs, next[q]);
+        if (last && !lift) restrict_tt(hh, next[q], bl, p, true);
         tt_round(hh, next[q], round_tol, 0);
         for (int d = 0; d < 3; ++d) next[q].core[d].rehome(h);
       });
       terms = std::move(next);  // the consumed terms are freed on h, after the helpers (ordered by the join)
+      if (last && !lift) restricted = true;
     }
     K = std::move(terms[0]);
     if (lift) {
       Kfull = clone_tt(h, K);
       for (int d = 0; d < 3; ++d) Kfull.core[d].rehome(c);
     }
-    restrict_tt(h, K, bl, p, true);
-    tt_round(h, K, round_tol, 0);
+    if (!restricted) {
+      restrict_tt(h, K, bl, p, true);
+      tt_round(h, K, round_tol, 0);
+    }
     for (int d = 0; d < 3; ++d) K.core[d].rehome(c);
   };
 
