@@ -125,6 +125,9 @@ struct Ctx {
   std::vector<std::unique_ptr<Ctx>> subs;
   Ctx *sub(int i);
   void release_subs();
+  // Host worker threads of run_concurrent, created on first use and kept for the
+  // context's lifetime (a new thread's first CUDA call costs a few hundred microseconds).
+  std::shared_ptr<struct WorkerPool> pool;
 
   // Live CUDA-event timing of one kernel family (0 = off), for roofline reporting.
   int prof_family = 0;

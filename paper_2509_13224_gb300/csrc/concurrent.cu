@@ -3,6 +3,8 @@
 // each part runs on a host thread with a helper context of its own stream, so
 // the host read-backs inside one part (ranks, pivots, validation maxima) no
 // longer serialise the others.  Ordering with the parent stream uses events.
+#include <condition_variable>
+#include <deque>
 #include <exception>
 #include <mutex>
 #include <set>
@@ -12,6 +14,63 @@
 #include "common.cuh"
 
 namespace ttiga {
+
+// Persistent host threads for run_concurrent: each sets the device once, then runs tasks
+// from a queue until the pool is destroyed.
+struct WorkerPool {
+  int device = 0;
+  std::mutex mu;
+  std::condition_variable cv;
+  std::deque<std::function<void()>> tasks;
+  std::vector<std::thread> threads;
+  bool stop = false;
+
+  explicit WorkerPool(int dev) : device(dev) {}
+  ~WorkerPool() {
+    {
+      std::lock_guard<std::mutex> lk(mu);
+      stop = true;
+    }
+    cv.notify_all();
+    for (auto &t : threads) t.join();
+  }
+  void ensure(int n) {
+    while ((int)threads.size() < n)
+      threads.emplace_back([this] {
+        cudaSetDevice(device);
+        for (;;) {
+          std::function<void()> task;
+          {
+            std::unique_lock<std::mutex> lk(mu);
+            cv.wait(lk, [this] { return stop || !tasks.empty(); });
+            if (tasks.empty()) return;  // stop requested and nothing left
+            task = std::move(tasks.front());
+            tasks.pop_front();
+          }
+          task();
+        }
+      });
+  }
+  // Run the n tasks concurrently (the pool has at least n threads) and wait for all.
+  void run(std::vector<std::function<void()>> &batch) {
+    ensure((int)batch.size());
+    std::mutex dmu;
+    std::condition_variable dcv;
+    int left = (int)batch.size();
+    {
+      std::lock_guard<std::mutex> lk(mu);
+      for (auto &f : batch)
+        tasks.emplace_back([&f, &dmu, &dcv, &left] {
+          f();
+          std::lock_guard<std::mutex> l2(dmu);
+          if (--left == 0) dcv.notify_all();
+        });
+    }
+    cv.notify_all();
+    std::unique_lock<std::mutex> lk(dmu);
+    dcv.wait(lk, [&] { return left == 0; });
+  }
+};
 
 Ctx *Ctx::sub(int i) {
   while ((int)subs.size() <= i) {
@@ -31,6 +90,7 @@ Ctx *Ctx::sub(int i) {
 }
 
 void Ctx::release_subs() {
+  pool.reset();  // joins the worker threads (no task is running: every run_concurrent waited for its own)
   for (auto &s : subs) {
     s->release_subs();
     if (s->stream) cudaStreamSynchronize(s->stream);
@@ -54,18 +114,18 @@ void run_concurrent(Ctx *c, int n, const std::function<void(int, Ctx *)> &f) {
   for (int i = 0; i < n; ++i) TTI_CUDA(cudaStreamWaitEvent(h[i]->stream, start, 0));
   cudaEventDestroy(start);
   std::vector<std::exception_ptr> err(n);
-  std::vector<std::thread> th;
-  th.reserve(n);
+  std::vector<std::function<void()>> batch;
+  batch.reserve(n);
   for (int i = 0; i < n; ++i)
-    th.emplace_back([&, i] {
+    batch.emplace_back([&, i] {
       try {
-        TTI_CUDA(cudaSetDevice(c->device));
         f(i, h[i]);
       } catch (...) {
         err[i] = std::current_exception();
       }
     });
-  for (auto &t : th) t.join();
+  if (!c->pool) c->pool = std::make_shared<WorkerPool>(c->device);
+  c->pool->run(batch);
   for (int i = 0; i < n; ++i) {
     cudaEvent_t done;
     TTI_CUDA(cudaEventCreateWithFlags(&done, cudaEventDisableTiming));
