@@ -169,8 +169,18 @@ struct Ctx {
     }
     return pinned;
   }
-  // Copy device -> host synchronously through the pinned scratch.
+  // Copy device -> host synchronously.  Small read-backs (ranks, pivots, norms, singular
+  // values: the host decisions of every call) go through the context's pinned scratch,
+  // which a pageable destination would otherwise make the driver stage on every call.
+  static constexpr size_t kPinnedSmall = 256 * 1024;
   void d2h(void *dst, const void *src, size_t bytes) {
+    if (bytes <= kPinnedSmall) {
+      void *h = host_scratch(kPinnedSmall);
+      TTI_CUDA(cudaMemcpyAsync(h, src, bytes, cudaMemcpyDeviceToHost, stream));
+      sync();
+      memcpy(dst, h, bytes);
+      return;
+    }
     TTI_CUDA(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToHost, stream));
     sync();
   }
